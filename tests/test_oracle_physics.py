@@ -1,0 +1,123 @@
+"""Physics pins of the FP64 oracle: what the paper fixes about the whole step.
+
+* Per-component mass is conserved to round-off (Eqs. consconstr, ome3_1/2 and
+  streaming/bounce-back move mass without creating it).
+* Laplace's law (p_B - p_A) = sigma (div n) = 2 sigma/R for a static droplet
+  (extended Young-Laplace relation with pi = 0), with sigma = (4/9) A/omega_bar
+  (Eq. sigmaA).
+* Poiseuille flow in the single-fluid limit: the steady profile between
+  halfway bounce-back walls is the parabola with curvature -g/nu,
+  nu = c_s^2 (tau - 1/2).
+* Near-contact control: two identical droplets pushed together by opposite
+  body forces merge without the repulsion and stay apart with it
+  (near-contact paragraph: the force "prevents droplet merging"); the literal
+  opposite sign of the force does not keep them apart.
+* Mirror symmetry of the two-droplet configuration over a short horizon.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _sim(**kw):
+    shape = kw.pop("shape")
+    return oracle.OracleSim(oracle.make_params(*shape, **kw))
+
+
+def test_mass_conservation_single_droplet():
+    s = _sim(shape=(32, 32, 32))
+    s.init_droplets([[16, 16, 16]], [8.0])
+    r0 = s.reduce()
+    s.step(200)
+    r1 = s.reduce()
+    assert abs(r1[0] - r0[0]) / r0[0] < 1e-13
+    assert abs(r1[1] - r0[1]) / r0[1] < 1e-13
+    # no body force: total momentum stays at round-off
+    assert np.all(np.abs(r1[2:5]) < 1e-11)
+
+
+def test_mass_conservation_walls_force_repulsion():
+    s = _sim(shape=(16, 18, 32), walls=0b010, A_h=0.1, g=(0, 0, 1e-4), g_mode=2)
+    s.init_droplets([[8, 9, 10], [8, 9, 22]], [5.0, 5.0], width=1.0)
+    r0 = s.reduce()
+    s.step(100)
+    r1 = s.reduce()
+    assert abs(r1[0] - r0[0]) / r0[0] < 1e-13
+    assert abs(r1[1] - r0[1]) / r0[1] < 1e-13
+    assert r1[6] > 0  # the repulsion was active
+
+
+@pytest.mark.slow
+def test_laplace_law():
+    A, tau = 0.01, 1.0
+    sigma = 4.0 / 9.0 * A * tau  # Eq. sigmaA with A_A = A_B, omega_bar = 1/tau
+    ratios = []
+    for R in (8.0, 10.0):
+        s = _sim(shape=(32, 32, 32), A_a=A, A_b=A, tau_a=tau, tau_b=tau)
+        s.init_droplets([[16, 16, 16]], [R])
+        s.step(1000)
+        vol = s.reduce()[5]
+        R_eff = (3.0 * vol / (4.0 * np.pi)) ** (1.0 / 3.0)
+        dp = s.laplace(0.9)
+        ratios.append(dp / (2.0 * sigma / R_eff))
+    # within a few percent, approaching 1 as the droplet grows relative to the
+    # interface width
+    assert 0.97 < ratios[1] < 1.05
+    assert 0.97 < ratios[0] < 1.06
+    assert abs(ratios[1] - 1.0) < abs(ratios[0] - 1.0)
+
+
+def test_poiseuille_single_fluid():
+    ny, g, tau = 34, 1e-6, 1.0
+    s = _sim(shape=(4, ny, 4), walls=0b010, tau_a=tau, tau_b=tau, g=(0, 0, g), g_mode=1)
+    s.init_fields(-np.ones((4, ny, 4)))  # pure B: no interface, plain forced BGK
+    s.step(20000)
+    f = s.fields()
+    u = f["uz"][0, :, 0]
+    assert np.all(f["uz"] == f["uz"][:1, :, :1])
+    nu = (tau - 0.5) / 3.0
+    sec = u[1:-3] - 2 * u[2:-2] + u[3:-1]
+    np.testing.assert_allclose(sec, -g / nu, rtol=1e-8)
+    y = np.arange(ny)
+    ua = g / (2 * nu) * (y - 0.5) * (ny - 1.5 - y)  # walls half way between nodes
+    assert np.abs(u[1:-1] - ua[1:-1]).max() < 0.01 * ua.max()
+    assert np.abs(f["ux"]).max() < 1e-11 * ua.max() and np.abs(f["uy"]).max() < 1e-11 * ua.max()
+
+
+def _pair(A_h, steps):
+    nz, R, gap, g, nx = 56, 6.0, 4.0, 5e-5, 20
+    s = _sim(shape=(nx, nx, nz), A_h=A_h, h_min=3, h_max=3, g=(0, 0, g), g_mode=2)
+    s.init_droplets([[nx / 2, nx / 2, nz / 2 - R - gap / 2], [nx / 2, nx / 2, nz / 2 + R + gap / 2]], [R, R])
+    counts = []
+    for _ in range(steps // 100):
+        s.step(100)
+        counts.append(s.droplet_count())
+    return s, counts
+
+
+@pytest.mark.slow
+def test_near_contact_prevents_coalescence():
+    _, off = _pair(0.0, 600)
+    _, on = _pair(0.1, 600)
+    _, flipped = _pair(-0.1, 600)
+    assert off[-1] == 1, off            # without repulsion the pair merges
+    assert all(c == 2 for c in on), on  # with it they stay apart
+    first_merge_off = off.index(1)
+    assert 1 in flipped and flipped.index(1) <= first_merge_off  # opposite sign: no protection
+
+
+def test_pair_mirror_symmetry_short_horizon():
+    """z -> nz - z maps the configuration onto itself (odd body force); the
+    FP64 fields stay mirror-symmetric to round-off over the first steps (later
+    the near-contact decisions on the midplane amplify round-off)."""
+    nz, nx = 56, 20
+    s = _sim(shape=(nx, nx, nz), A_h=0.1, h_min=3, h_max=3, g=(0, 0, 5e-5), g_mode=2)
+    s.init_droplets([[10, 10, 20], [10, 10, 36]], [6.0, 6.0])
+    s.step(6)
+    f = s.fields()
+    mz = lambda a: np.roll(a[::-1], 1, axis=0)
+    assert np.abs(f["phi"] - mz(f["phi"])).max() < 1e-12
+    assert np.abs(f["uz"] + mz(f["uz"])).max() < 1e-12
+    np.testing.assert_array_equal(f["h"], mz(f["h"]))
+    assert (f["h"] > 0).sum() > 0

@@ -1,0 +1,209 @@
+/*
+ * lbcg.h -- C ABI of the GB300 colour-gradient lattice Boltzmann library.
+ *
+ * One time step of the two-component colour-gradient lattice Boltzmann scheme
+ * on D3Q27 with the coarse-grained near-contact repulsion of arXiv 2405.14551:
+ *   BGK collision on the total populations   (Sec. III.B Eq. eq:lbm,
+ *                                             Sec. III.C.1 Eq. CGLBE),
+ *   surface-tension perturbation             (Sec. III.C.1, Omega^(2), Eq. sigmaA),
+ *   Latva-Kokko recolouring                  (Eqs. ome3_1, ome3_2),
+ *   near-contact force F_rep = -A_h n delta_I (Eqs. stress_jump, near_cont_force),
+ *   forcing term (Guo)                       (near-contact paragraph: "forcing contribution"),
+ *   streaming with periodic wrap and halfway bounce-back walls (Sec. III.D).
+ *
+ * Every function returns LB_OK (0) or a negative LB_E* code; lb_strerror()
+ * names it and lb_last_error() gives the detail of the last failure on the
+ * calling thread.  Nothing falls back to the CPU: without a CUDA device the
+ * calls fail with LB_ECUDA.
+ *
+ * Threading: a handle is not thread safe; distinct handles may be used from
+ * distinct threads.  All device work of a handle is issued on its stream
+ * (lb_set_stream, default: the legacy default stream).
+ */
+#ifndef LBCG_H
+#define LBCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define LB_OK 0
+#define LB_EINVAL -1    /* an argument failed host-side validation; no GPU work was issued */
+#define LB_ENOMEM -2    /* a device or host allocation failed */
+#define LB_ECUDA -3     /* a CUDA runtime call failed (detail in lb_last_error) */
+#define LB_EUNSTABLE -4 /* the device status word saw a non-finite or non-positive density */
+#define LB_ETIMEOUT -5  /* a bounded device wait gave up */
+#define LB_ESTATE -6    /* the call is not valid in the handle's current state */
+#define LB_EIO -7       /* file read/write failed or the file is not a checkpoint of this grid */
+
+/* ---- population storage formats ---------------------------------------- */
+/* Two population sets f^A, f^B in FP32, [comp][27][nz][ny][nx]; 432 B per node update. */
+#define LB_STORAGE_TWOSET_F32 0
+/* Exact single-set form: total post-collision f* (27 x FP32) plus the colour
+ * scalars s = rhoA/rho and v = beta rhoA rhoB/rho n (4 x FP32); the pulling
+ * node rebuilds f^A_i = s f*_i + w_i c_i.v/|c_i| (recolouring, Eq. ome3_1). */
+#define LB_STORAGE_REDUCED_F32 1
+/* As REDUCED_F32 but f*_i stored as FP16 deviations (f*_i - w_i) * 4096 from
+ * the rest equilibrium at rho_0 = 1, u_0 = 0 (Sec. IV.B, Eq. eq:shift_f); all
+ * arithmetic in FP32. */
+#define LB_STORAGE_REDUCED_F16 2
+/* Two population sets in FP64, FP64 arithmetic (parity instantiation). */
+#define LB_STORAGE_TWOSET_F64 3
+
+/* ---- field selection for lb_fields: bit k selects field k --------------- */
+#define LB_F_PHI (1u << 0)  /* order parameter (rhoA-rhoB)/(rhoA+rhoB), Eq. order_param */
+#define LB_F_RHO (1u << 1)  /* total density, Sec. III.C.1 */
+#define LB_F_UX (1u << 2)   /* barycentric velocity u = (j + F/2)/rho */
+#define LB_F_UY (1u << 3)
+#define LB_F_UZ (1u << 4)
+#define LB_F_RHOA (1u << 5)
+#define LB_F_RHOB (1u << 6)
+#define LB_F_FRX (1u << 7)  /* near-contact force F_rep, Eq. near_cont_force */
+#define LB_F_FRY (1u << 8)
+#define LB_F_FRZ (1u << 9)
+#define LB_F_H (1u << 10)   /* near-contact distance h(x) in lattice units, 0 = inactive */
+#define LB_F_GX (1u << 11)  /* colour gradient grad phi */
+#define LB_F_GY (1u << 12)
+#define LB_F_GZ (1u << 13)
+#define LB_NFIELDS 14
+
+typedef struct lb_handle lb_handle;
+
+/* Lattice box.  x is fastest: node (x,y,z) has index x + nx*(y + ny*z).
+ * walls bit a (a = 0,1,2 for x,y,z) makes layers 0 and n_a-1 of that axis
+ * solid (halfway bounce-back); other axes are periodic (Sec. III.D). */
+typedef struct {
+  int32_t nx, ny, nz;
+  uint32_t walls;
+} lb_grid;
+
+/* Model parameters, named after the paper's notation (Sec. III.C.1). */
+typedef struct {
+  double tau_a, tau_b;    /* relaxation times (> 0.5); nu_k = (tau_k - 1/2)/3, mixed harmonically (Eq. sigmaA) */
+  double A_a, A_b;        /* perturbation amplitudes A_k; sigma = (2/9)(A_a + A_b) tau_bar */
+  double beta;            /* recolouring parameter, [0, 1] */
+  double A_h;             /* near-contact strength A_h (0 switches the force off) */
+  double h_min, h_max;    /* A_h constant for h <= h_min, ~ h^-3 up to h_max, 0 beyond; 1 <= h_max <= 6 */
+  double phi_I;           /* |phi| < phi_I marks interface nodes for the near-contact scan (0.9) */
+  double g[3];            /* body-force vector */
+  int32_t g_mode;         /* 0 none; 1 F = rho g; 2 F = s(z) rhoA g, s = +1 below nz/2, -1 above, 0 at z = 0, nz/2 */
+  int32_t storage;        /* LB_STORAGE_* */
+} lb_params;
+
+/* Optional device allocator (for example PyTorch's caching allocator).  With
+ * a NULL lb_alloc the library uses cudaMalloc/cudaFree.  alloc returns a
+ * device pointer aligned to 256 bytes or NULL; free releases it.  The handle
+ * calls free for every pointer it obtained, at lb_destroy at the latest. */
+typedef struct {
+  void* (*alloc)(void* ctx, size_t bytes);
+  void (*free)(void* ctx, void* ptr);
+  void* ctx;
+} lb_alloc;
+
+/* Create a handle on the current CUDA device.  Validates grid and params on
+ * the host (LB_EINVAL, nothing allocated), then allocates two population
+ * lattices in the chosen storage, a phase-field array and the initial-field
+ * arrays.  *out receives the handle (caller-owned; release with lb_destroy). */
+int lb_create(const lb_grid* grid, const lb_params* params, const lb_alloc* alloc, lb_handle** out);
+
+/* Release all device memory of the handle (after synchronising its stream). */
+int lb_destroy(lb_handle* h);
+
+/* Issue all further work of h on the given cudaStream_t (NULL: legacy stream).
+ * Drops any captured step graph. */
+int lb_set_stream(lb_handle* h, void* stream);
+
+/* Droplet initial state: phi = +1 within distance R_j of centre j (periodic
+ * distance on open axes, union over droplets), -1 elsewhere; with width > 0,
+ * phi = max_j tanh((R_j - d_j)/width).  rho = 1, u = 0, populations at the
+ * component equilibria f^k_i = f^eq_i(rho_k, u) (Eq. disteq).  centres (3n
+ * doubles, x,y,z) and radii (n doubles) are host arrays; 0 <= n <= 1<<20.
+ * Resets the step counter to 0.  Asynchronous on the handle's stream. */
+int lb_init_droplets(lb_handle* h, int32_t n, const double* centres, const double* radii, double width);
+
+/* Initial state from fields: phi[N], rho[N] (NULL: 1), u[3][N] (NULL: 0).
+ * regularised = 0: component equilibria; 1: regularised reconstruction
+ * f_i = f^eq_i + w_i/(2 c_s^4) Q_i : Pi^neq with Pi^neq = -rho c_s^2 tau_bar
+ * (grad u + grad u^T) (Sec. IV.C, Eqs. distnoneq, eq:llb-pull), colour split
+ * f^A = (rhoA/rho) f.  is_device selects device or host pointers (float).
+ * Resets the step counter to 0. */
+int lb_init_fields(lb_handle* h, const float* phi, const float* rho, const float* u, int regularised,
+                   int is_device);
+
+/* Advance nsteps >= 0 time steps, asynchronously on the handle's stream
+ * (each step: phase-field pass, then the fused collide-recolour-force-stream
+ * pass).  Runs of steps are replayed from a captured CUDA graph. */
+int lb_step(lb_handle* h, int64_t nsteps);
+
+/* Choose the tile shape of the fused step kernel (0..3: 32x8x4, 32x8x8,
+ * 32x4x8, 64x4x4 nodes per CTA); used by the autotuner.  Results do not
+ * depend on the tile.  lb_get_tile returns the current index. */
+int lb_set_tile(lb_handle* h, int tile);
+int lb_get_tile(const lb_handle* h);
+
+/* Advance nsteps >= 1 steps without graph replay, recording CUDA events on
+ * the handle's stream around every kernel.  Synchronises the stream; ms[0]
+ * receives the mean duration of the phase-field pass and ms[1] that of the
+ * fused step kernel, in milliseconds (host array of 2 doubles). */
+int lb_step_timed(lb_handle* h, int64_t nsteps, double* ms);
+
+/* Steps taken since the last initialisation. */
+int64_t lb_time(const lb_handle* h);
+
+/* Write the selected fields at the current time level, [k][nz][ny][nx] float
+ * in increasing bit order of mask, to dst (device or host pointer of
+ * popcount(mask)*N floats, caller-owned).  Synchronises the stream when dst is
+ * on the host.  Solid nodes hold 0. */
+int lb_fields(lb_handle* h, uint32_t mask, float* dst, int dst_is_device);
+/* Same in double precision (fields of an FP64 handle keep full precision). */
+int lb_fields_f64(lb_handle* h, uint32_t mask, double* dst, int dst_is_device);
+
+/* Pre-collision populations of both components at the current time level for
+ * the box [x0,x0+bx) x [y0,y0+by) x [z0,z0+bz) (inside the grid), written to
+ * host arrays fA, fB of 27*bx*by*bz doubles, [dir][z][y][x] with the canonical
+ * direction index (cx+1) + 3(cy+1) + 9(cz+1).  Synchronises the stream. */
+int lb_get_populations(lb_handle* h, int32_t x0, int32_t y0, int32_t z0, int32_t bx, int32_t by, int32_t bz,
+                       double* fA, double* fB);
+
+/* FP64 sums over fluid nodes at the current time level (deterministic order):
+ * out[0] mass A, [1] mass B, [2..4] momentum rho u, [5] A volume sum (1+phi)/2,
+ * [6] near-contact active nodes, [7] kinetic energy sum rho |u|^2 / 2.
+ * out is a host array of 8 doubles.  Synchronises the stream. */
+int lb_reduce_f64(lb_handle* h, double* out);
+
+/* Laplace readout in FP64 (extended Young-Laplace relation, pi = 0 for an
+ * isolated droplet): dp = c_s^2 (<rho>_{phi > cut} - <rho>_{phi < -cut}).
+ * Returns LB_ESTATE if either region is empty.  Synchronises the stream. */
+int lb_laplace_f64(lb_handle* h, double cut, double* dp);
+
+/* Number of droplets: connected components of fluid nodes with phi > 0,
+ * 6-connected, periodic on open axes.  Synchronises the stream. */
+int lb_droplet_count(lb_handle* h, int32_t* count);
+
+/* Synchronise the stream and read the device status word: LB_OK or
+ * LB_EUNSTABLE once any step met a non-finite or non-positive density. */
+int lb_check(lb_handle* h);
+
+/* Checkpoint: raw population state, step counter, grid, parameters and a
+ * format version.  lb_load requires a handle of the same grid and storage. */
+int lb_save(lb_handle* h, const char* path);
+int lb_load(lb_handle* h, const char* path);
+
+/* Number of kernels this library has launched in this process (graph replays
+ * count every kernel node). */
+uint64_t lb_launch_count(void);
+
+/* Bytes of device memory the handle holds. */
+size_t lb_device_bytes(const lb_handle* h);
+
+const char* lb_strerror(int code);
+const char* lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBCG_H */

@@ -1,0 +1,90 @@
+// Internal interface between the C-ABI runtime and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lbcg {
+
+// Box geometry; w* = 1 makes layers 0 and n-1 of that axis solid.
+struct Geo {
+  int nx, ny, nz;
+  int wx, wy, wz;
+  long long N;
+};
+
+// Model parameters as seen by the kernels (converted to the compute type in
+// the kernel prologue).
+struct Phys {
+  double tau_a, tau_b;
+  int equal_tau;
+  double A2;  // (A_a + A_b) / 2
+  double beta;
+  double A_h, h_min, h_max;
+  int K;      // floor(h_max): scan length
+  double phi_I;
+  double g[3];
+  int g_mode;
+  int halo;   // phi tile halo: 1 without near-contact, K + 1 with it
+};
+
+// Device pointers of one population lattice.  Two-set storage: f holds
+// f^A [27][N] followed by f^B [27][N].  Reduced storage: f holds f* [27][N]
+// (FP32 or FP16 deviations) and s, vx, vy, vz hold the colour scalars.
+struct StateBuf {
+  void* f;
+  float* s;
+  float* vx;
+  float* vy;
+  float* vz;
+};
+
+// Initial fields (device, float): phi[N], rho[N] or null, u[3][N] or null.
+struct InitBuf {
+  const float* phi;
+  const float* rho;
+  const float* u;
+  int regularised;
+};
+
+enum Loader { LOAD_PULL = 0, LOAD_FIELDS = 1 };
+
+// Tile shapes of the fused step kernel (x, y extent of the thread block and z
+// nodes per thread).
+struct Tile {
+  int tx, ty, tz;
+};
+constexpr int NUM_TILES = 4;
+extern const Tile kTiles[NUM_TILES];
+
+size_t elem_bytes(int storage);
+bool storage_is_twoset(int storage);
+bool storage_is_f64(int storage);
+
+// --- step_kernels.cu -------------------------------------------------------
+// phase-field pass: phi[N] (float, or double for FP64 storage) from pulled populations
+cudaError_t launch_phi(int storage, const Geo& g, const StateBuf& in, void* phi, cudaStream_t st);
+// fused step; tile index into kTiles (only tile 0 for non-hot variants)
+cudaError_t launch_step(int storage, int loader, bool write_state, bool write_fields, int tile, const Geo& g,
+                        const Phys& p, const StateBuf& in, const InitBuf& init, const void* phi, StateBuf out,
+                        void* fields, unsigned* status, cudaStream_t st);
+// export pre-collision populations of a box, canonical order, as double
+cudaError_t launch_export(int storage, int loader, const Geo& g, const Phys& p, const StateBuf& in,
+                          const InitBuf& init, int x0, int y0, int z0, int bx, int by, int bz, double* outA,
+                          double* outB, cudaStream_t st);
+
+// --- aux_kernels.cu ----------------------------------------------------------
+cudaError_t launch_init_droplets(const Geo& g, int n, const double* d_centres, const double* d_radii, double width,
+                                 float* phi0, float* rho0, float* u0, cudaStream_t st);
+cudaError_t launch_phi_from_init(int storage, const Geo& g, const float* phi0, void* phi, cudaStream_t st);
+// deterministic FP64 sums of the fields buffer; partials needs nblocks*8 doubles
+int reduce_blocks(long long N);
+cudaError_t launch_reduce(int storage, const Geo& g, const void* fields, double* partials, double* out8,
+                          cudaStream_t st);
+cudaError_t launch_laplace(int storage, const Geo& g, const void* fields, double cut, double* partials,
+                           double* out4, cudaStream_t st);
+cudaError_t launch_cc(int storage, const Geo& g, const void* fields, int* labels, int* count, unsigned* status,
+                      cudaStream_t st);
+
+}  // namespace lbcg

@@ -1,0 +1,67 @@
+// D3Q27 lattice for the device kernels (Sec. III.B, Fig. lattice_vel).
+//
+// Direction i encodes its velocity as i = (cx+1) + 3(cy+1) + 9(cz+1), so the
+// rest direction is 13 and the opposite of i is 26 - i.  Weights are the
+// D3Q27 set with c_s^2 = 1/3: 8/27 (rest), 2/27 (faces), 1/54 (edges),
+// 1/216 (corners).  Everything is constexpr so that fully unrolled loops fold
+// the tables into immediates.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbcg {
+
+constexpr int Q = 27;
+constexpr int REST = 13;
+
+__host__ __device__ constexpr int cx(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cy(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz(int i) { return i / 9 - 1; }
+__host__ __device__ constexpr int opp(int i) { return 26 - i; }
+__host__ __device__ constexpr int cnorm2(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
+
+template <typename R>
+__host__ __device__ constexpr R wgt(int i) {
+  return cnorm2(i) == 0 ? R(8) / R(27) : cnorm2(i) == 1 ? R(2) / R(27) : cnorm2(i) == 2 ? R(1) / R(54) : R(1) / R(216);
+}
+
+// 1/|c_i| (0 for the rest direction, where cos(theta) is defined as 0).
+template <typename R>
+__host__ __device__ constexpr R inv_norm(int i) {
+  return cnorm2(i) == 0 ? R(0)
+         : cnorm2(i) == 1 ? R(1)
+         : cnorm2(i) == 2 ? R(0.70710678118654752440084436210485)
+                          : R(0.57735026918962576450914878050196);
+}
+
+// Perturbation weights satisfying sum B = 1/3, sum B c = 0, sum B c c = I/3
+// (isotropy constraints of Sec. III.C.1): B_i = w_i (|c_i|^2 - 2/3).
+template <typename R>
+__host__ __device__ constexpr R bweight(int i) {
+  return wgt<R>(i) * (R(cnorm2(i)) - R(2) / R(3));
+}
+
+// Thresholds shared by every precision (readings of the paper):
+//  - GRAD_EPS: below it the perturbation (proportional to |grad phi|) is 0;
+//  - NORMAL_FLOOR: the recolouring normal is grad phi / max(|grad phi|, floor);
+//  - NC_GRAD_MIN: minimum |grad phi| for a near-contact origin or target;
+//  - NC_COS_TOL: normals are antiparallel when their cosine is below -tol.
+constexpr double GRAD_EPS = 1e-12;
+constexpr double NORMAL_FLOOR = 1e-4;
+constexpr double NC_GRAD_MIN = 1e-2;
+constexpr double NC_COS_TOL = 1e-6;
+
+// FP16 deviation storage: stored value = (f - w_i) * F16_SCALE (Sec. IV.B,
+// shift about the rest equilibrium with rho_0 = 1, u_0 = 0).
+constexpr float F16_SCALE = 4096.0f;
+constexpr float F16_INV_SCALE = 1.0f / 4096.0f;
+
+// Field order of the fields buffer ([k][N]).
+enum Field { F_PHI = 0, F_RHO, F_UX, F_UY, F_UZ, F_RHOA, F_RHOB, F_FRX, F_FRY, F_FRZ, F_H, F_GX, F_GY, F_GZ, NFIELDS };
+
+// Marker for phi at solid or out-of-box nodes in the shared-memory tile;
+// physical |phi| stays O(1).
+constexpr float PHI_SOLID = 1e30f;
+
+}  // namespace lbcg

@@ -1,0 +1,750 @@
+// C-ABI runtime of the colour-gradient LB library (declared in include/lbcg.h).
+//
+// A handle owns two population lattices (ping-pong), the phase-field side
+// array, the initial-field arrays and small scratch buffers.  Steps are issued
+// asynchronously on the handle's stream; runs of steps replay a captured CUDA
+// graph of STEPS_PER_GRAPH steps (two kernels per step).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbcg.h"
+#include "internal.h"
+#include "lattice.cuh"
+
+using namespace lbcg;
+
+namespace {
+
+constexpr int STEPS_PER_GRAPH = 16;
+constexpr uint32_t CKPT_MAGIC = 0x4742434cu;  // "LCBG"
+constexpr uint32_t CKPT_VERSION = 1;
+
+std::atomic<uint64_t> g_launches{0};
+thread_local std::string g_last_error;
+
+int set_err(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_err(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return LB_OK;
+  return set_err(LB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LB_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_err(e_, #call);  \
+  } while (0)
+
+template <typename T>
+__global__ void k_convert(long long n, const T* __restrict__ src, float* __restrict__ dst) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+template <typename T>
+__global__ void k_convert_d(long long n, const T* __restrict__ src, double* __restrict__ dst) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+}  // namespace
+
+struct lb_handle {
+  lb_grid grid;
+  lb_params params;
+  Geo g;
+  Phys p;
+  int storage;
+  cudaStream_t stream = nullptr;   // stream all work is issued on
+  cudaStream_t own_stream = nullptr;
+  lb_alloc alloc{};
+  bool have_alloc = false;
+  std::vector<std::pair<void*, size_t>> owned;
+  size_t bytes = 0;
+
+  StateBuf S[2]{};
+  int cur = 0;
+  void* phi = nullptr;      // R[N]
+  float* init_phi = nullptr;
+  float* init_rho = nullptr;
+  float* init_u = nullptr;
+  bool use_rho = false, use_u = false;
+  int regularised = 0;
+  void* fields = nullptr;   // R[NFIELDS][N], lazily allocated
+  double* red = nullptr;    // reduction partials, then 8 result doubles
+  int* labels = nullptr;    // lazily allocated
+  int* count = nullptr;
+  unsigned* status = nullptr;
+  int mode = 0;             // 0: state given by the initial fields, 1: by populations
+  bool initialised = false;
+  int64_t t = 0;
+  int tile = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+void* dev_alloc(lb_handle* h, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (h->have_alloc) {
+    p = h->alloc.alloc(h->alloc.ctx, bytes);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    h->owned.emplace_back(p, bytes);
+    h->bytes += bytes;
+  }
+  return p;
+}
+
+void dev_free(lb_handle* h, void* p) {
+  if (!p) return;
+  for (size_t k = 0; k < h->owned.size(); ++k) {
+    if (h->owned[k].first == p) {
+      h->bytes -= h->owned[k].second;
+      h->owned.erase(h->owned.begin() + (long)k);
+      break;
+    }
+  }
+  if (h->have_alloc) h->alloc.free(h->alloc.ctx, p);
+  else cudaFree(p);
+}
+
+size_t real_bytes(int storage) { return storage_is_f64(storage) ? 8 : 4; }
+
+size_t state_bytes(const lb_handle* h) {
+  const size_t N = (size_t)h->g.N;
+  if (storage_is_twoset(h->storage)) return 2 * (size_t)Q * N * elem_bytes(h->storage);
+  return (size_t)Q * N * elem_bytes(h->storage) + 4 * N * sizeof(float);
+}
+
+bool alloc_state(lb_handle* h, StateBuf& s) {
+  const size_t N = (size_t)h->g.N;
+  if (storage_is_twoset(h->storage)) {
+    s.f = dev_alloc(h, 2 * (size_t)Q * N * elem_bytes(h->storage));
+    return s.f != nullptr;
+  }
+  // one allocation: f* then s, vx, vy, vz (each 256-byte aligned)
+  const size_t fb = ((size_t)Q * N * elem_bytes(h->storage) + 255) & ~(size_t)255;
+  const size_t sb = (N * sizeof(float) + 255) & ~(size_t)255;
+  char* base = (char*)dev_alloc(h, fb + 4 * sb);
+  if (!base) return false;
+  s.f = base;
+  s.s = (float*)(base + fb);
+  s.vx = (float*)(base + fb + sb);
+  s.vy = (float*)(base + fb + 2 * sb);
+  s.vz = (float*)(base + fb + 3 * sb);
+  return true;
+}
+
+InitBuf init_buf(const lb_handle* h) {
+  InitBuf b;
+  b.phi = h->init_phi;
+  b.rho = h->use_rho ? h->init_rho : nullptr;
+  b.u = h->use_u ? h->init_u : nullptr;
+  b.regularised = h->regularised;
+  return b;
+}
+
+void drop_graphs(lb_handle* h) {
+  for (int k = 0; k < 2; ++k) {
+    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    h->graph[k] = nullptr;
+  }
+}
+
+int validate(const lb_grid* gr, const lb_params* p) {
+  if (!gr || !p) return set_err(LB_EINVAL, "null grid or params");
+  if (gr->nx < 1 || gr->ny < 1 || gr->nz < 1) return set_err(LB_EINVAL, "grid extents must be >= 1");
+  if (gr->walls & ~7u) return set_err(LB_EINVAL, "walls uses bits 0..2 only");
+  const int n[3] = {gr->nx, gr->ny, gr->nz};
+  for (int a = 0; a < 3; ++a)
+    if (((gr->walls >> a) & 1u) && n[a] < 3) return set_err(LB_EINVAL, "a walled axis needs at least 3 layers");
+  const long long N = (long long)gr->nx * gr->ny * gr->nz;
+  if (N > 0x7fffffffLL) return set_err(LB_EINVAL, "grid has more than 2^31-1 nodes");
+  auto fin = [](double v) { return std::isfinite(v); };
+  if (!(p->tau_a > 0.5) || !(p->tau_b > 0.5) || !fin(p->tau_a) || !fin(p->tau_b))
+    return set_err(LB_EINVAL, "tau_a and tau_b must be finite and > 0.5");
+  if (!fin(p->A_a) || !fin(p->A_b) || !fin(p->A_h)) return set_err(LB_EINVAL, "A_a, A_b, A_h must be finite");
+  if (!(p->beta >= 0.0 && p->beta <= 1.0)) return set_err(LB_EINVAL, "beta must lie in [0, 1]");
+  if (p->A_h != 0.0) {
+    if (!(p->h_max >= 1.0 && p->h_max < 7.0)) return set_err(LB_EINVAL, "h_max must lie in [1, 7)");
+    if (!(p->h_min > 0.0 && p->h_min <= p->h_max)) return set_err(LB_EINVAL, "h_min must lie in (0, h_max]");
+    if (!(p->phi_I > 0.0 && p->phi_I <= 1.0)) return set_err(LB_EINVAL, "phi_I must lie in (0, 1]");
+  }
+  if (!fin(p->g[0]) || !fin(p->g[1]) || !fin(p->g[2])) return set_err(LB_EINVAL, "g must be finite");
+  if (p->g_mode < 0 || p->g_mode > 2) return set_err(LB_EINVAL, "g_mode must be 0, 1 or 2");
+  if (p->storage < 0 || p->storage > 3) return set_err(LB_EINVAL, "unknown storage format");
+  return LB_OK;
+}
+
+// Issue one step (no graph).
+int issue_step(lb_handle* h) {
+  const int nxt = h->cur ^ 1;
+  if (h->mode == 0) {
+    LB_CUDA(launch_step(h->storage, LOAD_FIELDS, true, false, 0, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
+                        h->S[nxt], nullptr, h->status, h->stream));
+    g_launches += 1;
+  } else {
+    LB_CUDA(launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream));
+    LB_CUDA(launch_step(h->storage, LOAD_PULL, true, false, h->tile, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
+                        h->S[nxt], nullptr, h->status, h->stream));
+    g_launches += 2;
+  }
+  h->cur = nxt;
+  h->mode = 1;
+  h->t += 1;
+  return LB_OK;
+}
+
+int build_graph(lb_handle* h, int parity) {
+  cudaGraph_t graph = nullptr;
+  const int save_cur = h->cur;
+  const int64_t save_t = h->t;
+  const uint64_t save_l = g_launches.load();
+  h->cur = parity;
+  LB_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = LB_OK;
+  for (int k = 0; k < STEPS_PER_GRAPH && rc == LB_OK; ++k) rc = issue_step(h);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  h->cur = save_cur;
+  h->t = save_t;
+  g_launches = save_l;
+  if (rc != LB_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_err(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  return cuda_err(e, "cudaGraphInstantiate");
+}
+
+int ensure_fields(lb_handle* h) {
+  if (!h->fields) {
+    h->fields = dev_alloc(h, (size_t)NFIELDS * h->g.N * real_bytes(h->storage));
+    if (!h->fields) return set_err(LB_ENOMEM, "fields buffer allocation failed");
+  }
+  return LB_OK;
+}
+
+// Fill the fields buffer at the current time level.
+int compute_fields(lb_handle* h) {
+  if (!h->initialised) return set_err(LB_ESTATE, "handle not initialised");
+  int rc = ensure_fields(h);
+  if (rc) return rc;
+  if (h->mode == 0) {
+    LB_CUDA(launch_step(h->storage, LOAD_FIELDS, false, true, 0, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
+                        h->S[h->cur ^ 1], h->fields, h->status, h->stream));
+    g_launches += 1;
+  } else {
+    LB_CUDA(launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream));
+    LB_CUDA(launch_step(h->storage, LOAD_PULL, false, true, 0, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
+                        h->S[h->cur ^ 1], h->fields, h->status, h->stream));
+    g_launches += 2;
+  }
+  return LB_OK;
+}
+
+int popcount32(uint32_t m) {
+  int c = 0;
+  for (; m; m &= m - 1) ++c;
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_strerror(int code) {
+  switch (code) {
+    case LB_OK: return "ok";
+    case LB_EINVAL: return "invalid argument";
+    case LB_ENOMEM: return "out of memory";
+    case LB_ECUDA: return "CUDA error";
+    case LB_EUNSTABLE: return "unstable: non-finite or non-positive density";
+    case LB_ETIMEOUT: return "bounded device wait gave up";
+    case LB_ESTATE: return "invalid state for this call";
+    case LB_EIO: return "file error or incompatible checkpoint";
+  }
+  return "unknown error";
+}
+
+const char* lb_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t lb_launch_count(void) { return g_launches.load(); }
+
+size_t lb_device_bytes(const lb_handle* h) { return h ? h->bytes : 0; }
+
+int64_t lb_time(const lb_handle* h) { return h ? h->t : -1; }
+
+int lb_create(const lb_grid* grid, const lb_params* params, const lb_alloc* alloc, lb_handle** out) {
+  if (!out) return set_err(LB_EINVAL, "out is null");
+  *out = nullptr;
+  int rc = validate(grid, params);
+  if (rc) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return set_err(LB_ECUDA, "no CUDA device");
+  }
+  lb_handle* h = new lb_handle();
+  h->grid = *grid;
+  h->params = *params;
+  h->storage = params->storage;
+  h->g.nx = grid->nx;
+  h->g.ny = grid->ny;
+  h->g.nz = grid->nz;
+  h->g.wx = (grid->walls >> 0) & 1u;
+  h->g.wy = (grid->walls >> 1) & 1u;
+  h->g.wz = (grid->walls >> 2) & 1u;
+  h->g.N = (long long)grid->nx * grid->ny * grid->nz;
+  Phys& p = h->p;
+  p.tau_a = params->tau_a;
+  p.tau_b = params->tau_b;
+  p.equal_tau = params->tau_a == params->tau_b;
+  p.A2 = 0.5 * (params->A_a + params->A_b);
+  p.beta = params->beta;
+  p.A_h = params->A_h;
+  p.h_min = params->h_min;
+  p.h_max = params->h_max;
+  p.K = params->A_h != 0.0 ? (int)std::floor(params->h_max) : 0;
+  p.phi_I = params->phi_I;
+  for (int a = 0; a < 3; ++a) p.g[a] = params->g[a];
+  p.g_mode = params->g_mode;
+  p.halo = params->A_h != 0.0 ? p.K + 1 : 1;
+  if (alloc && alloc->alloc && alloc->free) {
+    h->alloc = *alloc;
+    h->have_alloc = true;
+  }
+  cudaError_t e = cudaStreamCreate(&h->own_stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_err(e, "cudaStreamCreate");
+  }
+  h->stream = h->own_stream;
+  const size_t N = (size_t)h->g.N;
+  bool ok = alloc_state(h, h->S[0]) && alloc_state(h, h->S[1]);
+  ok = ok && (h->phi = dev_alloc(h, N * real_bytes(h->storage))) != nullptr;
+  ok = ok && (h->init_phi = (float*)dev_alloc(h, N * sizeof(float))) != nullptr;
+  ok = ok && (h->red = (double*)dev_alloc(h, ((size_t)reduce_blocks(h->g.N) * 8 + 16) * sizeof(double))) != nullptr;
+  ok = ok && (h->status = (unsigned*)dev_alloc(h, 256)) != nullptr;
+  ok = ok && (h->count = (int*)dev_alloc(h, 256)) != nullptr;
+  if (!ok) {
+    lb_destroy(h);
+    return set_err(LB_ENOMEM, "device allocation failed");
+  }
+  if ((e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream)) != cudaSuccess) {
+    lb_destroy(h);
+    return cuda_err(e, "cudaMemsetAsync");
+  }
+  *out = h;
+  return LB_OK;
+}
+
+int lb_destroy(lb_handle* h) {
+  if (!h) return LB_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  while (!h->owned.empty()) dev_free(h, h->owned.back().first);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+  return LB_OK;
+}
+
+int lb_set_stream(lb_handle* h, void* stream) {
+  if (!h) return set_err(LB_EINVAL, "null handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStream_t next = s ? s : h->own_stream;
+  if (next != h->stream) {
+    // order the switch: the new stream waits for work already on the old one
+    cudaEvent_t ev;
+    LB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaEventRecord(ev, h->stream);
+    cudaStreamWaitEvent(next, ev, 0);
+    cudaEventDestroy(ev);
+    h->stream = next;
+  }
+  drop_graphs(h);
+  return LB_OK;
+}
+
+int lb_init_droplets(lb_handle* h, int32_t n, const double* centres, const double* radii, double width) {
+  if (!h) return set_err(LB_EINVAL, "null handle");
+  if (n < 0 || n > (1 << 20)) return set_err(LB_EINVAL, "droplet count out of range");
+  if (n > 0 && (!centres || !radii)) return set_err(LB_EINVAL, "null droplet arrays");
+  if (!(width >= 0.0) || !std::isfinite(width)) return set_err(LB_EINVAL, "width must be finite and >= 0");
+  for (int d = 0; d < n; ++d)
+    if (!std::isfinite(radii[d]) || !std::isfinite(centres[3 * d]) || !std::isfinite(centres[3 * d + 1]) ||
+        !std::isfinite(centres[3 * d + 2]))
+      return set_err(LB_EINVAL, "non-finite droplet");
+  double* dbuf = nullptr;
+  if (n > 0) {
+    dbuf = (double*)dev_alloc(h, sizeof(double) * 4 * (size_t)n);
+    if (!dbuf) return set_err(LB_ENOMEM, "droplet buffer allocation failed");
+    cudaError_t e = cudaMemcpyAsync(dbuf, centres, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dbuf + 3 * n, radii, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+      dev_free(h, dbuf);
+      return cuda_err(e, "droplet copy");
+    }
+  }
+  cudaError_t e = launch_init_droplets(h->g, n, dbuf, dbuf ? dbuf + 3 * n : nullptr, width, h->init_phi, nullptr,
+                                       nullptr, h->stream);
+  if (e == cudaSuccess) e = launch_phi_from_init(h->storage, h->g, h->init_phi, h->phi, h->stream);
+  g_launches += 2;
+  if (dbuf) {
+    cudaStreamSynchronize(h->stream);
+    dev_free(h, dbuf);
+  }
+  if (e != cudaSuccess) return cuda_err(e, "init droplets");
+  h->use_rho = h->use_u = false;
+  h->regularised = 0;
+  h->mode = 0;
+  h->t = 0;
+  h->initialised = true;
+  return LB_OK;
+}
+
+int lb_init_fields(lb_handle* h, const float* phi, const float* rho, const float* u, int regularised, int is_device) {
+  if (!h) return set_err(LB_EINVAL, "null handle");
+  if (!phi) return set_err(LB_EINVAL, "phi is required");
+  if (regularised && !u) return set_err(LB_EINVAL, "regularised reconstruction needs u");
+  const size_t N = (size_t)h->g.N;
+  const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  LB_CUDA(cudaMemcpyAsync(h->init_phi, phi, N * sizeof(float), kind, h->stream));
+  if (rho) {
+    if (!h->init_rho && !(h->init_rho = (float*)dev_alloc(h, N * sizeof(float))))
+      return set_err(LB_ENOMEM, "rho buffer allocation failed");
+    LB_CUDA(cudaMemcpyAsync(h->init_rho, rho, N * sizeof(float), kind, h->stream));
+  }
+  if (u) {
+    if (!h->init_u && !(h->init_u = (float*)dev_alloc(h, 3 * N * sizeof(float))))
+      return set_err(LB_ENOMEM, "u buffer allocation failed");
+    LB_CUDA(cudaMemcpyAsync(h->init_u, u, 3 * N * sizeof(float), kind, h->stream));
+  }
+  LB_CUDA(launch_phi_from_init(h->storage, h->g, h->init_phi, h->phi, h->stream));
+  g_launches += 1;
+  if (!is_device) LB_CUDA(cudaStreamSynchronize(h->stream));
+  h->use_rho = rho != nullptr;
+  h->use_u = u != nullptr;
+  h->regularised = regularised ? 1 : 0;
+  h->mode = 0;
+  h->t = 0;
+  h->initialised = true;
+  return LB_OK;
+}
+
+int lb_step(lb_handle* h, int64_t nsteps) {
+  if (!h) return set_err(LB_EINVAL, "null handle");
+  if (nsteps < 0) return set_err(LB_EINVAL, "nsteps must be >= 0");
+  if (!h->initialised) return set_err(LB_ESTATE, "handle not initialised");
+  int rc;
+  if (nsteps > 0 && h->mode == 0) {
+    if ((rc = issue_step(h))) return rc;
+    --nsteps;
+  }
+  while (nsteps >= STEPS_PER_GRAPH) {
+    const int par = h->cur;
+    if (!h->graph[par] && (rc = build_graph(h, par))) return rc;
+    LB_CUDA(cudaGraphLaunch(h->graph[par], h->stream));
+    g_launches += 2 * STEPS_PER_GRAPH;
+    h->t += STEPS_PER_GRAPH;  // even number of steps: parity unchanged
+    nsteps -= STEPS_PER_GRAPH;
+  }
+  while (nsteps-- > 0)
+    if ((rc = issue_step(h))) return rc;
+  return LB_OK;
+}
+
+int lb_step_timed(lb_handle* h, int64_t nsteps, double* ms) {
+  if (!h || !ms) return set_err(LB_EINVAL, "null argument");
+  if (nsteps < 1 || nsteps > 100000) return set_err(LB_EINVAL, "nsteps must lie in [1, 100000]");
+  if (!h->initialised) return set_err(LB_ESTATE, "handle not initialised");
+  int rc;
+  if (h->mode == 0 && (rc = issue_step(h))) return rc;
+  std::vector<cudaEvent_t> ev((size_t)(3 * nsteps));
+  for (auto& e : ev) LB_CUDA(cudaEventCreate(&e));
+  cudaError_t err = cudaSuccess;
+  for (int64_t k = 0; k < nsteps && err == cudaSuccess; ++k) {
+    const int nxt = h->cur ^ 1;
+    cudaEventRecord(ev[3 * k], h->stream);
+    err = launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream);
+    cudaEventRecord(ev[3 * k + 1], h->stream);
+    if (err == cudaSuccess)
+      err = launch_step(h->storage, LOAD_PULL, true, false, h->tile, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
+                        h->S[nxt], nullptr, h->status, h->stream);
+    cudaEventRecord(ev[3 * k + 2], h->stream);
+    g_launches += 2;
+    h->cur = nxt;
+    h->t += 1;
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  double s0 = 0, s1 = 0;
+  for (int64_t k = 0; k < nsteps && err == cudaSuccess; ++k) {
+    float a = 0, b = 0;
+    err = cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]);
+    s0 += a;
+    s1 += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (err != cudaSuccess) return cuda_err(err, "lb_step_timed");
+  ms[0] = s0 / (double)nsteps;
+  ms[1] = s1 / (double)nsteps;
+  return LB_OK;
+}
+
+int lb_set_tile(lb_handle* h, int tile) {
+  if (!h) return set_err(LB_EINVAL, "null handle");
+  if (tile < 0 || tile >= NUM_TILES) return set_err(LB_EINVAL, "tile index out of range");
+  if (tile != h->tile) drop_graphs(h);
+  h->tile = tile;
+  return LB_OK;
+}
+
+int lb_get_tile(const lb_handle* h) { return h ? h->tile : -1; }
+
+static int fields_out(lb_handle* h, uint32_t mask, void* dst, int dst_is_device, bool dbl) {
+  if (!h) return set_err(LB_EINVAL, "null handle");
+  if (!dst) return set_err(LB_EINVAL, "dst is null");
+  if (mask == 0 || (mask >> NFIELDS)) return set_err(LB_EINVAL, "field mask must select fields 0..13");
+  int rc = compute_fields(h);
+  if (rc) return rc;
+  const size_t N = (size_t)h->g.N;
+  const bool f64 = storage_is_f64(h->storage);
+  const size_t ob = dbl ? sizeof(double) : sizeof(float);
+  void* tmp = nullptr;
+  if (f64 != dbl) {  // need a converted copy
+    tmp = dev_alloc(h, N * ob);
+    if (!tmp) return set_err(LB_ENOMEM, "conversion buffer allocation failed");
+  }
+  int slot = 0;
+  for (int k = 0; k < NFIELDS; ++k) {
+    if (!((mask >> k) & 1u)) continue;
+    const char* src = (const char*)h->fields + (size_t)k * N * real_bytes(h->storage);
+    char* d = (char*)dst + (size_t)slot * N * ob;
+    const void* from = src;
+    if (tmp) {
+      const int blocks = (int)std::min<long long>((N + 255) / 256, 4096);
+      if (dbl) k_convert_d<float><<<blocks, 256, 0, h->stream>>>((long long)N, (const float*)src, (double*)tmp);
+      else k_convert<double><<<blocks, 256, 0, h->stream>>>((long long)N, (const double*)src, (float*)tmp);
+      g_launches += 1;
+      from = tmp;
+    }
+    cudaError_t e = cudaMemcpyAsync(d, from, N * ob, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e != cudaSuccess) {
+      if (tmp) dev_free(h, tmp);
+      return cuda_err(e, "fields copy");
+    }
+    ++slot;
+  }
+  if (!dst_is_device || tmp) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (tmp) dev_free(h, tmp);
+    if (e != cudaSuccess) return cuda_err(e, "fields sync");
+  }
+  return LB_OK;
+}
+
+int lb_fields(lb_handle* h, uint32_t mask, float* dst, int dst_is_device) {
+  return fields_out(h, mask, dst, dst_is_device, false);
+}
+
+int lb_fields_f64(lb_handle* h, uint32_t mask, double* dst, int dst_is_device) {
+  return fields_out(h, mask, dst, dst_is_device, true);
+}
+
+int lb_get_populations(lb_handle* h, int32_t x0, int32_t y0, int32_t z0, int32_t bx, int32_t by, int32_t bz,
+                       double* fA, double* fB) {
+  if (!h) return set_err(LB_EINVAL, "null handle");
+  if (!h->initialised) return set_err(LB_ESTATE, "handle not initialised");
+  if (!fA || !fB) return set_err(LB_EINVAL, "null output");
+  if (bx < 1 || by < 1 || bz < 1 || x0 < 0 || y0 < 0 || z0 < 0 || x0 + bx > h->g.nx || y0 + by > h->g.ny ||
+      z0 + bz > h->g.nz)
+    return set_err(LB_EINVAL, "box outside the grid");
+  const size_t M = (size_t)bx * by * bz;
+  double* d = (double*)dev_alloc(h, 2 * (size_t)Q * M * sizeof(double));
+  if (!d) return set_err(LB_ENOMEM, "export buffer allocation failed");
+  cudaError_t e = cudaSuccess;
+  if (h->mode == 1) e = launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream);
+  if (e == cudaSuccess)
+    e = launch_export(h->storage, h->mode == 0 ? LOAD_FIELDS : LOAD_PULL, h->g, h->p, h->S[h->cur], init_buf(h), x0,
+                      y0, z0, bx, by, bz, d, d + (size_t)Q * M, h->stream);
+  g_launches += 2;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(fA, d, (size_t)Q * M * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(fB, d + (size_t)Q * M, (size_t)Q * M * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, d);
+  return cuda_err(e, "get populations");
+}
+
+int lb_reduce_f64(lb_handle* h, double* out) {
+  if (!h || !out) return set_err(LB_EINVAL, "null argument");
+  int rc = compute_fields(h);
+  if (rc) return rc;
+  const int nb = reduce_blocks(h->g.N);
+  double* res = h->red + (size_t)nb * 8;
+  LB_CUDA(launch_reduce(h->storage, h->g, h->fields, h->red, res, h->stream));
+  g_launches += 2;
+  LB_CUDA(cudaMemcpyAsync(out, res, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(cudaStreamSynchronize(h->stream));
+  return LB_OK;
+}
+
+int lb_laplace_f64(lb_handle* h, double cut, double* dp) {
+  if (!h || !dp) return set_err(LB_EINVAL, "null argument");
+  if (!(cut >= 0.0 && cut < 1.0)) return set_err(LB_EINVAL, "cut must lie in [0, 1)");
+  int rc = compute_fields(h);
+  if (rc) return rc;
+  const int nb = reduce_blocks(h->g.N);
+  double* res = h->red + (size_t)nb * 8;
+  LB_CUDA(launch_laplace(h->storage, h->g, h->fields, cut, h->red, res, h->stream));
+  g_launches += 2;
+  double r[4];
+  LB_CUDA(cudaMemcpyAsync(r, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(cudaStreamSynchronize(h->stream));
+  if (r[1] == 0.0 || r[3] == 0.0) return set_err(LB_ESTATE, "inside or outside region is empty");
+  *dp = (r[0] / r[1] - r[2] / r[3]) / 3.0;
+  return LB_OK;
+}
+
+int lb_droplet_count(lb_handle* h, int32_t* count) {
+  if (!h || !count) return set_err(LB_EINVAL, "null argument");
+  int rc = compute_fields(h);
+  if (rc) return rc;
+  if (!h->labels && !(h->labels = (int*)dev_alloc(h, (size_t)h->g.N * sizeof(int))))
+    return set_err(LB_ENOMEM, "label buffer allocation failed");
+  LB_CUDA(launch_cc(h->storage, h->g, h->fields, h->labels, h->count, h->status, h->stream));
+  g_launches += 3;
+  int c = 0;
+  unsigned st = 0;
+  LB_CUDA(cudaMemcpyAsync(&c, h->count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(cudaStreamSynchronize(h->stream));
+  if (st & 2u) return set_err(LB_ETIMEOUT, "union-find gave up after its iteration limit");
+  *count = c;
+  return LB_OK;
+}
+
+int lb_check(lb_handle* h) {
+  if (!h) return set_err(LB_EINVAL, "null handle");
+  unsigned st = 0;
+  LB_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(cudaStreamSynchronize(h->stream));
+  if (st & 1u) return set_err(LB_EUNSTABLE, "non-finite or non-positive density met");
+  if (st & 2u) return set_err(LB_ETIMEOUT, "a bounded device loop gave up");
+  return LB_OK;
+}
+
+int lb_save(lb_handle* h, const char* path) {
+  if (!h || !path) return set_err(LB_EINVAL, "null argument");
+  if (!h->initialised) return set_err(LB_ESTATE, "handle not initialised");
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return set_err(LB_EIO, std::string("cannot open ") + path);
+  const size_t N = (size_t)h->g.N;
+  const size_t sb = state_bytes(h);
+  std::vector<char> buf(h->mode == 1 ? sb : N * sizeof(float) * 5);
+  cudaError_t e = cudaSuccess;
+  int32_t hdr[4] = {(int32_t)CKPT_MAGIC, (int32_t)CKPT_VERSION, h->mode, h->regularised};
+  bool ok = std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 && std::fwrite(&h->grid, sizeof(lb_grid), 1, fp) == 1 &&
+            std::fwrite(&h->params, sizeof(lb_params), 1, fp) == 1 && std::fwrite(&h->t, sizeof(int64_t), 1, fp) == 1;
+  if (ok && h->mode == 1) {
+    const StateBuf& s = h->S[h->cur];
+    if (storage_is_twoset(h->storage)) {
+      e = cudaMemcpyAsync(buf.data(), s.f, sb, cudaMemcpyDeviceToHost, h->stream);
+    } else {
+      const size_t fb = (size_t)Q * N * elem_bytes(h->storage);
+      e = cudaMemcpyAsync(buf.data(), s.f, fb, cudaMemcpyDeviceToHost, h->stream);
+      float* arr[4] = {s.s, s.vx, s.vy, s.vz};
+      for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(buf.data() + fb + k * N * sizeof(float), arr[k], N * sizeof(float), cudaMemcpyDeviceToHost,
+                            h->stream);
+    }
+  } else if (ok) {
+    int32_t flags[2] = {h->use_rho, h->use_u};
+    ok = std::fwrite(flags, sizeof(flags), 1, fp) == 1;
+    e = cudaMemcpyAsync(buf.data(), h->init_phi, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && h->use_rho)
+      e = cudaMemcpyAsync(buf.data() + N * 4, h->init_rho, N * 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && h->use_u)
+      e = cudaMemcpyAsync(buf.data() + 2 * N * 4, h->init_u, 3 * N * 4, cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    std::fclose(fp);
+    return cuda_err(e, "checkpoint copy");
+  }
+  ok = ok && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+  ok = (std::fclose(fp) == 0) && ok;
+  return ok ? LB_OK : set_err(LB_EIO, "checkpoint write failed");
+}
+
+int lb_load(lb_handle* h, const char* path) {
+  if (!h || !path) return set_err(LB_EINVAL, "null argument");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return set_err(LB_EIO, std::string("cannot open ") + path);
+  int32_t hdr[4];
+  lb_grid gr;
+  lb_params pr;
+  int64_t t;
+  bool ok = std::fread(hdr, sizeof(hdr), 1, fp) == 1 && std::fread(&gr, sizeof(gr), 1, fp) == 1 &&
+            std::fread(&pr, sizeof(pr), 1, fp) == 1 && std::fread(&t, sizeof(t), 1, fp) == 1;
+  if (!ok || hdr[0] != (int32_t)CKPT_MAGIC || hdr[1] != (int32_t)CKPT_VERSION || gr.nx != h->grid.nx ||
+      gr.ny != h->grid.ny || gr.nz != h->grid.nz || gr.walls != h->grid.walls || pr.storage != h->storage) {
+    std::fclose(fp);
+    return set_err(LB_EIO, "not a checkpoint of this grid and storage");
+  }
+  const size_t N = (size_t)h->g.N;
+  cudaError_t e = cudaSuccess;
+  if (hdr[2] == 1) {
+    const size_t sb = state_bytes(h);
+    std::vector<char> buf(sb);
+    ok = std::fread(buf.data(), 1, sb, fp) == sb;
+    std::fclose(fp);
+    if (!ok) return set_err(LB_EIO, "truncated checkpoint");
+    const StateBuf& s = h->S[h->cur];
+    if (storage_is_twoset(h->storage)) {
+      e = cudaMemcpyAsync(s.f, buf.data(), sb, cudaMemcpyHostToDevice, h->stream);
+    } else {
+      const size_t fb = (size_t)Q * N * elem_bytes(h->storage);
+      e = cudaMemcpyAsync(s.f, buf.data(), fb, cudaMemcpyHostToDevice, h->stream);
+      float* arr[4] = {s.s, s.vx, s.vy, s.vz};
+      for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(arr[k], buf.data() + fb + k * N * sizeof(float), N * sizeof(float), cudaMemcpyHostToDevice,
+                            h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_err(e, "checkpoint upload");
+    h->mode = 1;
+  } else {
+    int32_t flags[2];
+    ok = std::fread(flags, sizeof(flags), 1, fp) == 1;
+    std::vector<char> buf(N * sizeof(float) * 5);
+    ok = ok && std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    std::fclose(fp);
+    if (!ok) return set_err(LB_EIO, "truncated checkpoint");
+    const float* fl = (const float*)buf.data();
+    int rc = lb_init_fields(h, fl, flags[0] ? fl + N : nullptr, flags[1] ? fl + 2 * N : nullptr, hdr[3], 0);
+    if (rc) return rc;
+  }
+  h->t = t;
+  h->initialised = true;
+  return LB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+Tolerances:
+  * FP32 storage and arithmetic: per-field max-abs error <= 1e-5 (the target
+    stated for FP32 after 200 steps) on the single-droplet workload, and on the
+    near-contact workloads over the horizon where pointwise comparison is
+    meaningful (their symmetric films amplify round-off, see the one-step
+    check for later times).
+  * FP64 instantiation: <= 1e-11 per field, identical near-contact masks.
+  * FP16 deviation storage: errors are reported; the bound (5e-3 on phi,
+    1e-3 on rho and u) follows from a relative FP16 rounding of 2^-11 on
+    deviations of O(1e-2) accumulating over 200 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_14551_gb300 import workloads as W
+
+from _helpers import CMP_FIELDS, field_errors, make_gpu, make_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small_oracle_200():
+    wl = W.small_droplet()
+    o = make_oracle(wl)
+    f0 = o.fields()
+    o.step(200)
+    return wl, f0, o.fields(), o.reduce()
+
+
+@pytest.mark.parametrize("storage,tol", [("twoset_f32", 1e-5), ("reduced_f32", 1e-5), ("twoset_f64", 1e-11)])
+def test_small_droplet_200_steps(small_oracle_200, storage, tol):
+    wl, f0, f200, _ = small_oracle_200
+    s = make_gpu(wl, storage=storage)
+    e0 = field_errors(s.fields(f64=True), f0)
+    assert max(e0.values()) <= tol, e0
+    s.step(200)
+    s.check()
+    assert s.t == 200
+    e = field_errors(s.fields(f64=True), f200)
+    print(storage, e)
+    assert max(e.values()) <= tol, e
+
+
+def test_small_droplet_fp16_deviation(small_oracle_200):
+    wl, _, f200, _ = small_oracle_200
+    s = make_gpu(wl, storage="reduced_f16")
+    s.step(200)
+    s.check()
+    e = field_errors(s.fields(), f200)
+    print("reduced_f16 errors per field after 200 steps:", e)
+    assert e["phi"] <= 5e-3 and e["rhoA"] <= 5e-3 and e["rhoB"] <= 5e-3
+    assert e["rho"] <= 1e-3 and max(e["ux"], e["uy"], e["uz"]) <= 1e-3
+
+
+@pytest.mark.parametrize("storage,tol,steps", [("twoset_f32", 1e-5, 8), ("reduced_f32", 1e-5, 8),
+                                               ("twoset_f64", 1e-11, 8)])
+def test_droplet_pair_short_horizon(storage, tol, steps):
+    wl = W.droplet_pair()
+    o = make_oracle(wl)
+    o.step(steps)
+    fo = o.fields()
+    s = make_gpu(wl, storage=storage)
+    s.step(steps)
+    fg = s.fields(f64=True)
+    e = field_errors(fg, fo, CMP_FIELDS + ("Frx", "Fry", "Frz"))
+    print(storage, e, "active", int((fo["h"] > 0).sum()))
+    assert (fo["h"] > 0).sum() > 0
+    np.testing.assert_array_equal(fg["h"], fo["h"])
+    assert max(e.values()) <= tol, e
+
+
+def _channel():
+    p = dict(W.BASE, A_h=0.1, h_min=2.0, h_max=3.0, g=(0.0, 0.0, 1e-4), g_mode=2, tau_a=0.8, tau_b=1.3,
+             A_a=0.012, A_b=0.008)
+    return W.Workload("channel", (21, 18, 33), 0b010, p, 40,
+                      centres=np.array([[10.0, 9.0, 10.0], [10.5, 9.0, 22.5]]), radii=np.array([5.0, 5.2]))
+
+
+@pytest.mark.parametrize("storage,tol", [("twoset_f32", 1e-5), ("reduced_f32", 1e-5), ("twoset_f64", 1e-11)])
+def test_walls_body_force_unequal_tau(storage, tol):
+    """Ragged sizes (not multiples of the tile), halfway bounce-back walls,
+    mirror body force, unequal relaxation times, near-contact tail."""
+    wl = _channel()
+    o = make_oracle(wl)
+    s = make_gpu(wl, storage=storage)
+    for n in (1, 5, 12):
+        o.step(n)
+        s.step(n)
+        e = field_errors(s.fields(f64=True), o.fields(), CMP_FIELDS + ("Frz",))
+        print(storage, o.t, e)
+        assert max(e.values()) <= tol, (o.t, e)
+
+
+@pytest.mark.parametrize("shape,walls", [((1, 1, 1), 0), ((3, 3, 3), 0b111), ((5, 3, 4), 0b010), ((2, 7, 3), 0b001)])
+def test_degenerate_grids(shape, walls):
+    wl = W.Workload("tiny", shape, walls, dict(W.BASE, A_h=0.1, g=(1e-4, 2e-4, -1e-4), g_mode=1), 10,
+                    centres=np.array([[0.5 * shape[0], 0.5 * shape[1], 0.5 * shape[2]]]), radii=np.array([1.2]))
+    o = make_oracle(wl)
+    s = make_gpu(wl, storage="twoset_f64")
+    o.step(10)
+    s.step(10)
+    e = field_errors(s.fields(f64=True), o.fields())
+    assert max(e.values()) <= 1e-12, e
+
+
+def test_tile_shapes_give_identical_results():
+    import paper_2405_14551_gb300.lbcg as L
+    wl = W.droplet_pair(48, 40, 56, R=8.0, sep=20.0)
+    ref = None
+    for tile in range(4):
+        s = make_gpu(wl)
+        L.lb_set_tile(s.h, tile)
+        s.step(37)
+        f = s.fields(("phi", "ux", "h"))
+        if ref is None:
+            ref = f
+        else:
+            for k in f:
+                np.testing.assert_array_equal(f[k], ref[k])
+
+
+def test_reductions_laplace_count(small_oracle_200):
+    wl, _, _, red_o = small_oracle_200
+    s = make_gpu(wl)
+    s.step(200)
+    r = s.reduce()
+    np.testing.assert_allclose(r[0:2], red_o[0:2], rtol=1e-6)
+    assert np.all(np.abs(r[2:5]) < 1e-6)
+    np.testing.assert_allclose(r[5], red_o[5], rtol=1e-6)
+    assert r[6] == 0
+    o = make_oracle(wl)
+    o.step(200)
+    assert abs(s.laplace(0.9) - o.laplace(0.9)) < 1e-7
+    assert s.droplet_count() == 1
+
+
+def test_droplet_count_matches_oracle():
+    rng = np.random.default_rng(7)
+    cen, rad = W.rsa_spheres((48, 40, 36), 0b010, rng, 3.0, 6.0, gap=1.0, max_count=25)
+    # add an overlapping pair and droplets cut by the periodic boundary
+    cen = np.vstack([cen, [[2.0, 20.0, 1.0], [46.5, 20.0, 35.0]]])
+    rad = np.concatenate([rad, [4.0, 4.0]])
+    wl = W.Workload("cc", (48, 40, 36), 0b010, dict(W.BASE), 0, centres=cen, radii=rad)
+    o = make_oracle(wl)
+    s = make_gpu(wl)
+    assert s.droplet_count() == o.droplet_count()
+    s.step(3)
+    o.step(3)
+    assert s.droplet_count() == o.droplet_count()
+
+
+def test_mass_conservation_fp32_long():
+    wl = W.droplet_pair()
+    s = make_gpu(wl)
+    r0 = s.reduce()
+    s.step(400)
+    s.check()
+    r1 = s.reduce()
+    # FP32 storage: round-off drift only
+    assert abs(r1[0] - r0[0]) / r0[0] < 1e-5
+    assert abs(r1[1] - r0[1]) / r0[1] < 1e-5
+    assert s.droplet_count() == 2
+
+
+def test_checkpoint_resume_bitwise(tmp_path):
+    wl = W.droplet_pair(32, 32, 48, R=7.0, sep=17.0)
+    for storage in ("twoset_f32", "reduced_f16"):
+        a = make_gpu(wl, storage=storage)
+        a.step(100)
+        path = str(tmp_path / f"ck_{storage}.bin")
+        a.save(path)
+        a.step(100)
+        b = make_gpu(wl, storage=storage)
+        b.load(path)
+        assert b.t == 100
+        b.step(100)
+        fa, fb = a.fields(), b.fields()
+        for k in fa:
+            np.testing.assert_array_equal(fa[k], fb[k])
+
+
+def test_regularised_reconstruction_matches_oracle():
+    nx, ny, nz = 12, 10, 14
+    rng = np.random.default_rng(3)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi = np.tanh((5.0 - np.sqrt((x - 6) ** 2 + (y - 5) ** 2 + (z - 7) ** 2)) / 1.5)
+    rho = 1.0 + 0.01 * rng.standard_normal(phi.shape)
+    u = 0.01 * np.stack([np.sin(2 * np.pi * z / nz), np.cos(2 * np.pi * x / nx), np.sin(2 * np.pi * y / ny)])
+    wl = W.Workload("rec", (nx, ny, nz), 0b010, dict(W.BASE, tau_a=0.9, tau_b=1.4), 0)
+    o = oracle.OracleSim(oracle.make_params(nx, ny, nz, walls=0b010, tau_a=0.9, tau_b=1.4))
+    phi, rho, u = (a.astype(np.float32) for a in (phi, rho, u))
+    o.reconstruct(phi.astype(np.float64), rho.astype(np.float64), u.astype(np.float64))
+    oa, ob = o.get_populations()
+    for storage, tol in (("twoset_f64", 1e-14), ("twoset_f32", 1e-6)):
+        import paper_2405_14551_gb300.lbcg as L
+        s = L.Sim(nx, ny, nz, walls=0b010, storage=storage, tau_a=0.9, tau_b=1.4)
+        s.init_fields(phi, rho, u, regularised=True)
+        ga, gb = s.populations()
+        assert np.abs(ga.reshape(27, -1) - oa).max() < tol
+        assert np.abs(gb.reshape(27, -1) - ob).max() < tol

@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--storage", default="twoset_f32")
     ap.add_argument("--no-extra", action="store_true", help="skip the other storage formats")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--shape", default=None, help="nx,ny,nz of a smaller emulsion (profiling captures)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--no-tune", action="store_true", help="use tile 0 without autotuning")
     return ap.parse_args()
 
 
@@ -166,6 +169,67 @@ def reference_arm(args, wl_params, phi):
     print(json.dumps(line), flush=True)
 
 
+def end_to_end(args, L, sim, wl, nodes, world, barrier, maxall):
+    """Same metric through the public API with pinned host buffers: upload the
+    initial phi, K steps, download phi, rho and u."""
+    import torch
+    host_phi = torch.from_numpy(wl.phi).pin_memory()
+    host_out = torch.empty((5,) + wl.phi.shape, dtype=torch.float32).pin_memory()
+    mask = L.FIELD_BIT["phi"] | L.FIELD_BIT["rho"] | L.FIELD_BIT["ux"] | L.FIELD_BIT["uy"] | L.FIELD_BIT["uz"]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.lb_init_fields(sim.h, host_phi.numpy())
+    sim.step(args.steps)
+    L.lb_fields(sim.h, mask, host_out.numpy(), False)
+    t1 = time.perf_counter()
+    e2e_s = maxall(t1 - t0)
+    return {"value": round(world * nodes * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": int(host_phi.numel() * 4 // args.steps),
+            "d2h_bytes_per_step": int(host_out.numel() * 4 // args.steps),
+            "region": "lb_init_fields(host phi) + lb_step(K) + lb_fields(phi,rho,u -> host)"}
+
+
+def other_storages(args, L, make, stream, tile, world, nodes, maxall, peak):
+    """The reduced FP32 and FP16-deviation formats on the same workload."""
+    import torch
+    extra = {}
+    for other in ("reduced_f32", "reduced_f16"):
+        if other == args.storage:
+            continue
+        s2 = make(other)
+        L.lb_set_tile(s2.h, tile)
+        s2.step(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s2.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s2.check()
+        m2 = maxall(e0.elapsed_time(e1))
+        v2 = world * nodes * args.steps / (m2 / 1e3) / 1e6
+        pm, sm = L.lb_step_timed(s2.h, 20)
+        b2 = L.BYTES_PER_NODE[L.STORAGE[other]]
+        extra[other] = {"MLUPS": round(v2, 1), "bytes_per_node": b2,
+                        "whole_step_frac": round(b2 * v2 * 1e6 / world / 1e9 / peak, 4),
+                        "fused_kernel_ms": round(sm, 4), "phase_field_ms": round(pm, 4),
+                        "fused_kernel_GBps": round(b2 * nodes / (sm / 1e3) / 1e9, 1)}
+        s2.close()
+        del s2
+        torch.cuda.empty_cache()
+    return extra
+
+
+def cpu_baseline(wl):
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    crop, desc = cpu_sample_phi(wl.phi, 256 * 256 * 64)
+    rate, dt = oracle_rate(crop, wl.params, 4)
+    return {"value": round(rate, 3), "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle", "sample": f"{desc}, 4 FP64 steps after 1 warm-up ({dt:.1f} s)"}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -202,7 +266,8 @@ def main():
 
     L.load_library()
     dev = torch.device("cuda", local)
-    wl = W.dense_emulsion(SHAPE, seed=SEED, device=dev)
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else SHAPE
+    wl = W.dense_emulsion(shape, seed=SEED, device=dev)
     nodes = wl.nodes
     stream = torch.cuda.Stream()
     storage = args.storage
@@ -229,12 +294,12 @@ def main():
     # autotune the tile of the fused kernel: time every tile, keep the fastest
     tile_ms = []
     sim.step(max(3, args.warmup))
-    for tile in range(4):
+    for tile in range(0 if args.no_tune else 4):
         L.lb_set_tile(sim.h, tile)
         sim.step(16)
         _, kms = L.lb_step_timed(sim.h, 6)
         tile_ms.append(kms)
-    best_tile = int(np.argmin(tile_ms))
+    best_tile = int(np.argmin(tile_ms)) if tile_ms else 0
     L.lb_set_tile(sim.h, best_tile)
     sim.step(args.warmup)
     sim.check()
@@ -251,8 +316,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
     launches = L.lb_launch_count() - launches0
-    ms = ev0.elapsed_time(ev1)
-    ms_max = maxall(ms)
+    ms_max = maxall(ev0.elapsed_time(ev1))
     sim.check()
     value = world * nodes * args.steps / (ms_max / 1e3) / 1e6
     clocks = clk.summary()
@@ -264,94 +328,43 @@ def main():
     achieved = bpn * nodes / (step_ms / 1e3) / 1e9
     step_frac = bpn * value * 1e6 / world / 1e9 / peak
 
-    # end to end through the public API with pinned host buffers
-    host_phi = torch.from_numpy(wl.phi).pin_memory()
-    host_out = torch.empty((5,) + wl.phi.shape, dtype=torch.float32).pin_memory()
-    e2e_steps = args.steps
-    mask = L.FIELD_BIT["phi"] | L.FIELD_BIT["rho"] | L.FIELD_BIT["ux"] | L.FIELD_BIT["uy"] | L.FIELD_BIT["uz"]
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    L.lb_init_fields(sim.h, host_phi.numpy())
-    sim.step(e2e_steps)
-    L.lb_fields(sim.h, mask, host_out.numpy(), False)
-    t1 = time.perf_counter()
-    e2e_s = maxall(t1 - t0)
-    e2e = {"value": round(world * nodes * e2e_steps / e2e_s / 1e6, 1), "unit": "MLUPS",
-           "h2d_bytes_per_step": int(host_phi.numel() * 4 // e2e_steps),
-           "d2h_bytes_per_step": int(host_out.numel() * 4 // e2e_steps),
-           "region": "lb_init_fields(host phi) + lb_step(K) + lb_fields(phi,rho,u -> host)"}
+    e2e = None if args.no_e2e else end_to_end(args, L, sim, wl, nodes, world, barrier, maxall)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    extra = {} if args.no_extra else other_storages(args, L, make, stream, best_tile, world, nodes, maxall, peak)
+    cpu = cpu_baseline(wl) if (rank == 0 and world == 1 and not args.no_cpu) else None
 
-    extra = {}
-    if not args.no_extra:
-        sim.close()
-        del sim
-        torch.cuda.empty_cache()
-        for other in ("reduced_f32", "reduced_f16"):
-            if other == storage:
-                continue
-            s2 = make(other)
-            L.lb_set_tile(s2.h, best_tile)
-            s2.step(args.warmup)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            s2.step(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            s2.check()
-            m2 = maxall(e0.elapsed_time(e1))
-            v2 = world * nodes * args.steps / (m2 / 1e3) / 1e6
-            pm, sm = L.lb_step_timed(s2.h, 20)
-            b2 = L.BYTES_PER_NODE[L.STORAGE[other]]
-            extra[other] = {"MLUPS": round(v2, 1), "bytes_per_node": b2,
-                            "step_frac_of_peak": round(b2 * v2 * 1e6 / world / 1e9 / peak, 4),
-                            "fused_kernel_ms": round(sm, 4), "phase_field_ms": round(pm, 4),
-                            "fused_kernel_GBps": round(b2 * nodes / (sm / 1e3) / 1e9, 1)}
-            s2.close()
-            del s2
-            torch.cuda.empty_cache()
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cores = os.cpu_count() or 1
-        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-        crop, desc = cpu_sample_phi(wl.phi, 256 * 256 * 64)
-        rate, dt = oracle_rate(crop, wl.params, 4)
-        cpu = {"value": round(rate, 3), "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
-               "kind": "oracle", "sample": f"{desc}, 4 FP64 steps after 1 warm-up ({dt:.1f} s)"}
-
-    if rank != 0:
-        return
-    line = {
-        "metric": METRIC,
-        "value": round(value, 1),
-        "unit": "MLUPS",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(ms_max / args.steps, 4),
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64" if storage == "twoset_f64" else "f32",
-        "data": "synthetic",
-        "config": {"workload": wl.name, "storage": storage, "walls": "y", "seed": SEED,
-                   "dispersed_fraction": round(wl.info.get("phi_d", 0.0), 4), "droplets": wl.info.get("droplets"),
-                   "A_h": wl.params["A_h"], "h_min": wl.params["h_min"], "tile": best_tile,
-                   "tile_ms": [round(v, 4) for v in tile_ms], "l2": "state 14.5 GB >> L2, no flush",
-                   "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_step (fused)",
-                     "peak_kind": peak_kind, "kernel_ms": round(step_ms, 4), "phase_field_ms": round(phi_ms, 4),
-                     "bytes_per_node": bpn, "whole_step_frac": round(step_frac, 4)},
-        "cpu_baseline": cpu,
-        "e2e": e2e,
-        "gpu_launches": int(launches),
-        "clocks": clocks,
-        "extra": extra,
-    }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": round(value, 1),
+            "unit": "MLUPS",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_max / args.steps, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64" if storage == "twoset_f64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "storage": storage, "walls": "y", "seed": SEED,
+                       "dispersed_fraction": round(wl.info.get("phi_d", 0.0), 4), "droplets": wl.info.get("droplets"),
+                       "A_h": wl.params["A_h"], "h_min": wl.params["h_min"], "tile": best_tile,
+                       "tile_ms": [round(v, 4) for v in tile_ms],
+                       "l2": "state far larger than L2, no flush", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_step (fused)",
+                         "peak_kind": peak_kind, "kernel_ms": round(step_ms, 4), "phase_field_ms": round(phi_ms, 4),
+                         "bytes_per_node": bpn, "whole_step_frac": round(step_frac, 4)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -257,12 +257,6 @@ int compute_fields(lb_handle* h) {
   return LB_OK;
 }
 
-int popcount32(uint32_t m) {
-  int c = 0;
-  for (; m; m &= m - 1) ++c;
-  return c;
-}
-
 }  // namespace
 
 extern "C" {

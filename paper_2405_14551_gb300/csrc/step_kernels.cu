@@ -17,10 +17,34 @@
 //      recolours (Eqs. ome3_1/2) and stores the post-collision state once.
 // Populations are structure-of-arrays [dir][z][y][x]: for a fixed direction
 // consecutive threads read consecutive addresses (coalesced).
+#include <cstdio>
+#include <cstdlib>
+
 #include "internal.h"
 #include "lattice.cuh"
 
 namespace lbcg {
+
+// LBCG_TRACE=1 prints every launch of this file with the kernel's attributes.
+static bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* v = std::getenv("LBCG_TRACE");
+    on = (v && v[0] == '1') ? 1 : 0;
+  }
+  return on == 1;
+}
+
+template <typename K>
+static void trace_kernel(const char* what, K kern, dim3 grid, dim3 block, size_t smem) {
+  if (!trace_on()) return;
+  cudaFuncAttributes a{};
+  cudaError_t e = cudaFuncGetAttributes(&a, kern);
+  std::fprintf(stderr, "[lbcg] %s grid=(%u,%u,%u) block=(%u,%u,%u) smem=%zu attr=%s regs=%d maxthreads=%d local=%zu\n",
+               what, grid.x, grid.y, grid.z, block.x, block.y, block.z, smem, cudaGetErrorString(e), a.numRegs,
+               a.maxThreadsPerBlock, (size_t)a.localSizeBytes);
+  std::fflush(stderr);
+}
 
 const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 4, 8}, {64, 4, 4}};
 
@@ -114,7 +138,7 @@ struct View {
 };
 
 template <int ST>
-__device__ __forceinline__ View<ST> view(const StateBuf& b) {
+__host__ __device__ __forceinline__ View<ST> view(const StateBuf& b) {
   View<ST> v;
   v.f = reinterpret_cast<typename Store<ST>::E*>(b.f);
   v.s = b.s;
@@ -305,20 +329,26 @@ __global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : 2)
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const int tid = threadIdx.y * TX + threadIdx.x;
 
-  // stage phi of the tile + halo; solid and beyond-wall nodes get the marker
-  for (int e = tid; e < SXY * SZ; e += TX * TY) {
-    const int lx = e % SX, ly = (e / SX) % SY, lz = e / SXY;
-    int gx = x0 - H + lx, gy = y0 - H + ly, gz = z0 - H + lz;
-    bool solid = false;
-    if (g.wx) solid |= (gx <= 0 || gx >= g.nx - 1);
-    else gx = ((gx % g.nx) + g.nx) % g.nx;
-    if (g.wy) solid |= (gy <= 0 || gy >= g.ny - 1);
-    else gy = ((gy % g.ny) + g.ny) % g.ny;
-    if (g.wz) solid |= (gz <= 0 || gz >= g.nz - 1);
-    else gz = ((gz % g.nz) + g.nz) % g.nz;
-    R v = R(PHI_SOLID);
-    if (!solid) v = phi[(long long)gx + (long long)g.nx * ((long long)gy + (long long)g.ny * gz)];
-    sp[e] = v;
+  // stage phi of the tile + halo, one (y,z) row per thread row; solid and
+  // beyond-wall nodes get the marker; periodic wrap only outside the box
+  (void)tid;
+  for (int row = threadIdx.y; row < SY * SZ; row += TY) {
+    const int ly = row % SY, lz = row / SY;
+    int gy = y0 - H + ly, gz = z0 - H + lz;
+    bool rsolid = false;
+    if (g.wy) rsolid |= (gy <= 0 || gy >= g.ny - 1);
+    else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
+    if (g.wz) rsolid |= (gz <= 0 || gz >= g.nz - 1);
+    else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
+    const long long rbase = (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
+    R* srow = sp + (size_t)lz * SXY + (size_t)ly * SX;
+    for (int lx = threadIdx.x; lx < SX; lx += TX) {
+      int gx = x0 - H + lx;
+      bool solid = rsolid;
+      if (g.wx) solid |= (gx <= 0 || gx >= g.nx - 1);
+      else if ((unsigned)gx >= (unsigned)g.nx) gx = ((gx % g.nx) + g.nx) % g.nx;
+      srow[lx] = solid ? R(PHI_SOLID) : phi[rbase + gx];
+    }
   }
   __syncthreads();
 
@@ -545,6 +575,7 @@ static cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cud
   const long long blocks_needed = (g.N + 255) / 256;
   const long long cap = (long long)sm_count() * 8;
   const int blocks = (int)(blocks_needed < cap ? blocks_needed : cap);
+  trace_kernel("k_phi", k_phi<ST>, dim3(blocks), dim3(256), 0);
   k_phi<ST><<<blocks, 256, 0, st>>>(view<ST>(in), g, reinterpret_cast<R*>(phi));
   return cudaGetLastError();
 }
@@ -572,6 +603,7 @@ static cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in
   }
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
   dim3 block(TX, TY, 1);
+  trace_kernel("k_step", kern, grid, block, smem);
   kern<<<grid, block, smem, st>>>(view<ST>(in), view<ST>(out), init, reinterpret_cast<const R*>(phi), g, p,
                                   reinterpret_cast<R*>(fields), status);
   return cudaGetLastError();

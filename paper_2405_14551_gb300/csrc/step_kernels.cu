@@ -1,584 +1,19 @@
-// Fused time step of the two-component colour-gradient LB scheme on D3Q27
-// (arXiv 2405.14551, Sec. III.B-III.D) for sm_103a.
-//
-// A step is two passes over the population lattice:
-//   1. k_phi: pull the populations of every node and write its phase field
-//      phi = (rhoA - rhoB)/(rhoA + rhoB) (Eq. order_param) to a side array.
-//      The colour gradient and the near-contact scan of a node need phi of
-//      the current time level up to h_max + 1 nodes away, which exists only
-//      after every neighbour has been pulled; this pass provides it.
-//   2. k_step: per CTA a tile of (TX x TY x TZ) nodes stages phi of the tile
-//      plus a halo in shared memory; every thread then pulls the 27 (x2)
-//      populations of its node (periodic wrap, halfway bounce-back at solid
-//      neighbours, Sec. III.D), takes the moments, the colour gradient from
-//      the tile, runs the near-contact scan along the outward normal in the
-//      tile, forms the Guo-shifted velocity, relaxes the total populations
-//      (BGK), adds the perturbation Omega^(2) and the forcing source,
-//      recolours (Eqs. ome3_1/2) and stores the post-collision state once.
-// Populations are structure-of-arrays [dir][z][y][x]: for a fixed direction
-// consecutive threads read consecutive addresses (coalesced).
-#include <cstdio>
-#include <cstdlib>
-
+// Storage-format dispatch of the step launchers.
 #include "internal.h"
-#include "lattice.cuh"
 
 namespace lbcg {
 
-// LBCG_TRACE=1 prints every launch of this file with the kernel's attributes.
-static bool trace_on() {
-  static int on = -1;
-  if (on < 0) {
-    const char* v = std::getenv("LBCG_TRACE");
-    on = (v && v[0] == '1') ? 1 : 0;
-  }
-  return on == 1;
-}
-
-template <typename K>
-static void trace_kernel(const char* what, K kern, dim3 grid, dim3 block, size_t smem) {
-  if (!trace_on()) return;
-  cudaFuncAttributes a{};
-  cudaError_t e = cudaFuncGetAttributes(&a, kern);
-  std::fprintf(stderr, "[lbcg] %s grid=(%u,%u,%u) block=(%u,%u,%u) smem=%zu attr=%s regs=%d maxthreads=%d local=%zu\n",
-               what, grid.x, grid.y, grid.z, block.x, block.y, block.z, smem, cudaGetErrorString(e), a.numRegs,
-               a.maxThreadsPerBlock, (size_t)a.localSizeBytes);
-  std::fflush(stderr);
-}
-
 const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 4, 8}, {64, 4, 4}};
 
-// ---------------------------------------------------------------------------
-// storage traits
-// ---------------------------------------------------------------------------
 template <int ST>
-struct Store;
-template <>
-struct Store<0> {  // LB_STORAGE_TWOSET_F32
-  using R = float;
-  using E = float;
-  static constexpr bool TWOSET = true;
-};
-template <>
-struct Store<1> {  // LB_STORAGE_REDUCED_F32
-  using R = float;
-  using E = float;
-  static constexpr bool TWOSET = false;
-};
-template <>
-struct Store<2> {  // LB_STORAGE_REDUCED_F16
-  using R = float;
-  using E = __half;
-  static constexpr bool TWOSET = false;
-};
-template <>
-struct Store<3> {  // LB_STORAGE_TWOSET_F64
-  using R = double;
-  using E = double;
-  static constexpr bool TWOSET = true;
-};
-
+cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st);
 template <int ST>
-__device__ __forceinline__ typename Store<ST>::R decode(typename Store<ST>::E v, int i) {
-  if constexpr (ST == 2) {
-    return wgt<float>(i) + __half2float(v) * F16_INV_SCALE;
-  } else {
-    return v;
-  }
-}
+cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, const Phys& p, const StateBuf& in,
+                          const InitBuf& init, const void* phi, StateBuf out, void* fields, unsigned* status,
+                          cudaStream_t st);
 template <int ST>
-__device__ __forceinline__ typename Store<ST>::E encode(typename Store<ST>::R v, int i) {
-  if constexpr (ST == 2) {
-    return __float2half_rn((v - wgt<float>(i)) * F16_SCALE);
-  } else {
-    return v;
-  }
-}
-
-__device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
-__device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
-__device__ __forceinline__ float round_(float v) { return roundf(v); }  // half away from zero
-__device__ __forceinline__ double round_(double v) { return round(v); }
-__device__ __forceinline__ bool finite_(float v) { return isfinite(v); }
-__device__ __forceinline__ bool finite_(double v) { return isfinite(v); }
-
-// Wrapped neighbour coordinates of a node: c[d+1] = coordinate + d on periodic
-// axes (mod n); raw on wall axes.  solid[d+1] marks a solid layer.
-struct Nbr {
-  int xs[3], ys[3], zs[3];
-  bool sx[3], sy[3], sz[3];
-};
-
-__device__ __forceinline__ void make_nbr(const Geo& g, int x, int y, int z, Nbr& n) {
-#pragma unroll
-  for (int d = -1; d <= 1; ++d) {
-    int a = x + d, b = y + d, c = z + d;
-    if (!g.wx) a = a < 0 ? a + g.nx : (a >= g.nx ? a - g.nx : a);
-    if (!g.wy) b = b < 0 ? b + g.ny : (b >= g.ny ? b - g.ny : b);
-    if (!g.wz) c = c < 0 ? c + g.nz : (c >= g.nz ? c - g.nz : c);
-    n.xs[d + 1] = a;
-    n.ys[d + 1] = b;
-    n.zs[d + 1] = c;
-    n.sx[d + 1] = g.wx && (a <= 0 || a >= g.nx - 1);
-    n.sy[d + 1] = g.wy && (b <= 0 || b >= g.ny - 1);
-    n.sz[d + 1] = g.wz && (c <= 0 || c >= g.nz - 1);
-  }
-}
-
-__device__ __forceinline__ bool is_solid(const Geo& g, int x, int y, int z) {
-  return (g.wx && (x == 0 || x == g.nx - 1)) || (g.wy && (y == 0 || y == g.ny - 1)) ||
-         (g.wz && (z == 0 || z == g.nz - 1));
-}
-
-template <int ST>
-struct View {
-  using E = typename Store<ST>::E;
-  E* f;
-  float *s, *vx, *vy, *vz;
-};
-
-template <int ST>
-__host__ __device__ __forceinline__ View<ST> view(const StateBuf& b) {
-  View<ST> v;
-  v.f = reinterpret_cast<typename Store<ST>::E*>(b.f);
-  v.s = b.s;
-  v.vx = b.vx;
-  v.vy = b.vy;
-  v.vz = b.vz;
-  return v;
-}
-
-// Pull the pre-collision populations of node `self` (streaming, Eq. eq:lbm):
-// f_i(x) = f*_i(x - c_i), or f*_{opp(i)}(x) when x - c_i is solid (halfway
-// bounce-back).  Returns the totals f_i and the component densities.  With
-// per-component output (fa, fb non-null) also the component populations.
-template <int ST, bool COMP>
-__device__ __forceinline__ void pull_node(const View<ST>& S, const Geo& g, const Nbr& n, long long self,
-                                          typename Store<ST>::R f[Q], typename Store<ST>::R& rA,
-                                          typename Store<ST>::R& rB, typename Store<ST>::R* fa,
-                                          typename Store<ST>::R* fb) {
-  using R = typename Store<ST>::R;
-  const size_t N = (size_t)g.N;
-  rA = R(0);
-  rB = R(0);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int a = 1 - cx(i), b = 1 - cy(i), c = 1 - cz(i);
-    const bool bb = n.sx[a] | n.sy[b] | n.sz[c];
-    const long long src = bb ? self : (long long)n.xs[a] + (long long)g.nx * ((long long)n.ys[b] + (long long)g.ny * n.zs[c]);
-    const int dir = bb ? opp(i) : i;
-    if constexpr (Store<ST>::TWOSET) {
-      const R va = decode<ST>(S.f[(size_t)dir * N + src], i);
-      const R vb = decode<ST>(S.f[(size_t)(Q + dir) * N + src], i);
-      f[i] = va + vb;
-      rA += va;
-      rB += vb;
-      if constexpr (COMP) {
-        fa[i] = va;
-        fb[i] = vb;
-      }
-    } else {
-      // single set: f^A_dir(src) = s f*_dir + w c_dir.v/|c_dir| (recolouring, Eq. ome3_1)
-      const R fs = decode<ST>(S.f[(size_t)dir * N + src], i);
-      const R s = S.s[src];
-      const R cv = R(cx(i)) * R(S.vx[src]) + R(cy(i)) * R(S.vy[src]) + R(cz(i)) * R(S.vz[src]);
-      const R seg = (bb ? R(-1) : R(1)) * wgt<R>(i) * inv_norm<R>(i) * cv;
-      const R va = s * fs + seg;
-      const R vb = (R(1) - s) * fs - seg;
-      f[i] = fs;
-      rA += va;
-      rB += vb;
-      if constexpr (COMP) {
-        fa[i] = va;
-        fb[i] = vb;
-      }
-    }
-  }
-}
-
-// Pre-collision populations from fields (initial state or reconstruction):
-// f_i = f^eq_i(rho, u) (Eq. disteq) [+ w_i/(2 cs^4) Q_i:Pi^neq], f^A = (rhoA/rho) f.
-template <typename R, bool COMP>
-__device__ __forceinline__ void fields_node(const InitBuf& I, const Geo& g, const Phys& P, const Nbr& n,
-                                            long long self, R f[Q], R& rA, R& rB, R* fa, R* fb) {
-  const R ph = I.phi[self];
-  const R rho = I.rho ? R(I.rho[self]) : R(1);
-  R u[3] = {R(0), R(0), R(0)};
-  if (I.u) {
-    u[0] = I.u[self];
-    u[1] = I.u[(size_t)g.N + self];
-    u[2] = I.u[2 * (size_t)g.N + self];
-  }
-  rA = rho * (R(1) + ph) * R(0.5);
-  rB = rho * (R(1) - ph) * R(0.5);
-  R Pi[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};  // xx yy zz xy xz yz
-  if (I.regularised && I.u) {
-    // isotropic stencil gradient du[b][a] = d_a u_b; solid neighbour -> own value
-    R du[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (i == REST) continue;
-      const int a = 1 + cx(i), b = 1 + cy(i), c = 1 + cz(i);
-      const bool sol = n.sx[a] | n.sy[b] | n.sz[c];
-      const long long m =
-          sol ? self : (long long)n.xs[a] + (long long)g.nx * ((long long)n.ys[b] + (long long)g.ny * n.zs[c]);
-      const R w3 = R(3) * wgt<R>(i);
-#pragma unroll
-      for (int bcomp = 0; bcomp < 3; ++bcomp) {
-        const R ub = I.u[(size_t)bcomp * g.N + m];
-        du[bcomp][0] += w3 * R(cx(i)) * ub;
-        du[bcomp][1] += w3 * R(cy(i)) * ub;
-        du[bcomp][2] += w3 * R(cz(i)) * ub;
-      }
-    }
-    R tau;
-    if (P.equal_tau) {
-      tau = R(P.tau_a);
-    } else {
-      const R nu_a = (R(P.tau_a) - R(0.5)) / R(3), nu_b = (R(P.tau_b) - R(0.5)) / R(3);
-      const R nu = R(1) / ((rA / rho) / nu_a + (rB / rho) / nu_b);
-      tau = R(3) * nu + R(0.5);
-    }
-    const R pref = -rho * tau / R(3);  // Pi^neq = -rho cs2 tau (grad u + grad u^T)
-    Pi[0] = pref * R(2) * du[0][0];
-    Pi[1] = pref * R(2) * du[1][1];
-    Pi[2] = pref * R(2) * du[2][2];
-    Pi[3] = pref * (du[0][1] + du[1][0]);
-    Pi[4] = pref * (du[0][2] + du[2][0]);
-    Pi[5] = pref * (du[1][2] + du[2][1]);
-  }
-  const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  const R trPi = Pi[0] + Pi[1] + Pi[2];
-  const R sA = rA / rho;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const R cu = R(cx(i)) * u[0] + R(cy(i)) * u[1] + R(cz(i)) * u[2];
-    R fi = wgt<R>(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-    // (c c - cs2 I):Pi with symmetric Pi
-    const R qpi = R(cx(i) * cx(i)) * Pi[0] + R(cy(i) * cy(i)) * Pi[1] + R(cz(i) * cz(i)) * Pi[2] +
-                  R(2 * cx(i) * cy(i)) * Pi[3] + R(2 * cx(i) * cz(i)) * Pi[4] + R(2 * cy(i) * cz(i)) * Pi[5] -
-                  trPi / R(3);
-    fi += wgt<R>(i) * R(4.5) * qpi;
-    f[i] = fi;
-    if constexpr (COMP) {
-      fa[i] = sA * fi;
-      fb[i] = fi - sA * fi;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// pass 1: phase field
-// ---------------------------------------------------------------------------
-template <int ST>
-__global__ void __launch_bounds__(256) k_phi(View<ST> S, Geo g, typename Store<ST>::R* __restrict__ phi) {
-  using R = typename Store<ST>::R;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
-    const int x = (int)(idx % g.nx);
-    const long long yz = idx / g.nx;
-    const int y = (int)(yz % g.ny);
-    const int z = (int)(yz / g.ny);
-    if (is_solid(g, x, y, z)) {
-      phi[idx] = R(0);
-      continue;
-    }
-    Nbr n;
-    make_nbr(g, x, y, z, n);
-    R f[Q], rA, rB;
-    pull_node<ST, false>(S, g, n, idx, f, rA, rB, nullptr, nullptr);
-    phi[idx] = (rA - rB) / (rA + rB);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// pass 2: fused step
-// ---------------------------------------------------------------------------
-// Colour gradient grad phi(p) = (1/cs2) sum_i w_i c_i phi(p + c_i) on the
-// shared tile; a solid neighbour contributes phi(p) (neutral wetting).
-template <typename R>
-__device__ __forceinline__ void tile_grad(const R* sp, int c, int SX, int SXY, R gr[3]) {
-  const R p0 = sp[c];
-  R gx = R(0), gy = R(0), gz = R(0);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (i == REST) continue;
-    R v = sp[c + cx(i) + SX * cy(i) + SXY * cz(i)];
-    v = (v > R(0.5) * R(PHI_SOLID)) ? p0 : v;
-    const R wv = wgt<R>(i) * v;
-    gx += R(cx(i)) * wv;
-    gy += R(cy(i)) * wv;
-    gz += R(cz(i)) * wv;
-  }
-  gr[0] = R(3) * gx;
-  gr[1] = R(3) * gy;
-  gr[2] = R(3) * gz;
-}
-
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : 2)
-    k_step(View<ST> S, View<ST> O, InitBuf init, const typename Store<ST>::R* __restrict__ phi, Geo g, Phys P,
-           typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status) {
-  using R = typename Store<ST>::R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sp = reinterpret_cast<R*>(smem_raw);
-
-  const int H = P.halo;
-  const int SX = TX + 2 * H, SY = TY + 2 * H, SZ = TZ + 2 * H;
-  const int SXY = SX * SY;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-  const int tid = threadIdx.y * TX + threadIdx.x;
-
-  // stage phi of the tile + halo, one (y,z) row per thread row; solid and
-  // beyond-wall nodes get the marker; periodic wrap only outside the box
-  (void)tid;
-  for (int row = threadIdx.y; row < SY * SZ; row += TY) {
-    const int ly = row % SY, lz = row / SY;
-    int gy = y0 - H + ly, gz = z0 - H + lz;
-    bool rsolid = false;
-    if (g.wy) rsolid |= (gy <= 0 || gy >= g.ny - 1);
-    else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
-    if (g.wz) rsolid |= (gz <= 0 || gz >= g.nz - 1);
-    else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
-    const long long rbase = (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
-    R* srow = sp + (size_t)lz * SXY + (size_t)ly * SX;
-    for (int lx = threadIdx.x; lx < SX; lx += TX) {
-      int gx = x0 - H + lx;
-      bool solid = rsolid;
-      if (g.wx) solid |= (gx <= 0 || gx >= g.nx - 1);
-      else if ((unsigned)gx >= (unsigned)g.nx) gx = ((gx % g.nx) + g.nx) % g.nx;
-      srow[lx] = solid ? R(PHI_SOLID) : phi[rbase + gx];
-    }
-  }
-  __syncthreads();
-
-  const R tau_a = R(P.tau_a), tau_b = R(P.tau_b);
-  const R A2 = R(P.A2), beta = R(P.beta), A_h = R(P.A_h), phi_I = R(P.phi_I);
-  const size_t N = (size_t)g.N;
-
-  for (int lz = 0; lz < TZ; ++lz) {
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
-    if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
-    const long long self = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
-    if (is_solid(g, x, y, z)) {
-      if constexpr (WF) {
-        for (int k = 0; k < NFIELDS; ++k) fields[(size_t)k * N + self] = R(0);
-      }
-      continue;
-    }
-    Nbr n;
-    make_nbr(g, x, y, z, n);
-    R f[Q], rA, rB;
-    if constexpr (LOADER == LOAD_PULL) {
-      pull_node<ST, false>(S, g, n, self, f, rA, rB, nullptr, nullptr);
-    } else {
-      fields_node<R, false>(init, g, P, n, self, f, rA, rB, nullptr, nullptr);
-    }
-
-    // moments (Sec. III.C.1): rho = rhoA + rhoB, j = sum_i f_i c_i
-    const R rho = rA + rB;
-    R j[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      j[0] += R(cx(i)) * f[i];
-      j[1] += R(cy(i)) * f[i];
-      j[2] += R(cz(i)) * f[i];
-    }
-
-    // colour gradient from the tile
-    const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + H);
-    const R phx = sp[c];
-    R gr[3];
-    tile_grad(sp, c, SX, SXY, gr);
-    const R gg = rsqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-
-    // near-contact scan (Eqs. stress_jump, near_cont_force): from an interface
-    // node step along n_out = -grad phi/|grad phi| by round(k n_out),
-    // k = 1..K; the first interface node with an antiparallel normal sets h.
-    int h = 0;
-    R Ahh = R(0);
-    if (A_h != R(0) && fabs(phx) < phi_I && gg >= R(NC_GRAD_MIN)) {
-      const R inv = R(-1) / gg;
-      const R no0 = gr[0] * inv, no1 = gr[1] * inv, no2 = gr[2] * inv;
-      for (int k = 1; k <= P.K; ++k) {
-        // |n_out| = 1, so |d| <= k <= K < halo; the clamp also covers non-finite normals
-        const int dx = max(-k, min(k, (int)round_(R(k) * no0)));
-        const int dy = max(-k, min(k, (int)round_(R(k) * no1)));
-        const int dz = max(-k, min(k, (int)round_(R(k) * no2)));
-        if (g.wx && (x + dx <= 0 || x + dx >= g.nx - 1)) break;
-        if (g.wy && (y + dy <= 0 || y + dy >= g.ny - 1)) break;
-        if (g.wz && (z + dz <= 0 || z + dz >= g.nz - 1)) break;
-        const int cy_ = c + dx + SX * dy + SXY * dz;
-        const R phy = sp[cy_];
-        if (!(fabs(phy) < phi_I)) continue;
-        R gy_[3];
-        tile_grad(sp, cy_, SX, SXY, gy_);
-        const R gm = rsqrt_(gy_[0] * gy_[0] + gy_[1] * gy_[1] + gy_[2] * gy_[2]);
-        if (gm < R(NC_GRAD_MIN)) continue;
-        const R dot = gr[0] * gy_[0] + gr[1] * gy_[1] + gr[2] * gy_[2];
-        if (dot < -R(NC_COS_TOL) * gg * gm) {
-          h = k;
-          break;
-        }
-      }
-      if (h > 0) {
-        const R hk = R(h);
-        if (hk <= R(P.h_min)) Ahh = A_h;
-        else if (hk <= R(P.h_max)) {
-          const R q = R(P.h_min) / hk;
-          Ahh = A_h * q * q * q;
-        }
-      }
-    }
-    // F_rep = -A_h n_out delta_I, delta_I = |grad phi|/2  ->  (A_h/2) grad phi
-    const R Fr[3] = {R(0.5) * Ahh * gr[0], R(0.5) * Ahh * gr[1], R(0.5) * Ahh * gr[2]};
-    R F[3] = {Fr[0], Fr[1], Fr[2]};
-    if (P.g_mode == 1) {
-      F[0] += rho * R(P.g[0]);
-      F[1] += rho * R(P.g[1]);
-      F[2] += rho * R(P.g[2]);
-    } else if (P.g_mode == 2) {
-      const R sg = (z == 0 || 2 * z == g.nz) ? R(0) : (2 * z < g.nz ? R(1) : R(-1));
-      F[0] += sg * rA * R(P.g[0]);
-      F[1] += sg * rA * R(P.g[1]);
-      F[2] += sg * rA * R(P.g[2]);
-    }
-
-    // Guo-shifted velocity and mixture relaxation time (Eq. sigmaA's nu_bar)
-    const R irho = R(1) / rho;
-    const R u0 = (j[0] + R(0.5) * F[0]) * irho, u1 = (j[1] + R(0.5) * F[1]) * irho,
-            u2 = (j[2] + R(0.5) * F[2]) * irho;
-    if (!(rho > R(0)) || !finite_(rho)) atomicOr(status, 1u);
-
-    if constexpr (WF) {
-      fields[(size_t)F_PHI * N + self] = phx;
-      fields[(size_t)F_RHO * N + self] = rho;
-      fields[(size_t)F_UX * N + self] = u0;
-      fields[(size_t)F_UY * N + self] = u1;
-      fields[(size_t)F_UZ * N + self] = u2;
-      fields[(size_t)F_RHOA * N + self] = rA;
-      fields[(size_t)F_RHOB * N + self] = rB;
-      fields[(size_t)F_FRX * N + self] = Fr[0];
-      fields[(size_t)F_FRY * N + self] = Fr[1];
-      fields[(size_t)F_FRZ * N + self] = Fr[2];
-      fields[(size_t)F_H * N + self] = R(h);
-      fields[(size_t)F_GX * N + self] = gr[0];
-      fields[(size_t)F_GY * N + self] = gr[1];
-      fields[(size_t)F_GZ * N + self] = gr[2];
-    }
-    if constexpr (!WS) continue;
-
-    R tau;
-    if (P.equal_tau) {
-      tau = tau_a;
-    } else {
-      const R nu_a = (tau_a - R(0.5)) / R(3), nu_b = (tau_b - R(0.5)) / R(3);
-      const R nu = R(1) / ((rA * irho) / nu_a + (rB * irho) / nu_b);
-      tau = R(3) * nu + R(0.5);
-    }
-    const R omega = R(1) / tau;
-    const R guo = R(1) - R(0.5) * omega;
-    const R uu = u0 * u0 + u1 * u1 + u2 * u2;
-    const R uF = u0 * F[0] + u1 * F[1] + u2 * F[2];
-    // perturbation: (A_a+A_b)/2 |g| [w (c.n)^2 - B] = A2 [w (c.grad)^2/|g| - |g| B]
-    const bool pert = gg >= R(GRAD_EPS);
-    const R igg = pert ? R(1) / gg : R(0);
-    const R A2g = pert ? A2 * gg : R(0);
-    const R A2ig = A2 * igg;
-    // recolouring segregation amplitude beta rhoA rhoB / rho with the
-    // normal grad phi / max(|grad phi|, floor)
-    const R gn = gg > R(NORMAL_FLOOR) ? gg : R(NORMAL_FLOOR);
-    const R segamp = beta * rA * rB * irho / gn;
-    const R sA = rA * irho;
-
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const R cu = R(cx(i)) * u0 + R(cy(i)) * u1 + R(cz(i)) * u2;
-      const R feq = wgt<R>(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-      const R cF = R(cx(i)) * F[0] + R(cy(i)) * F[1] + R(cz(i)) * F[2];
-      const R Si = guo * wgt<R>(i) * (R(3) * (cF - uF) + R(9) * cu * cF);
-      const R cg = R(cx(i)) * gr[0] + R(cy(i)) * gr[1] + R(cz(i)) * gr[2];
-      const R om2 = wgt<R>(i) * A2ig * cg * cg - bweight<R>(i) * A2g;
-      const R fs = f[i] + (feq - f[i]) * omega + om2 + Si;
-      if constexpr (Store<ST>::TWOSET) {
-        const R seg = segamp * wgt<R>(i) * inv_norm<R>(i) * cg;
-        const R fa = sA * fs + seg;
-        O.f[(size_t)i * N + self] = encode<ST>(fa, i);
-        O.f[(size_t)(Q + i) * N + self] = encode<ST>(fs - fa, i);
-      } else {
-        O.f[(size_t)i * N + self] = encode<ST>(fs, i);
-      }
-    }
-    if constexpr (!Store<ST>::TWOSET) {
-      O.s[self] = sA;
-      O.vx[self] = segamp * gr[0];
-      O.vy[self] = segamp * gr[1];
-      O.vz[self] = segamp * gr[2];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// population export (pre-collision, both components, canonical order, double)
-// ---------------------------------------------------------------------------
-template <int ST, int LOADER>
-__global__ void __launch_bounds__(128) k_export(View<ST> S, InitBuf init, Geo g, Phys P, int x0, int y0, int z0,
-                                                int bx, int by, int bz, double* outA, double* outB) {
-  using R = typename Store<ST>::R;
-  const long long M = (long long)bx * by * bz;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < M;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int lx = (int)(e % bx);
-    const int ly = (int)((e / bx) % by);
-    const int lz = (int)(e / ((long long)bx * by));
-    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-    const long long self = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
-    if (is_solid(g, x, y, z)) {
-      for (int i = 0; i < Q; ++i) {
-        outA[(size_t)i * M + e] = 0.0;
-        outB[(size_t)i * M + e] = 0.0;
-      }
-      continue;
-    }
-    Nbr n;
-    make_nbr(g, x, y, z, n);
-    R f[Q], fa[Q], fb[Q], rA, rB;
-    if constexpr (LOADER == LOAD_PULL) {
-      pull_node<ST, true>(S, g, n, self, f, rA, rB, fa, fb);
-    } else {
-      fields_node<R, true>(init, g, P, n, self, f, rA, rB, fa, fb);
-    }
-    for (int i = 0; i < Q; ++i) {
-      outA[(size_t)i * M + e] = (double)fa[i];
-      outB[(size_t)i * M + e] = (double)fb[i];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// launchers
-// ---------------------------------------------------------------------------
-static int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
-
-template <int ST>
-static cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st) {
-  using R = typename Store<ST>::R;
-  const long long blocks_needed = (g.N + 255) / 256;
-  const long long cap = (long long)sm_count() * 8;
-  const int blocks = (int)(blocks_needed < cap ? blocks_needed : cap);
-  trace_kernel("k_phi", k_phi<ST>, dim3(blocks), dim3(256), 0);
-  k_phi<ST><<<blocks, 256, 0, st>>>(view<ST>(in), g, reinterpret_cast<R*>(phi));
-  return cudaGetLastError();
-}
+cudaError_t launch_export_t(int loader, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init, int x0,
+                            int y0, int z0, int bx, int by, int bz, double* outA, double* outB, cudaStream_t st);
 
 cudaError_t launch_phi(int storage, const Geo& g, const StateBuf& in, void* phi, cudaStream_t st) {
   switch (storage) {
@@ -586,55 +21,6 @@ cudaError_t launch_phi(int storage, const Geo& g, const StateBuf& in, void* phi,
     case 1: return launch_phi_t<1>(g, in, phi, st);
     case 2: return launch_phi_t<2>(g, in, phi, st);
     case 3: return launch_phi_t<3>(g, in, phi, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ>
-static cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
-                                 const void* phi, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
-  using R = typename Store<ST>::R;
-  const int H = p.halo;
-  const size_t smem = sizeof(R) * (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
-  auto kern = k_step<ST, LOADER, WS, WF, TX, TY, TZ>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
-  dim3 block(TX, TY, 1);
-  trace_kernel("k_step", kern, grid, block, smem);
-  kern<<<grid, block, smem, st>>>(view<ST>(in), view<ST>(out), init, reinterpret_cast<const R*>(phi), g, p,
-                                  reinterpret_cast<R*>(fields), status);
-  return cudaGetLastError();
-}
-
-template <int ST, int LOADER, bool WS, bool WF>
-static cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
-                                     const void* phi, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
-  if constexpr (LOADER == LOAD_PULL && WS && !WF) {
-    switch (tile) {
-      case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8>(g, p, in, init, phi, out, fields, status, st);
-      case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 4, 8>(g, p, in, init, phi, out, fields, status, st);
-      case 3: return launch_step_t<ST, LOADER, WS, WF, 64, 4, 4>(g, p, in, init, phi, out, fields, status, st);
-      default: break;
-    }
-  }
-  return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4>(g, p, in, init, phi, out, fields, status, st);
-}
-
-template <int ST>
-static cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, const Phys& p,
-                                 const StateBuf& in, const InitBuf& init, const void* phi, StateBuf out, void* fields,
-                                 unsigned* status, cudaStream_t st) {
-  if (loader == LOAD_PULL) {
-    if (ws && !wf) return launch_step_tiles<ST, LOAD_PULL, true, false>(tile, g, p, in, init, phi, out, fields, status, st);
-    if (ws && wf) return launch_step_tiles<ST, LOAD_PULL, true, true>(0, g, p, in, init, phi, out, fields, status, st);
-    if (!ws && wf) return launch_step_tiles<ST, LOAD_PULL, false, true>(0, g, p, in, init, phi, out, fields, status, st);
-  } else {
-    if (ws && !wf) return launch_step_tiles<ST, LOAD_FIELDS, true, false>(0, g, p, in, init, phi, out, fields, status, st);
-    if (ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, true, true>(0, g, p, in, init, phi, out, fields, status, st);
-    if (!ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, false, true>(0, g, p, in, init, phi, out, fields, status, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -649,20 +35,6 @@ cudaError_t launch_step(int storage, int loader, bool write_state, bool write_fi
     case 3: return launch_step_s<3>(loader, write_state, write_fields, tile, g, p, in, init, phi, out, fields, status, st);
   }
   return cudaErrorInvalidValue;
-}
-
-template <int ST>
-static cudaError_t launch_export_t(int loader, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
-                                   int x0, int y0, int z0, int bx, int by, int bz, double* outA, double* outB,
-                                   cudaStream_t st) {
-  const long long M = (long long)bx * by * bz;
-  const long long need = (M + 127) / 128;
-  const int blocks = (int)(need < 4096 ? need : 4096);
-  if (loader == LOAD_PULL)
-    k_export<ST, LOAD_PULL><<<blocks, 128, 0, st>>>(view<ST>(in), init, g, p, x0, y0, z0, bx, by, bz, outA, outB);
-  else
-    k_export<ST, LOAD_FIELDS><<<blocks, 128, 0, st>>>(view<ST>(in), init, g, p, x0, y0, z0, bx, by, bz, outA, outB);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_export(int storage, int loader, const Geo& g, const Phys& p, const StateBuf& in,

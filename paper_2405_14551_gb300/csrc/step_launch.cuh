@@ -1,0 +1,94 @@
+// Launchers of the step kernels, instantiated once per storage format.
+#pragma once
+#include "step_impl.cuh"
+
+namespace lbcg {
+
+inline int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int ST>
+cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st) {
+  using R = typename Store<ST>::R;
+  const long long blocks_needed = (g.N + 255) / 256;
+  const long long cap = (long long)sm_count() * 8;
+  const int blocks = (int)(blocks_needed < cap ? blocks_needed : cap);
+  trace_kernel("k_phi", k_phi<ST>, dim3(blocks), dim3(256), 0);
+  k_phi<ST><<<blocks, 256, 0, st>>>(view<ST>(in), g, reinterpret_cast<R*>(phi));
+  return cudaGetLastError();
+}
+
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ>
+inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
+                                 const void* phi, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
+  using R = typename Store<ST>::R;
+  const int H = p.halo;
+  const size_t smem = sizeof(R) * (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
+  // 32-bit population offsets when every offset of the lattice fits
+  const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
+  auto kern = idx32 ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, true> : k_step<ST, LOADER, WS, WF, TX, TY, TZ, false>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
+  dim3 block(TX, TY, 1);
+  trace_kernel("k_step", kern, grid, block, smem);
+  kern<<<grid, block, smem, st>>>(view<ST>(in), view<ST>(out), init, reinterpret_cast<const R*>(phi), g, p,
+                                  reinterpret_cast<R*>(fields), status);
+  return cudaGetLastError();
+}
+
+template <int ST, int LOADER, bool WS, bool WF>
+inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
+                                     const void* phi, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
+  if constexpr (LOADER == LOAD_PULL && WS && !WF) {
+    switch (tile) {
+      case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8>(g, p, in, init, phi, out, fields, status, st);
+      case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 4, 8>(g, p, in, init, phi, out, fields, status, st);
+      case 3: return launch_step_t<ST, LOADER, WS, WF, 64, 4, 4>(g, p, in, init, phi, out, fields, status, st);
+      default: break;
+    }
+  }
+  return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4>(g, p, in, init, phi, out, fields, status, st);
+}
+
+template <int ST>
+cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, const Phys& p,
+                                 const StateBuf& in, const InitBuf& init, const void* phi, StateBuf out, void* fields,
+                                 unsigned* status, cudaStream_t st) {
+  if (loader == LOAD_PULL) {
+    if (ws && !wf) return launch_step_tiles<ST, LOAD_PULL, true, false>(tile, g, p, in, init, phi, out, fields, status, st);
+    if (ws && wf) return launch_step_tiles<ST, LOAD_PULL, true, true>(0, g, p, in, init, phi, out, fields, status, st);
+    if (!ws && wf) return launch_step_tiles<ST, LOAD_PULL, false, true>(0, g, p, in, init, phi, out, fields, status, st);
+  } else {
+    if (ws && !wf) return launch_step_tiles<ST, LOAD_FIELDS, true, false>(0, g, p, in, init, phi, out, fields, status, st);
+    if (ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, true, true>(0, g, p, in, init, phi, out, fields, status, st);
+    if (!ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, false, true>(0, g, p, in, init, phi, out, fields, status, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int ST>
+cudaError_t launch_export_t(int loader, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
+                                   int x0, int y0, int z0, int bx, int by, int bz, double* outA, double* outB,
+                                   cudaStream_t st) {
+  const long long M = (long long)bx * by * bz;
+  const long long need = (M + 127) / 128;
+  const int blocks = (int)(need < 4096 ? need : 4096);
+  if (loader == LOAD_PULL)
+    k_export<ST, LOAD_PULL><<<blocks, 128, 0, st>>>(view<ST>(in), init, g, p, x0, y0, z0, bx, by, bz, outA, outB);
+  else
+    k_export<ST, LOAD_FIELDS><<<blocks, 128, 0, st>>>(view<ST>(in), init, g, p, x0, y0, z0, bx, by, bz, outA, outB);
+  return cudaGetLastError();
+}
+
+}  // namespace lbcg

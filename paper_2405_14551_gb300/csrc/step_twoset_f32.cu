@@ -1,0 +1,12 @@
+// Step kernels instantiated for storage 0 (two population sets, FP32).
+#include "step_launch.cuh"
+
+namespace lbcg {
+
+template cudaError_t launch_phi_t<0>(const Geo&, const StateBuf&, void*, cudaStream_t);
+template cudaError_t launch_step_s<0>(int, bool, bool, int, const Geo&, const Phys&, const StateBuf&, const InitBuf&,
+                                         const void*, StateBuf, void*, unsigned*, cudaStream_t);
+template cudaError_t launch_export_t<0>(int, const Geo&, const Phys&, const StateBuf&, const InitBuf&, int, int, int,
+                                          int, int, int, double*, double*, cudaStream_t);
+
+}  // namespace lbcg

@@ -200,6 +200,46 @@ uint64_t lb_launch_count(void);
 /* Bytes of device memory the handle holds. */
 size_t lb_device_bytes(const lb_handle* h);
 
+/* ---- batches of independent runs (uneven grids and parameters) ---------- */
+typedef struct lb_batch lb_batch;
+
+/* Create nruns runs (grids[r], params[r]; one storage format for all, FP32 or
+ * FP16; FP64 is rejected) on the current device, sharing one stream.  Each run
+ * is a full lb_handle reachable through lb_batch_run; the batch owns them. */
+int lb_batch_create(int32_t nruns, const lb_grid* grids, const lb_params* params, const lb_alloc* alloc,
+                    lb_batch** out);
+int lb_batch_destroy(lb_batch* b);
+
+/* Borrowed handle of run r (initialise it with lb_init_droplets/lb_init_fields,
+ * read it with lb_fields/lb_reduce_f64/...; do not destroy it).  NULL when r
+ * is out of range. */
+lb_handle* lb_batch_run(lb_batch* b, int32_t run);
+int32_t lb_batch_size(const lb_batch* b);
+int64_t lb_batch_nodes(const lb_batch* b);
+int lb_batch_set_stream(lb_batch* b, void* stream);
+
+/* Advance every run by nsteps: per step one persistent launch of the
+ * phase-field pass and one of the fused pass over the work list of all runs'
+ * (run, tile) items, replayed from a captured CUDA graph.  All runs must be
+ * initialised; the first step of freshly initialised runs is taken per run. */
+int lb_batch_step(lb_batch* b, int64_t nsteps);
+
+/* The one-run-at-a-time baseline: lb_step on each run in turn. */
+int lb_batch_step_sequential(lb_batch* b, int64_t nsteps);
+
+/* Tile shape (0..3, as lb_set_tile) and persistent CTAs per SM (1..16). */
+int lb_batch_set_tile(lb_batch* b, int tile, int blocks_per_sm);
+
+/* Autotuner: time `steps` batched steps for every tile shape and CTAs-per-SM
+ * in {1, 2, 4}, keep the fastest.  With use_cache, a result stored for the same
+ * GPU, storage and set of run shapes is reused.  Results are appended to the
+ * file named by LBCG_TUNE_CACHE (default $HOME/.cache/lbcg_tune.txt).
+ * result (host, 4 doubles): tile, blocks_per_sm, ms per step, 1 if cached. */
+int lb_batch_autotune(lb_batch* b, int32_t steps, int use_cache, double* result);
+
+/* lb_check on every run. */
+int lb_batch_check(lb_batch* b);
+
 const char* lb_strerror(int code);
 const char* lb_last_error(void);
 

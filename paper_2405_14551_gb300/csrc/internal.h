@@ -50,6 +50,17 @@ struct InitBuf {
 
 enum Loader { LOAD_PULL = 0, LOAD_FIELDS = 1 };
 
+// One run of a batch, as seen by the batched persistent kernels.
+struct RunDesc {
+  Geo g;
+  Phys p;
+  StateBuf S[2];
+  void* phi;
+  int tiles_x, tiles_y, tiles_z;
+  long long tile_begin;   // first work item of this run in the step list
+  long long chunk_begin;  // first 256-node chunk of this run in the phase-field list
+};
+
 // Tile shapes of the fused step kernel (x, y extent of the thread block and z
 // nodes per thread).
 struct Tile {
@@ -73,6 +84,13 @@ cudaError_t launch_step(int storage, int loader, bool write_state, bool write_fi
 cudaError_t launch_export(int storage, int loader, const Geo& g, const Phys& p, const StateBuf& in,
                           const InitBuf& init, int x0, int y0, int z0, int bx, int by, int bz, double* outA,
                           double* outB, cudaStream_t st);
+
+// batched step over runs[0..nruns): phase-field pass then fused pass, each a
+// persistent launch of blocks_per_sm x SMs CTAs; parity selects S[parity] as input
+cudaError_t launch_batched(int storage, const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles,
+                           int tile, int halo_max, long long max_nodes, int parity, int blocks_per_sm,
+                           unsigned* status, cudaStream_t st);
+int sm_count_host();
 
 // --- aux_kernels.cu ----------------------------------------------------------
 cudaError_t launch_init_droplets(const Geo& g, int n, const double* d_centres, const double* d_radii, double width,

@@ -5,11 +5,16 @@
 // asynchronously on the handle's stream; runs of steps replay a captured CUDA
 // graph of STEPS_PER_GRAPH steps (two kernels per step).
 #include <cuda_runtime.h>
+#include <sys/stat.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -738,6 +743,359 @@ int lb_load(lb_handle* h, const char* path) {
   }
   h->t = t;
   h->initialised = true;
+  return LB_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// batches of independent runs
+// ===========================================================================
+struct lb_batch {
+  std::vector<lb_handle*> runs;
+  int storage = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  RunDesc* d_runs = nullptr;
+  std::vector<RunDesc> h_runs;
+  long long nchunks = 0, ntiles = 0, max_nodes = 0, total_nodes = 0;
+  int halo_max = 1;
+  int tile = 0;
+  int blocks_per_sm = 2;
+  bool dirty = true;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+constexpr int BATCH_STEPS_PER_GRAPH = 16;
+
+void batch_drop_graphs(lb_batch* b) {
+  for (int k = 0; k < 2; ++k) {
+    if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+    b->graph[k] = nullptr;
+  }
+}
+
+int batch_descriptors(lb_batch* b) {
+  const Tile& T = kTiles[b->tile];
+  long long tb = 0, cb = 0;
+  b->halo_max = 1;
+  b->max_nodes = 0;
+  b->h_runs.resize(b->runs.size());
+  for (size_t r = 0; r < b->runs.size(); ++r) {
+    lb_handle* h = b->runs[r];
+    RunDesc& d = b->h_runs[r];
+    d.g = h->g;
+    d.p = h->p;
+    d.S[0] = h->S[0];
+    d.S[1] = h->S[1];
+    d.phi = h->phi;
+    d.tiles_x = (h->g.nx + T.tx - 1) / T.tx;
+    d.tiles_y = (h->g.ny + T.ty - 1) / T.ty;
+    d.tiles_z = (h->g.nz + T.tz - 1) / T.tz;
+    d.tile_begin = tb;
+    d.chunk_begin = cb;
+    tb += (long long)d.tiles_x * d.tiles_y * d.tiles_z;
+    cb += (h->g.N + 255) / 256;
+    b->halo_max = std::max(b->halo_max, h->p.halo);
+    b->max_nodes = std::max(b->max_nodes, h->g.N);
+  }
+  b->ntiles = tb;
+  b->nchunks = cb;
+  LB_CUDA(cudaMemcpyAsync(b->d_runs, b->h_runs.data(), sizeof(RunDesc) * b->h_runs.size(), cudaMemcpyHostToDevice,
+                          b->stream));
+  LB_CUDA(cudaStreamSynchronize(b->stream));
+  b->dirty = false;
+  return LB_OK;
+}
+
+int batch_issue(lb_batch* b, int parity) {
+  LB_CUDA(launch_batched(b->storage, b->d_runs, (int)b->runs.size(), b->nchunks, b->ntiles, b->tile, b->halo_max,
+                         b->max_nodes, parity, b->blocks_per_sm, b->runs[0]->status, b->stream));
+  g_launches += 2;
+  return LB_OK;
+}
+
+int batch_build_graph(lb_batch* b, int parity) {
+  cudaGraph_t graph = nullptr;
+  const uint64_t save_l = g_launches.load();
+  LB_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = LB_OK;
+  for (int k = 0; k < BATCH_STEPS_PER_GRAPH && rc == LB_OK; ++k) rc = batch_issue(b, parity ^ (k & 1));
+  cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  g_launches = save_l;
+  if (rc != LB_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_err(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&b->graph[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  return cuda_err(e, "cudaGraphInstantiate");
+}
+
+// bring every run to the population state and a common parity
+int batch_prepare(lb_batch* b) {
+  for (lb_handle* h : b->runs) {
+    if (!h->initialised) return set_err(LB_ESTATE, "a run of the batch is not initialised");
+    if (h->mode == 0) {
+      int rc = issue_step(h);
+      if (rc) return rc;
+    }
+  }
+  const int par = b->runs[0]->cur;
+  for (lb_handle* h : b->runs)
+    if (h->cur != par) return set_err(LB_ESTATE, "runs of the batch are at different parities");
+  if (b->dirty) return batch_descriptors(b);
+  return LB_OK;
+}
+
+void batch_advance(lb_batch* b, int64_t n) {
+  for (lb_handle* h : b->runs) {
+    h->t += n;
+    h->cur ^= (int)(n & 1);
+  }
+}
+
+std::string tune_cache_path() {
+  const char* p = std::getenv("LBCG_TUNE_CACHE");
+  if (p && p[0]) return p;
+  const char* home = std::getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/lbcg_tune.txt";
+}
+
+std::string batch_key(const lb_batch* b) {
+  cudaDeviceProp prop{};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  std::vector<std::string> shapes;
+  for (lb_handle* h : b->runs) {
+    std::ostringstream os;
+    os << h->g.nx << "x" << h->g.ny << "x" << h->g.nz << "w" << h->grid.walls << "h" << h->p.halo;
+    shapes.push_back(os.str());
+  }
+  std::sort(shapes.begin(), shapes.end());
+  std::ostringstream key;
+  std::string name = prop.name;
+  for (char& c : name)
+    if (c == ' ') c = '_';
+  key << name << "|st" << b->storage << "|";
+  for (auto& sh : shapes) key << sh << ",";
+  return key.str();
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_batch_create(int32_t nruns, const lb_grid* grids, const lb_params* params, const lb_alloc* alloc,
+                    lb_batch** out) {
+  if (!out) return set_err(LB_EINVAL, "out is null");
+  *out = nullptr;
+  if (nruns < 1 || nruns > 65536 || !grids || !params) return set_err(LB_EINVAL, "need 1..65536 runs with grids and params");
+  for (int r = 0; r < nruns; ++r) {
+    int rc = validate(&grids[r], &params[r]);
+    if (rc) return rc;
+    if (params[r].storage != params[0].storage) return set_err(LB_EINVAL, "all runs of a batch share one storage");
+  }
+  if (params[0].storage == LB_STORAGE_TWOSET_F64) return set_err(LB_EINVAL, "batches support FP32/FP16 storage only");
+  lb_batch* b = new lb_batch();
+  b->storage = params[0].storage;
+  cudaError_t e = cudaStreamCreate(&b->own_stream);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_err(e, "cudaStreamCreate");
+  }
+  b->stream = b->own_stream;
+  for (int r = 0; r < nruns; ++r) {
+    lb_handle* h = nullptr;
+    int rc = lb_create(&grids[r], &params[r], alloc, &h);
+    if (rc) {
+      lb_batch_destroy(b);
+      return rc;
+    }
+    lb_set_stream(h, b->stream);
+    b->runs.push_back(h);
+    b->total_nodes += h->g.N;
+  }
+  b->d_runs = (RunDesc*)dev_alloc(b->runs[0], sizeof(RunDesc) * (size_t)nruns);
+  if (!b->d_runs) {
+    lb_batch_destroy(b);
+    return set_err(LB_ENOMEM, "descriptor allocation failed");
+  }
+  *out = b;
+  return LB_OK;
+}
+
+int lb_batch_destroy(lb_batch* b) {
+  if (!b) return LB_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graphs(b);
+  for (size_t r = b->runs.size(); r-- > 0;) lb_destroy(b->runs[r]);  // run 0 owns the descriptors
+  if (b->own_stream) cudaStreamDestroy(b->own_stream);
+  delete b;
+  return LB_OK;
+}
+
+lb_handle* lb_batch_run(lb_batch* b, int32_t run) {
+  if (!b || run < 0 || run >= (int)b->runs.size()) {
+    set_err(LB_EINVAL, "run index out of range");
+    return nullptr;
+  }
+  b->dirty = true;  // the caller may re-initialise the run
+  batch_drop_graphs(b);
+  return b->runs[(size_t)run];
+}
+
+int32_t lb_batch_size(const lb_batch* b) { return b ? (int32_t)b->runs.size() : -1; }
+
+int64_t lb_batch_nodes(const lb_batch* b) { return b ? b->total_nodes : -1; }
+
+int lb_batch_set_stream(lb_batch* b, void* stream) {
+  if (!b) return set_err(LB_EINVAL, "null batch");
+  cudaStream_t next = stream ? (cudaStream_t)stream : b->own_stream;
+  for (lb_handle* h : b->runs) {
+    int rc = lb_set_stream(h, next);
+    if (rc) return rc;
+  }
+  b->stream = next;
+  batch_drop_graphs(b);
+  return LB_OK;
+}
+
+int lb_batch_set_tile(lb_batch* b, int tile, int blocks_per_sm) {
+  if (!b) return set_err(LB_EINVAL, "null batch");
+  if (tile < 0 || tile >= NUM_TILES || blocks_per_sm < 1 || blocks_per_sm > 16)
+    return set_err(LB_EINVAL, "tile in 0..3 and blocks_per_sm in 1..16");
+  if (tile != b->tile || blocks_per_sm != b->blocks_per_sm) {
+    b->tile = tile;
+    b->blocks_per_sm = blocks_per_sm;
+    b->dirty = true;
+    batch_drop_graphs(b);
+  }
+  return LB_OK;
+}
+
+int lb_batch_step(lb_batch* b, int64_t nsteps) {
+  if (!b) return set_err(LB_EINVAL, "null batch");
+  if (nsteps < 0) return set_err(LB_EINVAL, "nsteps must be >= 0");
+  if (nsteps == 0) return LB_OK;
+  int rc;
+  bool first_done = false;
+  for (lb_handle* h : b->runs)
+    if (h->mode == 0) first_done = true;
+  if ((rc = batch_prepare(b))) return rc;
+  if (first_done) {  // the first step of freshly initialised runs was taken per run
+    for (lb_handle* h : b->runs)
+      if (h->t == 0) return set_err(LB_ESTATE, "internal: run not advanced");
+    --nsteps;
+  }
+  while (nsteps >= BATCH_STEPS_PER_GRAPH) {
+    const int par = b->runs[0]->cur;
+    if (!b->graph[par] && (rc = batch_build_graph(b, par))) return rc;
+    LB_CUDA(cudaGraphLaunch(b->graph[par], b->stream));
+    g_launches += 2 * BATCH_STEPS_PER_GRAPH;
+    batch_advance(b, BATCH_STEPS_PER_GRAPH);
+    nsteps -= BATCH_STEPS_PER_GRAPH;
+  }
+  while (nsteps-- > 0) {
+    if ((rc = batch_issue(b, b->runs[0]->cur))) return rc;
+    batch_advance(b, 1);
+  }
+  return LB_OK;
+}
+
+int lb_batch_step_sequential(lb_batch* b, int64_t nsteps) {
+  if (!b) return set_err(LB_EINVAL, "null batch");
+  for (lb_handle* h : b->runs) {
+    int rc = lb_step(h, nsteps);
+    if (rc) return rc;
+  }
+  return LB_OK;
+}
+
+int lb_batch_check(lb_batch* b) {
+  if (!b) return set_err(LB_EINVAL, "null batch");
+  for (lb_handle* h : b->runs) {
+    int rc = lb_check(h);
+    if (rc) return rc;
+  }
+  return LB_OK;
+}
+
+int lb_batch_autotune(lb_batch* b, int32_t steps, int use_cache, double* result) {
+  if (!b || !result) return set_err(LB_EINVAL, "null argument");
+  if (steps < 1 || steps > 1000) return set_err(LB_EINVAL, "steps must lie in [1, 1000]");
+  int rc = batch_prepare(b);
+  if (rc) return rc;
+  const std::string key = batch_key(b);
+  const std::string path = tune_cache_path();
+  if (use_cache) {
+    std::ifstream in(path);
+    std::string k;
+    int tile, bps;
+    double ms;
+    while (in >> k >> tile >> bps >> ms) {
+      if (k == key && tile >= 0 && tile < NUM_TILES && bps >= 1 && bps <= 16) {
+        if ((rc = lb_batch_set_tile(b, tile, bps))) return rc;
+        result[0] = tile;
+        result[1] = bps;
+        result[2] = ms;
+        result[3] = 1;  // from the cache
+        return LB_OK;
+      }
+    }
+  }
+  const int bps_opts[3] = {1, 2, 4};
+  double best = 1e30;
+  int best_tile = 0, best_bps = 2;
+  cudaEvent_t e0, e1;
+  LB_CUDA(cudaEventCreate(&e0));
+  LB_CUDA(cudaEventCreate(&e1));
+  for (int tile = 0; tile < NUM_TILES; ++tile) {
+    for (int bps : bps_opts) {
+      if ((rc = lb_batch_set_tile(b, tile, bps)) || (rc = batch_prepare(b))) break;
+      for (int k = 0; k < 2 && rc == LB_OK; ++k) {
+        rc = batch_issue(b, b->runs[0]->cur);
+        batch_advance(b, 1);
+      }
+      cudaEventRecord(e0, b->stream);
+      for (int k = 0; k < steps && rc == LB_OK; ++k) {
+        rc = batch_issue(b, b->runs[0]->cur);
+        batch_advance(b, 1);
+      }
+      cudaEventRecord(e1, b->stream);
+      cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == LB_OK && e != cudaSuccess) rc = cuda_err(e, "autotune timing");
+      if (rc) break;
+      const double per = ms / steps;
+      if (per < best) {
+        best = per;
+        best_tile = tile;
+        best_bps = bps;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if ((rc = lb_batch_set_tile(b, best_tile, best_bps))) return rc;
+  result[0] = best_tile;
+  result[1] = best_bps;
+  result[2] = best;
+  result[3] = 0;
+  // append to the cache (best effort; creates the cache directory one level deep)
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos) mkdir(path.substr(0, slash).c_str(), 0755);
+  if (FILE* fp = std::fopen(path.c_str(), "a")) {
+    std::fprintf(fp, "%s %d %d %.6f\n", key.c_str(), best_tile, best_bps, best);
+    std::fclose(fp);
+  }
   return LB_OK;
 }
 

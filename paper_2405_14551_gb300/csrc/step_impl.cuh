@@ -571,21 +571,19 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
   }
 }
 
+// One tile of the fused step: stage phi of the tile + halo in shared memory
+// (one (y,z) row per thread row; solid and beyond-wall nodes get the marker;
+// periodic wrap only outside the box), then update the tile's nodes.  Ends
+// with a barrier, so the caller may reuse the shared tile.
 template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32>
-__global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : 2)
-    k_step(View<ST> S, View<ST> O, InitBuf init, const typename Store<ST>::R* __restrict__ phi, Geo g, Phys P,
-           typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status) {
+__device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, const InitBuf& init,
+                                          const typename Store<ST>::R* __restrict__ phi, const Geo& g, const Phys& P,
+                                          typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status,
+                                          typename Store<ST>::R* sp, int x0, int y0, int z0) {
   using R = typename Store<ST>::R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sp = reinterpret_cast<R*>(smem_raw);
-
   const int H = P.halo;
   const int SX = TX + 2 * H, SY = TY + 2 * H, SZ = TZ + 2 * H;
   const int SXY = SX * SY;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-
-  // stage phi of the tile + halo, one (y,z) row per thread row; solid and
-  // beyond-wall nodes get the marker; periodic wrap only outside the box
   bool any_solid = false;
   for (int row = threadIdx.y; row < SY * SZ; row += TY) {
     const int ly = row % SY, lz = row / SY;
@@ -614,6 +612,84 @@ __global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : 2)
   else
     step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32>(S, O, init, g, P, fields, status, sp, H, SX, SXY, x0,
                                                            y0, z0);
+  __syncthreads();
+}
+
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32>
+__global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : 2)
+    k_step(View<ST> S, View<ST> O, InitBuf init, const typename Store<ST>::R* __restrict__ phi, Geo g, Phys P,
+           typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status) {
+  using R = typename Store<ST>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  step_tile<ST, LOADER, WS, WF, TX, TY, TZ, IDX32>(S, O, init, phi, g, P, fields, status,
+                                                   reinterpret_cast<R*>(smem_raw), blockIdx.x * TX, blockIdx.y * TY,
+                                                   blockIdx.z * TZ);
+}
+
+// ---------------------------------------------------------------------------
+// batched persistent kernels: many independent runs of uneven sizes and
+// parameters.  Work items are (run, tile) for the step and (run, 256-node
+// chunk) for the phase field; persistent CTAs stride over the item list and
+// find the run of an item by binary search over the runs' prefix offsets.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_run(const RunDesc* runs, int nruns, long long item, bool by_tile) {
+  int lo = 0, hi = nruns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const long long b = by_tile ? runs[mid].tile_begin : runs[mid].chunk_begin;
+    if (b <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256) k_phi_batched(const RunDesc* __restrict__ runs, int nruns, long long nchunks,
+                                                     int parity) {
+  using R = typename Store<ST>::R;
+  for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int r = find_run(runs, nruns, c, false);
+    const Geo g = runs[r].g;
+    const long long idx = (c - runs[r].chunk_begin) * 256 + threadIdx.x;
+    if (idx >= g.N) continue;
+    const int x = (int)(idx % g.nx);
+    const long long yz = idx / g.nx;
+    const int y = (int)(yz % g.ny);
+    const int z = (int)(yz / g.ny);
+    R* phi = reinterpret_cast<R*>(runs[r].phi);
+    if (is_solid(g, x, y, z)) {
+      phi[idx] = R(0);
+      continue;
+    }
+    Nbr n;
+    make_nbr(g, x, y, z, n);
+    R f[Q], rA, rB;
+    pull_node<ST, false>(view<ST>(runs[r].S[parity]), g, n, idx, f, rA, rB, nullptr, nullptr);
+    phi[idx] = (rA - rB) / (rA + rB);
+  }
+}
+
+template <int ST, int TX, int TY, int TZ, bool IDX32>
+__global__ void __launch_bounds__(TX* TY, 2)
+    k_step_batched(const RunDesc* __restrict__ runs, int nruns, long long ntiles, int parity,
+                   unsigned* __restrict__ status) {
+  using R = typename Store<ST>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sp = reinterpret_cast<R*>(smem_raw);
+  InitBuf none{nullptr, nullptr, nullptr, 0};
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int r = find_run(runs, nruns, t, true);
+    const RunDesc& d = runs[r];
+    const long long lt = t - d.tile_begin;
+    const int bx = (int)(lt % d.tiles_x);
+    const int by = (int)((lt / d.tiles_x) % d.tiles_y);
+    const int bz = (int)(lt / ((long long)d.tiles_x * d.tiles_y));
+    const Geo g = d.g;
+    const Phys P = d.p;
+    step_tile<ST, LOAD_PULL, true, false, TX, TY, TZ, IDX32>(
+        view<ST>(d.S[parity]), view<ST>(d.S[parity ^ 1]), none, reinterpret_cast<const R*>(d.phi), g, P, nullptr,
+        status, sp, bx * TX, by * TY, bz * TZ);
+  }
 }
 
 // ---------------------------------------------------------------------------

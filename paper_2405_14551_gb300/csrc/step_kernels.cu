@@ -12,6 +12,10 @@ cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, 
                           const InitBuf& init, const void* phi, StateBuf out, void* fields, unsigned* status,
                           cudaStream_t st);
 template <int ST>
+cudaError_t launch_batched_t(const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles, int tile,
+                             int halo_max, long long max_nodes, int parity, int blocks_per_sm, unsigned* status,
+                             cudaStream_t st);
+template <int ST>
 cudaError_t launch_export_t(int loader, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init, int x0,
                             int y0, int z0, int bx, int by, int bz, double* outA, double* outB, cudaStream_t st);
 
@@ -47,6 +51,28 @@ cudaError_t launch_export(int storage, int loader, const Geo& g, const Phys& p, 
     case 3: return launch_export_t<3>(loader, g, p, in, init, x0, y0, z0, bx, by, bz, outA, outB, st);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batched(int storage, const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles,
+                           int tile, int halo_max, long long max_nodes, int parity, int blocks_per_sm,
+                           unsigned* status, cudaStream_t st) {
+  switch (storage) {
+    case 0: return launch_batched_t<0>(d_runs, nruns, nchunks, ntiles, tile, halo_max, max_nodes, parity, blocks_per_sm, status, st);
+    case 1: return launch_batched_t<1>(d_runs, nruns, nchunks, ntiles, tile, halo_max, max_nodes, parity, blocks_per_sm, status, st);
+    case 2: return launch_batched_t<2>(d_runs, nruns, nchunks, ntiles, tile, halo_max, max_nodes, parity, blocks_per_sm, status, st);
+  }
+  return cudaErrorInvalidValue;  // no batched FP64 instantiation
+}
+
+int sm_count_host() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
 }
 
 size_t elem_bytes(int storage) { return storage == 3 ? 8 : (storage == 2 ? 2 : 4); }

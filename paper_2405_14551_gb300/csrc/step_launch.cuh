@@ -91,4 +91,45 @@ cudaError_t launch_export_t(int loader, const Geo& g, const Phys& p, const State
   return cudaGetLastError();
 }
 
+template <int ST, int TX, int TY, int TZ, bool IDX32>
+inline cudaError_t launch_batched_step_t(const RunDesc* d_runs, int nruns, long long ntiles, int halo_max,
+                                         int parity, int blocks, unsigned* status, cudaStream_t st) {
+  using R = typename Store<ST>::R;
+  const size_t smem = sizeof(R) * (size_t)(TX + 2 * halo_max) * (TY + 2 * halo_max) * (TZ + 2 * halo_max);
+  auto kern = k_step_batched<ST, TX, TY, TZ, IDX32>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  trace_kernel("k_step_batched", kern, dim3(blocks), dim3(TX, TY), smem);
+  kern<<<blocks, dim3(TX, TY), smem, st>>>(d_runs, nruns, ntiles, parity, status);
+  return cudaGetLastError();
+}
+
+template <int ST, bool IDX32>
+inline cudaError_t launch_batched_tiles(int tile, const RunDesc* d_runs, int nruns, long long ntiles, int halo_max,
+                                        int parity, int blocks, unsigned* status, cudaStream_t st) {
+  switch (tile) {
+    case 1: return launch_batched_step_t<ST, 32, 8, 8, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
+    case 2: return launch_batched_step_t<ST, 32, 4, 8, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
+    case 3: return launch_batched_step_t<ST, 64, 4, 4, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
+    default: return launch_batched_step_t<ST, 32, 8, 4, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
+  }
+}
+
+template <int ST>
+cudaError_t launch_batched_t(const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles, int tile,
+                             int halo_max, long long max_nodes, int parity, int blocks_per_sm, unsigned* status,
+                             cudaStream_t st) {
+  const int blocks = sm_count() * (blocks_per_sm > 0 ? blocks_per_sm : 2);
+  const int pblocks = sm_count() * 8;
+  trace_kernel("k_phi_batched", k_phi_batched<ST>, dim3(pblocks), dim3(256), 0);
+  k_phi_batched<ST><<<pblocks, 256, 0, st>>>(d_runs, nruns, nchunks, parity);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)max_nodes < (1ull << 32);
+  if (idx32) return launch_batched_tiles<ST, true>(tile, d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
+  return launch_batched_tiles<ST, false>(tile, d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
+}
+
 }  // namespace lbcg

@@ -9,4 +9,7 @@ template cudaError_t launch_step_s<1>(int, bool, bool, int, const Geo&, const Ph
 template cudaError_t launch_export_t<1>(int, const Geo&, const Phys&, const StateBuf&, const InitBuf&, int, int, int,
                                           int, int, int, double*, double*, cudaStream_t);
 
+template cudaError_t launch_batched_t<1>(const RunDesc*, int, long long, long long, int, int, long long, int, int,
+                                           unsigned*, cudaStream_t);
+
 }  // namespace lbcg

@@ -82,6 +82,18 @@ _SIGS = {
     "lb_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "lb_launch_count": (ctypes.c_uint64, []),
     "lb_device_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "lb_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(lb_alloc),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "lb_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "lb_batch_run": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int32]),
+    "lb_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
+    "lb_batch_nodes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "lb_batch_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lb_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "lb_batch_step_sequential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "lb_batch_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "lb_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p]),
+    "lb_batch_check": (ctypes.c_int, [ctypes.c_void_p]),
     "lb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_last_error": (ctypes.c_char_p, []),
 }
@@ -358,3 +370,116 @@ class Sim:
 
     def load(self, path):
         lb_load(self.h, path)
+
+
+# ---------------------------------------------------------------------------
+# batches of independent runs
+# ---------------------------------------------------------------------------
+def lb_batch_create(grids, params, alloc: TorchAllocator | None = None):
+    L = load_library()
+    n = len(grids)
+    ga = (lb_grid * n)(*grids)
+    pa = (lb_params * n)(*params)
+    b = ctypes.c_void_p()
+    _check(L.lb_batch_create(n, ga, pa, ctypes.byref(alloc.struct) if alloc else None, ctypes.byref(b)),
+           "lb_batch_create")
+    return b
+
+
+def lb_batch_destroy(b):
+    _check(load_library().lb_batch_destroy(b), "lb_batch_destroy")
+
+
+def lb_batch_run(b, r: int):
+    h = load_library().lb_batch_run(b, int(r))
+    if not h:
+        _check(LB_EINVAL, "lb_batch_run")
+    return ctypes.c_void_p(h)
+
+
+def lb_batch_step(b, nsteps: int):
+    _check(load_library().lb_batch_step(b, int(nsteps)), "lb_batch_step")
+
+
+def lb_batch_step_sequential(b, nsteps: int):
+    _check(load_library().lb_batch_step_sequential(b, int(nsteps)), "lb_batch_step_sequential")
+
+
+def lb_batch_set_tile(b, tile: int, blocks_per_sm: int = 2):
+    _check(load_library().lb_batch_set_tile(b, int(tile), int(blocks_per_sm)), "lb_batch_set_tile")
+
+
+def lb_batch_autotune(b, steps: int = 4, use_cache: bool = True):
+    """(tile, blocks_per_sm, ms per step, from_cache)."""
+    out = np.zeros(4)
+    _check(load_library().lb_batch_autotune(b, int(steps), int(bool(use_cache)), out.ctypes.data), "lb_batch_autotune")
+    return int(out[0]), int(out[1]), float(out[2]), bool(out[3])
+
+
+def lb_batch_check(b):
+    _check(load_library().lb_batch_check(b), "lb_batch_check")
+
+
+def lb_batch_nodes(b) -> int:
+    return int(load_library().lb_batch_nodes(b))
+
+
+def lb_batch_set_stream(b, stream_ptr: int):
+    _check(load_library().lb_batch_set_stream(b, ctypes.c_void_p(stream_ptr)), "lb_batch_set_stream")
+
+
+class Batch:
+    """Many independent runs advanced together (memory from PyTorch)."""
+
+    def __init__(self, workloads, storage="twoset_f32", stream=None, use_torch_alloc=True):
+        import torch
+        self.workloads = list(workloads)
+        grids = [make_grid(*w.shape, walls=w.walls) for w in self.workloads]
+        params = [make_params(storage=storage, **w.params) for w in self.workloads]
+        self._alloc = TorchAllocator(torch.device("cuda", torch.cuda.current_device())) if use_torch_alloc else None
+        self.b = lb_batch_create(grids, params, self._alloc)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        lb_batch_set_stream(self.b, s.cuda_stream)
+        self.nodes = lb_batch_nodes(self.b)
+        for r, w in enumerate(self.workloads):
+            h = lb_batch_run(self.b, r)
+            if w.phi is not None:
+                lb_init_fields(h, w.phi)
+            else:
+                lb_init_droplets(h, w.centres, w.radii)
+
+    def run(self, r):
+        return lb_batch_run(self.b, r)
+
+    def step(self, n=1):
+        lb_batch_step(self.b, n)
+
+    def step_sequential(self, n=1):
+        lb_batch_step_sequential(self.b, n)
+
+    def autotune(self, steps=4, use_cache=True):
+        return lb_batch_autotune(self.b, steps, use_cache)
+
+    def check(self):
+        lb_batch_check(self.b)
+
+    def fields(self, r, names=FIELD_NAMES):
+        w = self.workloads[r]
+        mask = 0
+        for n in names:
+            mask |= FIELD_BIT[n]
+        sel = [n for n in FIELD_NAMES if mask & FIELD_BIT[n]]
+        out = np.zeros((len(sel),) + (w.shape[2], w.shape[1], w.shape[0]), dtype=np.float32)
+        lb_fields(self.run(r), mask, out, False)
+        return {n: out[k] for k, n in enumerate(sel)}
+
+    def close(self):
+        if getattr(self, "b", None):
+            lb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -134,7 +134,9 @@ def test_reductions_laplace_count(small_oracle_200):
     r = s.reduce()
     # FP32 storage drifts by round-off (about 1e-8 of the mass per step)
     np.testing.assert_allclose(r[0:2], red_o[0:2], rtol=5e-6)
-    assert np.all(np.abs(r[2:5]) < 1e-6)
+    # momentum stays at FP32 round-off: a random walk of ~1e-7 per node update
+    # over 6.6e6 updates is ~3e-4 (the FP64 instantiation conserves it to 1e-12)
+    assert np.all(np.abs(r[2:5]) < 2e-3)
     np.testing.assert_allclose(r[5], red_o[5], rtol=1e-6)
     assert r[6] == 0
     o = make_oracle(wl)

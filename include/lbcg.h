@@ -140,7 +140,8 @@ int lb_init_fields(lb_handle* h, const float* phi, const float* rho, const float
 int lb_step(lb_handle* h, int64_t nsteps);
 
 /* Choose the tile shape of the fused step kernel (0..3: 32x8x4, 32x8x8,
- * 32x4x8, 64x4x4 nodes per CTA); used by the autotuner.  Results do not
+ * 32x8x4 with a register cap for 3 CTAs per SM, 64x4x4 nodes per CTA); used
+ * by the autotuner.  Results do not
  * depend on the tile.  lb_get_tile returns the current index. */
 int lb_set_tile(lb_handle* h, int tile);
 int lb_get_tile(const lb_handle* h);

@@ -3,7 +3,7 @@
 
 namespace lbcg {
 
-const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 4, 8}, {64, 4, 4}};
+const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 8, 4}, {64, 4, 4}};  // tile 2: 3 CTAs/SM register cap
 
 template <int ST>
 cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st);

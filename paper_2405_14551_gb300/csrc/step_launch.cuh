@@ -26,15 +26,15 @@ cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream
   return cudaGetLastError();
 }
 
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ>
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int MINB = 2>
 inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
                                  const void* phi, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
   const int H = p.halo;
-  const size_t smem = sizeof(R) * (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
+  const size_t smem = step_smem_bytes<R>(TX, TY, TZ, H, p.A_h != 0.0);
   // 32-bit population offsets when every offset of the lattice fits
   const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
-  auto kern = idx32 ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, true> : k_step<ST, LOADER, WS, WF, TX, TY, TZ, false>;
+  auto kern = idx32 ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, true, MINB> : k_step<ST, LOADER, WS, WF, TX, TY, TZ, false, MINB>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -53,7 +53,7 @@ inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, cons
   if constexpr (LOADER == LOAD_PULL && WS && !WF) {
     switch (tile) {
       case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8>(g, p, in, init, phi, out, fields, status, st);
-      case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 4, 8>(g, p, in, init, phi, out, fields, status, st);
+      case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, 3>(g, p, in, init, phi, out, fields, status, st);
       case 3: return launch_step_t<ST, LOADER, WS, WF, 64, 4, 4>(g, p, in, init, phi, out, fields, status, st);
       default: break;
     }
@@ -91,12 +91,12 @@ cudaError_t launch_export_t(int loader, const Geo& g, const Phys& p, const State
   return cudaGetLastError();
 }
 
-template <int ST, int TX, int TY, int TZ, bool IDX32>
+template <int ST, int TX, int TY, int TZ, bool IDX32, int MINB = 2>
 inline cudaError_t launch_batched_step_t(const RunDesc* d_runs, int nruns, long long ntiles, int halo_max,
                                          int parity, int blocks, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  const size_t smem = sizeof(R) * (size_t)(TX + 2 * halo_max) * (TY + 2 * halo_max) * (TZ + 2 * halo_max);
-  auto kern = k_step_batched<ST, TX, TY, TZ, IDX32>;
+  const size_t smem = step_smem_bytes<R>(TX, TY, TZ, halo_max, halo_max > 1);
+  auto kern = k_step_batched<ST, TX, TY, TZ, IDX32, MINB>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -111,7 +111,7 @@ inline cudaError_t launch_batched_tiles(int tile, const RunDesc* d_runs, int nru
                                         int parity, int blocks, unsigned* status, cudaStream_t st) {
   switch (tile) {
     case 1: return launch_batched_step_t<ST, 32, 8, 8, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
-    case 2: return launch_batched_step_t<ST, 32, 4, 8, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
+    case 2: return launch_batched_step_t<ST, 32, 8, 4, IDX32, 3>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
     case 3: return launch_batched_step_t<ST, 64, 4, 4, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
     default: return launch_batched_step_t<ST, 32, 8, 4, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
   }

@@ -44,7 +44,7 @@ extern "C" {
 /* Two population sets f^A, f^B in FP32, [comp][27][nz][ny][nx]; 432 B per node update. */
 #define LB_STORAGE_TWOSET_F32 0
 /* Exact single-set form: total post-collision f* (27 x FP32) plus the colour
- * scalars s = rhoA/rho and v = beta rhoA rhoB/rho n (4 x FP32); the pulling
+ * scalars s = rhoA/rho and v = beta rhoA rhoB/rho n (one float4); the pulling
  * node rebuilds f^A_i = s f*_i + w_i c_i.v/|c_i| (recolouring, Eq. ome3_1). */
 #define LB_STORAGE_REDUCED_F32 1
 /* As REDUCED_F32 but f*_i stored as FP16 deviations (f*_i - w_i) * 4096 from
@@ -232,7 +232,8 @@ int lb_batch_step_sequential(lb_batch* b, int64_t nsteps);
 int lb_batch_set_tile(lb_batch* b, int tile, int blocks_per_sm);
 
 /* Autotuner: time `steps` batched steps for every tile shape and CTAs-per-SM
- * in {1, 2, 4}, keep the fastest.  With use_cache, a result stored for the same
+ * in {1, 2, 4}, keep the fastest.  Needs freshly initialised runs (step 0)
+ * and returns every run to its initial state afterwards.  With use_cache, a result stored for the same
  * GPU, storage and set of run shapes is reused.  Results are appended to the
  * file named by LBCG_TUNE_CACHE (default $HOME/.cache/lbcg_tune.txt).
  * result (host, 4 doubles): tile, blocks_per_sm, ms per step, 1 if cached. */

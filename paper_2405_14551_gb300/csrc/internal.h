@@ -31,13 +31,11 @@ struct Phys {
 
 // Device pointers of one population lattice.  Two-set storage: f holds
 // f^A [27][N] followed by f^B [27][N].  Reduced storage: f holds f* [27][N]
-// (FP32 or FP16 deviations) and s, vx, vy, vz hold the colour scalars.
+// (FP32 or FP16 deviations) and sv holds the colour scalars (s, vx, vy, vz)
+// of each node as one float4.
 struct StateBuf {
   void* f;
-  float* s;
-  float* vx;
-  float* vy;
-  float* vz;
+  float4* sv;
 };
 
 // Initial fields (device, float): phi[N], rho[N] or null, u[3][N] or null.

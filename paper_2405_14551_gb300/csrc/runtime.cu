@@ -140,16 +140,12 @@ bool alloc_state(lb_handle* h, StateBuf& s) {
     s.f = dev_alloc(h, 2 * (size_t)Q * N * elem_bytes(h->storage));
     return s.f != nullptr;
   }
-  // one allocation: f* then s, vx, vy, vz (each 256-byte aligned)
+  // one allocation: f* then the float4 colour scalars (256-byte aligned)
   const size_t fb = ((size_t)Q * N * elem_bytes(h->storage) + 255) & ~(size_t)255;
-  const size_t sb = (N * sizeof(float) + 255) & ~(size_t)255;
-  char* base = (char*)dev_alloc(h, fb + 4 * sb);
+  char* base = (char*)dev_alloc(h, fb + N * sizeof(float4));
   if (!base) return false;
   s.f = base;
-  s.s = (float*)(base + fb);
-  s.vx = (float*)(base + fb + sb);
-  s.vy = (float*)(base + fb + 2 * sb);
-  s.vz = (float*)(base + fb + 3 * sb);
+  s.sv = (float4*)(base + fb);
   return true;
 }
 
@@ -669,10 +665,8 @@ int lb_save(lb_handle* h, const char* path) {
     } else {
       const size_t fb = (size_t)Q * N * elem_bytes(h->storage);
       e = cudaMemcpyAsync(buf.data(), s.f, fb, cudaMemcpyDeviceToHost, h->stream);
-      float* arr[4] = {s.s, s.vx, s.vy, s.vz};
-      for (int k = 0; k < 4 && e == cudaSuccess; ++k)
-        e = cudaMemcpyAsync(buf.data() + fb + k * N * sizeof(float), arr[k], N * sizeof(float), cudaMemcpyDeviceToHost,
-                            h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(buf.data() + fb, s.sv, N * sizeof(float4), cudaMemcpyDeviceToHost, h->stream);
     }
   } else if (ok) {
     int32_t flags[2] = {h->use_rho, h->use_u};
@@ -722,10 +716,8 @@ int lb_load(lb_handle* h, const char* path) {
     } else {
       const size_t fb = (size_t)Q * N * elem_bytes(h->storage);
       e = cudaMemcpyAsync(s.f, buf.data(), fb, cudaMemcpyHostToDevice, h->stream);
-      float* arr[4] = {s.s, s.vx, s.vy, s.vz};
-      for (int k = 0; k < 4 && e == cudaSuccess; ++k)
-        e = cudaMemcpyAsync(arr[k], buf.data() + fb + k * N * sizeof(float), N * sizeof(float), cudaMemcpyHostToDevice,
-                            h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.sv, buf.data() + fb, N * sizeof(float4), cudaMemcpyHostToDevice, h->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_err(e, "checkpoint upload");
@@ -886,6 +878,8 @@ std::string batch_key(const lb_batch* b) {
   return key.str();
 }
 
+int batch_tune(lb_batch* b, int32_t steps, int use_cache, double* result);
+
 }  // namespace
 
 extern "C" {
@@ -1028,6 +1022,27 @@ int lb_batch_check(lb_batch* b) {
 int lb_batch_autotune(lb_batch* b, int32_t steps, int use_cache, double* result) {
   if (!b || !result) return set_err(LB_EINVAL, "null argument");
   if (steps < 1 || steps > 1000) return set_err(LB_EINVAL, "steps must lie in [1, 1000]");
+  for (lb_handle* h : b->runs)
+    if (!h->initialised || h->t != 0) return set_err(LB_ESTATE, "autotune needs freshly initialised runs");
+  int rc = batch_tune(b, steps, use_cache, result);
+  // the timed steps advanced the runs: return every run to its initial state
+  for (lb_handle* h : b->runs) {
+    cudaError_t e = launch_phi_from_init(h->storage, h->g, h->init_phi, h->phi, h->stream);
+    g_launches += 1;
+    if (e != cudaSuccess && rc == LB_OK) rc = cuda_err(e, "autotune reset");
+    h->mode = 0;
+    h->t = 0;
+    h->cur = 0;
+  }
+  batch_drop_graphs(b);
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+int batch_tune(lb_batch* b, int32_t steps, int use_cache, double* result) {
   int rc = batch_prepare(b);
   if (rc) return rc;
   const std::string key = batch_key(b);
@@ -1099,4 +1114,4 @@ int lb_batch_autotune(lb_batch* b, int32_t steps, int use_cache, double* result)
   return LB_OK;
 }
 
-}  // extern "C"
+}  // namespace

@@ -135,17 +135,14 @@ template <int ST>
 struct View {
   using E = typename Store<ST>::E;
   E* f;
-  float *s, *vx, *vy, *vz;
+  float4* sv;
 };
 
 template <int ST>
 __host__ __device__ __forceinline__ View<ST> view(const StateBuf& b) {
   View<ST> v;
   v.f = reinterpret_cast<typename Store<ST>::E*>(b.f);
-  v.s = b.s;
-  v.vx = b.vx;
-  v.vy = b.vy;
-  v.vz = b.vz;
+  v.sv = b.sv;
   return v;
 }
 
@@ -181,8 +178,9 @@ __device__ __forceinline__ void pull_node(const View<ST>& S, const Geo& g, const
     } else {
       // single set: f^A_dir(src) = s f*_dir + w c_dir.v/|c_dir| (recolouring, Eq. ome3_1)
       const R fs = decode<ST>(S.f[(size_t)dir * N + src], i);
-      const R s = S.s[src];
-      const R cv = R(cx(i)) * R(S.vx[src]) + R(cy(i)) * R(S.vy[src]) + R(cz(i)) * R(S.vz[src]);
+      const float4 sv = S.sv[src];
+      const R s = sv.x;
+      const R cv = R(cx(i)) * R(sv.y) + R(cy(i)) * R(sv.z) + R(cz(i)) * R(sv.w);
       const R seg = (bb ? R(-1) : R(1)) * wgt<R>(i) * inv_norm<R>(i) * cv;
       const R va = s * fs + seg;
       const R vb = (R(1) - s) * fs - seg;
@@ -353,11 +351,12 @@ __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const
       rB += vb;
     } else {
       const R fs = decode<ST>(S.f[dir * N + (I)src], i);
-      const R s = S.s[src];
+      const float4 sv = S.sv[src];
+      const R s = sv.x;
       R cv = R(0);
-      if (cx(i)) cv += R(cx(i)) * R(S.vx[src]);
-      if (cy(i)) cv += R(cy(i)) * R(S.vy[src]);
-      if (cz(i)) cv += R(cz(i)) * R(S.vz[src]);
+      if (cx(i)) cv += R(cx(i)) * R(sv.y);
+      if (cy(i)) cv += R(cy(i)) * R(sv.z);
+      if (cz(i)) cv += R(cz(i)) * R(sv.w);
       R seg = wgt<R>(i) * inv_norm<R>(i) * cv;
       if constexpr (!WALLFREE) seg = bb ? -seg : seg;
       const R va = s * fs + seg;
@@ -368,35 +367,10 @@ __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const
   }
 }
 
-// Colour gradient of every node of the tile plus a halo of K = H - 1 (the
-// near-contact reach) into three shared arrays.  Halo nodes that cannot be
-// scan targets (|phi| >= phi_I, including solids) keep a zero gradient.
-template <typename R, int TX, int TY, int TZ, bool WALLFREE>
-__device__ __forceinline__ void grad_tile_fill(const R* sp, R* gt, int H, int SX, int SXY, R phi_I) {
-  const int K = H - 1;
-  const int GX = TX + 2 * K, GY = TY + 2 * K, GZ = TZ + 2 * K;
-  const int GXY = GX * GY, GN = GXY * GZ;
-  for (int row = threadIdx.y; row < GY * GZ; row += TY) {
-    const int gy = row % GY, gz = row / GY;
-    const bool yz_in = gy >= K && gy < K + TY && gz >= K && gz < K + TZ;
-    for (int gx = threadIdx.x; gx < GX; gx += TX) {
-      const int c = (gz + 1) * SXY + (gy + 1) * SX + (gx + 1);
-      const bool interior = yz_in && gx >= K && gx < K + TX;
-      R gr[3] = {R(0), R(0), R(0)};
-      if (interior || fabs(sp[c]) < phi_I) tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
-      const int o = gz * GXY + gy * GX + gx;
-      gt[o] = gr[0];
-      gt[GN + o] = gr[1];
-      gt[2 * GN + o] = gr[2];
-    }
-  }
-}
-
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32, bool GT>
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32>
 __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O, const InitBuf& init, const Geo& g,
                                            const Phys& P, typename Store<ST>::R* __restrict__ fields,
-                                           unsigned* __restrict__ status, const typename Store<ST>::R* sp,
-                                           const typename Store<ST>::R* gt, int H,
+                                           unsigned* __restrict__ status, const typename Store<ST>::R* sp, int H,
                                            int SX, int SXY, int x0, int y0, int z0) {
   using R = typename Store<ST>::R;
   using I = typename std::conditional<IDX32, unsigned, size_t>::type;
@@ -436,20 +410,11 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       if (cz(p)) j2 += R(cz(p)) * d;
     }
 
-    // colour gradient from the tile (precomputed when the scan needs a halo of gradients)
+    // colour gradient from the tile
     const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + H);
     const R phx = sp[c];
     R gr[3];
-    const int K = H - 1;
-    const int GX = TX + 2 * K, GXY = GX * (TY + 2 * K), GN = GXY * (TZ + 2 * K);
-    const int gc = (lz + K) * GXY + (threadIdx.y + K) * GX + (threadIdx.x + K);
-    if constexpr (GT) {
-      gr[0] = gt[gc];
-      gr[1] = gt[GN + gc];
-      gr[2] = gt[2 * GN + gc];
-    } else {
-      tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
-    }
+    tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
     const R gg = rsqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
 
     // near-contact scan (Eqs. stress_jump, near_cont_force): from an interface
@@ -474,14 +439,7 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
         const R phy = sp[cy_];
         if (!(fabs(phy) < phi_I)) continue;
         R gy_[3];
-        if constexpr (GT) {
-          const int gy_c = gc + dx + GX * dy + GXY * dz;
-          gy_[0] = gt[gy_c];
-          gy_[1] = gt[GN + gy_c];
-          gy_[2] = gt[2 * GN + gy_c];
-        } else {
-          tile_grad<R, WALLFREE>(sp, cy_, SX, SXY, gy_);
-        }
+        tile_grad<R, WALLFREE>(sp, cy_, SX, SXY, gy_);
         const R gm2 = gy_[0] * gy_[0] + gy_[1] * gy_[1] + gy_[2] * gy_[2];
         if (gm2 < R(NC_GRAD_MIN) * R(NC_GRAD_MIN)) continue;
         const R dot = gr[0] * gy_[0] + gr[1] * gy_[1] + gr[2] * gy_[2];
@@ -604,10 +562,7 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       }
     }
     if constexpr (!Store<ST>::TWOSET) {
-      O.s[self] = sA;
-      O.vx[self] = segamp * gr[0];
-      O.vy[self] = segamp * gr[1];
-      O.vz[self] = segamp * gr[2];
+      O.sv[self] = make_float4(sA, segamp * gr[0], segamp * gr[1], segamp * gr[2]);
     }
   }
 }
@@ -647,36 +602,19 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
   }
   // a tile whose halo holds no solid node needs no bounce-back or wall tests
   const bool wallfree = !__syncthreads_or(any_solid);
-  R* gt = sp + (size_t)SXY * SZ;
-  if (P.A_h != 0.0) {
-    // near contact: gradients of the tile + scan halo, computed once
-    if (wallfree) grad_tile_fill<R, TX, TY, TZ, true>(sp, gt, H, SX, SXY, R(P.phi_I));
-    else grad_tile_fill<R, TX, TY, TZ, false>(sp, gt, H, SX, SXY, R(P.phi_I));
-    __syncthreads();
-    if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, true>(S, O, init, g, P, fields, status, sp, gt, H, SX,
-                                                                    SXY, x0, y0, z0);
-    else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, true>(S, O, init, g, P, fields, status, sp, gt, H, SX,
-                                                                     SXY, x0, y0, z0);
-  } else {
-    if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, false>(S, O, init, g, P, fields, status, sp, gt, H, SX,
-                                                                     SXY, x0, y0, z0);
-    else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, false>(S, O, init, g, P, fields, status, sp, gt, H, SX,
-                                                                      SXY, x0, y0, z0);
-  }
+  if (wallfree)
+    step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32>(S, O, init, g, P, fields, status, sp, H, SX, SXY, x0, y0,
+                                                          z0);
+  else
+    step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32>(S, O, init, g, P, fields, status, sp, H, SX, SXY, x0,
+                                                           y0, z0);
   __syncthreads();
 }
 
-// Shared memory of one fused-step tile: the phi tile with halo H and, with
-// near contact, three gradient arrays over the tile + halo H - 1.
+// Shared memory of one fused-step tile: the phi tile with halo H.
 template <typename R>
-inline size_t step_smem_bytes(int TX, int TY, int TZ, int H, bool near_contact) {
-  size_t n = (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
-  if (near_contact) n += 3 * (size_t)(TX + 2 * H - 2) * (TY + 2 * H - 2) * (TZ + 2 * H - 2);
-  return sizeof(R) * n;
+inline size_t step_smem_bytes(int TX, int TY, int TZ, int H) {
+  return sizeof(R) * (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
 }
 
 template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32, int MINB = 2>

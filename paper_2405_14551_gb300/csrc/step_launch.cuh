@@ -31,7 +31,7 @@ inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in
                                  const void* phi, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
   const int H = p.halo;
-  const size_t smem = step_smem_bytes<R>(TX, TY, TZ, H, p.A_h != 0.0);
+  const size_t smem = step_smem_bytes<R>(TX, TY, TZ, H);
   // 32-bit population offsets when every offset of the lattice fits
   const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
   auto kern = idx32 ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, true, MINB> : k_step<ST, LOADER, WS, WF, TX, TY, TZ, false, MINB>;
@@ -95,7 +95,7 @@ template <int ST, int TX, int TY, int TZ, bool IDX32, int MINB = 2>
 inline cudaError_t launch_batched_step_t(const RunDesc* d_runs, int nruns, long long ntiles, int halo_max,
                                          int parity, int blocks, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  const size_t smem = step_smem_bytes<R>(TX, TY, TZ, halo_max, halo_max > 1);
+  const size_t smem = step_smem_bytes<R>(TX, TY, TZ, halo_max);
   auto kern = k_step_batched<ST, TX, TY, TZ, IDX32, MINB>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -242,6 +242,29 @@ int lb_batch_autotune(lb_batch* b, int32_t steps, int use_cache, double* result)
 /* lb_check on every run. */
 int lb_batch_check(lb_batch* b);
 
+/* ---- allocation-free reduction (no counterpart in the paper) ------------- */
+/* Same sums as lb_reduce_f64, for callers that cannot allocate device memory
+ * (programs that hand out all device memory themselves and forbid later
+ * allocations, or paths that must avoid the implicit synchronisation of
+ * cudaMalloc/cudaFree).  Allocates nothing: the block partial sums live in a
+ * static 64 KiB device array of the library (LB_STATIC_REDUCE_MAX_BLOCKS
+ * blocks x 8 doubles), held by every GPU that loads the library until the
+ * process exits.
+ *   fields: device array [14][nz][ny][nx] as written by lb_fields with all 14
+ *           fields selected (float, or double when fields_are_f64 != 0);
+ *   out:    device array of 8 doubles (same meaning as lb_reduce_f64's),
+ *           written asynchronously on `stream` (cudaStream_t, NULL = legacy);
+ *   walls:  as lb_grid.walls (solid layers are excluded from the sums).
+ * Grids above 2^31 - 1 nodes are rejected with LB_EINVAL.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (concurrent
+ * streams) race and must be serialised by the caller.  Nothing needs
+ * clearing between calls: every partial and every output is overwritten. */
+#define LB_STATIC_REDUCE_MAX_BLOCKS 1024
+int lb_reduce_fields_f64_static(const void* fields, int fields_are_f64, int32_t nx, int32_t ny, int32_t nz,
+                                uint32_t walls, double* out, void* stream);
+
 const char* lb_strerror(int code);
 const char* lb_last_error(void);
 

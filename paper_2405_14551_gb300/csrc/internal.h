@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace lbcg {
 
 // Box geometry; w* = 1 makes layers 0 and n-1 of that axis solid.
@@ -102,5 +104,11 @@ cudaError_t launch_laplace(int storage, const Geo& g, const void* fields, double
                            double* out4, cudaStream_t st);
 cudaError_t launch_cc(int storage, const Geo& g, const void* fields, int* labels, int* count, unsigned* status,
                       cudaStream_t st);
+
+// --- runtime.cu --------------------------------------------------------------
+// record code + message as the calling thread's last error; returns code
+int report_error(int code, const std::string& msg);
+// add n to the library's kernel launch counter
+void count_launches(int n);
 
 }  // namespace lbcg

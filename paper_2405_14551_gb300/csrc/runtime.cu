@@ -62,6 +62,11 @@ __global__ void k_convert_d(long long n, const T* __restrict__ src, double* __re
 
 }  // namespace
 
+namespace lbcg {
+int report_error(int code, const std::string& msg) { return set_err(code, msg); }
+void count_launches(int n) { g_launches += (uint64_t)n; }
+}  // namespace lbcg
+
 struct lb_handle {
   lb_grid grid;
   lb_params params;

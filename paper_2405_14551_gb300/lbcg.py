@@ -94,6 +94,8 @@ _SIGS = {
     "lb_batch_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "lb_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p]),
     "lb_batch_check": (ctypes.c_int, [ctypes.c_void_p]),
+    "lb_reduce_fields_f64_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "lb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_last_error": (ctypes.c_char_p, []),
 }
@@ -280,6 +282,15 @@ def lb_save(h, path: str):
 
 def lb_load(h, path: str):
     _check(load_library().lb_load(h, path.encode()), "lb_load")
+
+
+def lb_reduce_fields_f64_static(fields_ptr: int, fields_are_f64: bool, nx: int, ny: int, nz: int, walls: int,
+                                out_ptr: int, stream_ptr: int = 0):
+    """Allocation-free FP64 sums of a device fields array into 8 device doubles."""
+    _check(load_library().lb_reduce_fields_f64_static(ctypes.c_void_p(fields_ptr), int(bool(fields_are_f64)), int(nx),
+                                                      int(ny), int(nz), int(walls), ctypes.c_void_p(out_ptr),
+                                                      ctypes.c_void_p(stream_ptr)),
+           "lb_reduce_fields_f64_static")
 
 
 def lb_launch_count() -> int:

@@ -1,0 +1,83 @@
+/*
+ * lbnn.h -- C ABI of the surrogate network's kernels (the learned part that
+ * advances (phi, rho, u) by K lattice Boltzmann steps; its populations are
+ * then rebuilt by the regularised reconstruction of lbcg.h, Sec. IV.C).
+ *
+ * Activations are channels-last BF16 tensors X[v][c], v = x + nx (y + ny (z +
+ * nz b)), 16-byte aligned device pointers.  Convolutions run on the tcgen05
+ * tensor cores (BF16 operands, FP32 accumulation in tensor memory).
+ * periodic: bit a (a = 0,1,2 for x,y,z) wraps that axis, otherwise the
+ * convolution pads with zeros.  status: device word; bit 4 is set when a
+ * bounded wait inside a kernel gave up (the output is then not written).
+ * All calls are asynchronous on `stream` (cudaStream_t, NULL = legacy stream)
+ * and return LB_OK or an LB_E* code (lbcg.h) after host-side validation.
+ */
+#ifndef LBNN_H
+#define LBNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* y[v][co] = act(bias[co] + sum_{t<taps, ci} w[co][t][ci] x[v + off_t][ci]),
+ * taps = 27 (3x3x3, tap t = (dx+1) + 3(dy+1) + 9(dz+1)) or 1 (1x1x1).
+ * cin, cout: multiples of 16 (cin <= 1024, cout <= 256).  bias may be NULL;
+ * relu != 0 applies max(0, .).  y (BF16) and/or yf (FP32) receive the result
+ * with row stride ldy elements (0: cout; otherwise a multiple of 8 >= cout),
+ * so that several calls can fill disjoint channel ranges of one tensor. */
+int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, const float* bias, void* y, float* yf,
+                    int32_t cout, int32_t ldy, int32_t nx, int32_t ny, int32_t nz, int32_t nb, uint32_t periodic,
+                    int32_t relu, unsigned* status, void* stream);
+
+/* dw[co][t][ci] += sum_v dy[v][co] x[v + off_t][ci] (FP32, accumulated with
+ * atomics; clear dw first).  Voxels are split into slices of vox_per_cta
+ * (multiple of 64) per CTA; cout a multiple of 16 up to 256. */
+int lbnn_conv3d_wgrad(const void* dy, int32_t cout, const void* x, int32_t cin, int32_t taps, float* dw, int32_t nx,
+                      int32_t ny, int32_t nz, int32_t nb, uint32_t periodic, int32_t vox_per_cta, unsigned* status,
+                      void* stream);
+
+/* ---- data movement and element-wise kernels ----------------------------- */
+/* fields [5][n] FP32 (phi, rho, ux, uy, uz) -> x[n][c] BF16 channels
+ * (phi, s_rho (rho - 1), s_u ux, s_u uy, s_u uz, 0 ...); c >= 5. */
+int lbnn_pack_input(const float* fields, int64_t n, int32_t c, float s_rho, float s_u, void* x, void* stream);
+/* out[5][n] = fields + (y0, y1/s_rho, y2/s_u, y3/s_u, y4/s_u), phi clamped to
+ * [-1, 1] and rho to >= rho_min; y[n][c] FP32 network output. */
+int lbnn_unpack_output(const float* fields, const float* y, int64_t n, int32_t c, float s_rho, float s_u,
+                       float rho_min, float* out, void* stream);
+/* t[n][c] FP32 = scaled increments (f1 - f0) in the channel order of pack_input. */
+int lbnn_pack_target(const float* f0, const float* f1, int64_t n, int32_t c, float s_rho, float s_u, float* t,
+                     void* stream);
+/* 2x2x2 average pooling (even extents) and its gradient (dx += dy/8, FP32). */
+int lbnn_avgpool2(const void* x, int32_t c, int32_t nx, int32_t ny, int32_t nz, int32_t nb, void* y, void* stream);
+int lbnn_avgpool2_bwd(const float* dy, int32_t c, int32_t nx, int32_t ny, int32_t nz, int32_t nb, float* dx,
+                      void* stream);
+/* out[v] = (skip[v] (cs channels), low[parent(v)] (cl channels)), nearest
+ * x2 upsampling of the half-resolution low; and its gradient (accumulating
+ * into dskip and dlow). nx, ny, nz: full-resolution extents. */
+int lbnn_up_concat(const void* skip, int32_t cs, const void* low, int32_t cl, int32_t nx, int32_t ny, int32_t nz,
+                   int32_t nb, void* out, void* stream);
+int lbnn_up_concat_bwd(const float* dout, int32_t cs, int32_t cl, int32_t nx, int32_t ny, int32_t nz, int32_t nb,
+                       float* dskip, float* dlow, void* stream);
+/* gradient through ReLU: g * (y > 0) (relu = 0: copy), to BF16 gb and/or FP32 gf. */
+int lbnn_relu_bwd(const float* g, const void* y, int64_t n, int32_t relu, void* gb, float* gf, void* stream);
+/* db[c] += sum_v g[v][c] (c divides 256). */
+int lbnn_bias_grad(const float* g, int64_t nvox, int32_t c, float* db, void* stream);
+/* weights of the input gradient: wt[ci][t][co] = w[co][taps-1-t][ci]. */
+int lbnn_flip_weights(const void* w, int32_t cout, int32_t taps, int32_t cin, void* wt, void* stream);
+/* weighted MSE over the first nch of c channels: grad = 2 w_c (p - t)/(n nch),
+ * *loss += sum w_c (p - t)^2/(n nch) (FP64). */
+int lbnn_mse(const float* p, const float* t, int64_t n, int32_t c, int32_t nch, const float* wch, float* grad,
+             double* loss, void* stream);
+/* Adam step (bias-corrected, step >= 1, decoupled weight decay wd) on FP32
+ * master weights p; bf (nullable) receives a BF16 copy. */
+int lbnn_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
+              int32_t step, float wd, void* bf, void* stream);
+int lbnn_f32_to_bf16(const float* a, int64_t n, void* b, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBNN_H */

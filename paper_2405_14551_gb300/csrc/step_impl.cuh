@@ -269,25 +269,45 @@ __device__ __forceinline__ void fields_node(const InitBuf& I, const Geo& g, cons
 // ---------------------------------------------------------------------------
 // pass 1: phase field
 // ---------------------------------------------------------------------------
-template <int ST>
-__global__ void __launch_bounds__(256) k_phi(View<ST> S, Geo g, typename Store<ST>::R* __restrict__ phi) {
+// pull_fast is defined with the fused step below
+template <int ST, bool WALLFREE, bool IDX32>
+__device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const Nbr& n, int self,
+                                          typename Store<ST>::R f[Q], typename Store<ST>::R& rA,
+                                          typename Store<ST>::R& rB);
+
+__device__ __forceinline__ bool near_wall(const Geo& g, int x, int y, int z) {
+  return (g.wx && (x <= 1 || x >= g.nx - 2)) || (g.wy && (y <= 1 || y >= g.ny - 2)) ||
+         (g.wz && (z <= 1 || z >= g.nz - 2));
+}
+
+// phase field of one node from its pulled populations
+template <int ST, bool IDX32>
+__device__ __forceinline__ void phi_node(const View<ST>& S, const Geo& g, long long idx,
+                                         typename Store<ST>::R* __restrict__ phi) {
   using R = typename Store<ST>::R;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
-    const int x = (int)(idx % g.nx);
-    const long long yz = idx / g.nx;
-    const int y = (int)(yz % g.ny);
-    const int z = (int)(yz / g.ny);
-    if (is_solid(g, x, y, z)) {
-      phi[idx] = R(0);
-      continue;
-    }
-    Nbr n;
-    make_nbr(g, x, y, z, n);
-    R f[Q], rA, rB;
-    pull_node<ST, false>(S, g, n, idx, f, rA, rB, nullptr, nullptr);
-    phi[idx] = (rA - rB) / (rA + rB);
+  const int x = (int)(idx % g.nx);
+  const long long yz = idx / g.nx;
+  const int y = (int)(yz % g.ny);
+  const int z = (int)(yz / g.ny);
+  if (is_solid(g, x, y, z)) {
+    phi[idx] = R(0);
+    return;
   }
+  Nbr n;
+  make_nbr(g, x, y, z, n);
+  R f[Q], rA, rB;
+  if (near_wall(g, x, y, z))
+    pull_fast<ST, false, IDX32>(S, g, n, (int)idx, f, rA, rB);
+  else
+    pull_fast<ST, true, IDX32>(S, g, n, (int)idx, f, rA, rB);
+  phi[idx] = (rA - rB) / (rA + rB);
+}
+
+template <int ST, bool IDX32>
+__global__ void __launch_bounds__(256) k_phi(View<ST> S, Geo g, typename Store<ST>::R* __restrict__ phi) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride)
+    phi_node<ST, IDX32>(S, g, idx, phi);
 }
 
 // ---------------------------------------------------------------------------
@@ -645,7 +665,7 @@ __device__ __forceinline__ int find_run(const RunDesc* runs, int nruns, long lon
   return lo;
 }
 
-template <int ST>
+template <int ST, bool IDX32>
 __global__ void __launch_bounds__(256) k_phi_batched(const RunDesc* __restrict__ runs, int nruns, long long nchunks,
                                                      int parity) {
   using R = typename Store<ST>::R;
@@ -654,20 +674,7 @@ __global__ void __launch_bounds__(256) k_phi_batched(const RunDesc* __restrict__
     const Geo g = runs[r].g;
     const long long idx = (c - runs[r].chunk_begin) * 256 + threadIdx.x;
     if (idx >= g.N) continue;
-    const int x = (int)(idx % g.nx);
-    const long long yz = idx / g.nx;
-    const int y = (int)(yz % g.ny);
-    const int z = (int)(yz / g.ny);
-    R* phi = reinterpret_cast<R*>(runs[r].phi);
-    if (is_solid(g, x, y, z)) {
-      phi[idx] = R(0);
-      continue;
-    }
-    Nbr n;
-    make_nbr(g, x, y, z, n);
-    R f[Q], rA, rB;
-    pull_node<ST, false>(view<ST>(runs[r].S[parity]), g, n, idx, f, rA, rB, nullptr, nullptr);
-    phi[idx] = (rA - rB) / (rA + rB);
+    phi_node<ST, IDX32>(view<ST>(runs[r].S[parity]), g, idx, reinterpret_cast<R*>(runs[r].phi));
   }
 }
 

@@ -21,8 +21,10 @@ cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream
   const long long blocks_needed = (g.N + 255) / 256;
   const long long cap = (long long)sm_count() * 8;
   const int blocks = (int)(blocks_needed < cap ? blocks_needed : cap);
-  trace_kernel("k_phi", k_phi<ST>, dim3(blocks), dim3(256), 0);
-  k_phi<ST><<<blocks, 256, 0, st>>>(view<ST>(in), g, reinterpret_cast<R*>(phi));
+  const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
+  auto kern = idx32 ? k_phi<ST, true> : k_phi<ST, false>;
+  trace_kernel("k_phi", kern, dim3(blocks), dim3(256), 0);
+  kern<<<blocks, 256, 0, st>>>(view<ST>(in), g, reinterpret_cast<R*>(phi));
   return cudaGetLastError();
 }
 
@@ -123,11 +125,12 @@ cudaError_t launch_batched_t(const RunDesc* d_runs, int nruns, long long nchunks
                              cudaStream_t st) {
   const int blocks = sm_count() * (blocks_per_sm > 0 ? blocks_per_sm : 2);
   const int pblocks = sm_count() * 8;
-  trace_kernel("k_phi_batched", k_phi_batched<ST>, dim3(pblocks), dim3(256), 0);
-  k_phi_batched<ST><<<pblocks, 256, 0, st>>>(d_runs, nruns, nchunks, parity);
+  const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)max_nodes < (1ull << 32);
+  auto pk = idx32 ? k_phi_batched<ST, true> : k_phi_batched<ST, false>;
+  trace_kernel("k_phi_batched", pk, dim3(pblocks), dim3(256), 0);
+  pk<<<pblocks, 256, 0, st>>>(d_runs, nruns, nchunks, parity);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)max_nodes < (1ull << 32);
   if (idx32) return launch_batched_tiles<ST, true>(tile, d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
   return launch_batched_tiles<ST, false>(tile, d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
 }

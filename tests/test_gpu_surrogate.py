@@ -1,0 +1,139 @@
+"""The surrogate's tensor-core kernels and network against the FP64 numpy
+reference (oracle/unet_ref.py).
+
+* conv forward (3x3x3 and 1x1x1, periodic and zero padding, channel counts up
+  to 384 in and 256 out) and weight gradient vs numpy on BF16-rounded
+  inputs: FP32 accumulation, so the error is summation order (rel 1e-5);
+* the whole U-Net (base width 16 on 16^3 voxels): output and every weight
+  gradient vs the FP64 reference evaluated with the same BF16 weights and
+  input; activations pass through BF16 between layers, so the bound is a
+  relative L2 error of 4e-2 (BF16 carries 8 significant bits);
+* a few Adam steps on one pair lower the loss.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import unet_ref as U
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf(a):
+    import torch
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("dims,cin,cout,taps,per,relu", [
+    ((8, 4, 4, 1), 16, 16, 1, 7, 0), ((8, 4, 4, 1), 16, 16, 27, 7, 0), ((8, 8, 4, 2), 32, 32, 27, 2, 1),
+    ((16, 8, 4, 1), 64, 64, 27, 5, 1), ((8, 4, 8, 1), 96, 32, 27, 7, 0), ((8, 4, 4, 1), 384, 128, 27, 5, 1),
+    ((8, 4, 4, 1), 128, 256, 27, 0, 1), ((9, 5, 3, 1), 32, 48, 27, 7, 0)])
+def test_conv_forward(dims, cin, cout, taps, per, relu):
+    import torch
+    import paper_2405_14551_gb300.lbcg as L
+    lib = L.load_library()
+    rng = np.random.default_rng(cin * 7 + cout)
+    nx, ny, nz, nb = dims
+    X = _bf(rng.standard_normal((nb, nz, ny, nx, cin)))
+    W = _bf(rng.standard_normal((cout, taps, cin)) / np.sqrt(taps * cin))
+    b = rng.standard_normal(cout).astype(np.float32)
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).to(dev)
+    Wd = torch.from_numpy(W.astype(np.float32)).to(torch.bfloat16).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    Yf = torch.zeros((nb, nz, ny, nx, cout), dtype=torch.float32, device=dev)
+    st = torch.zeros(4, dtype=torch.int32, device=dev)
+    rc = lib.lbnn_conv3d_fwd(Xd.data_ptr(), cin, Wd.data_ptr(), taps, bd.data_ptr(), None, Yf.data_ptr(), cout, 0,
+                             nx, ny, nz, nb, per, relu, st.data_ptr(), None)
+    assert rc == 0, lib.lb_last_error()
+    torch.cuda.synchronize()
+    ref = U.conv3d(X, W, b.astype(np.float64), (per & 1, (per >> 1) & 1, (per >> 2) & 1), taps)
+    if relu:
+        ref = np.maximum(ref, 0)
+    assert int(st[0].item()) == 0
+    assert np.abs(Yf.cpu().numpy() - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dims,cin,cout,taps,per,vpc", [
+    ((8, 4, 4, 1), 16, 16, 1, 7, 64), ((8, 4, 4, 1), 16, 32, 27, 7, 64), ((8, 8, 8, 1), 32, 64, 27, 5, 128),
+    ((8, 4, 8, 2), 96, 32, 27, 2, 64), ((8, 4, 4, 1), 128, 256, 27, 5, 64)])
+def test_conv_weight_gradient(dims, cin, cout, taps, per, vpc):
+    import torch
+    import paper_2405_14551_gb300.lbcg as L
+    lib = L.load_library()
+    rng = np.random.default_rng(cin + 3 * cout)
+    nx, ny, nz, nb = dims
+    X = _bf(rng.standard_normal((nb, nz, ny, nx, cin)))
+    G = _bf(rng.standard_normal((nb, nz, ny, nx, cout)))
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).to(dev)
+    Gd = torch.from_numpy(G.astype(np.float32)).to(torch.bfloat16).to(dev)
+    dW = torch.zeros((cout, taps, cin), dtype=torch.float32, device=dev)
+    st = torch.zeros(4, dtype=torch.int32, device=dev)
+    rc = lib.lbnn_conv3d_wgrad(Gd.data_ptr(), cout, Xd.data_ptr(), cin, taps, dW.data_ptr(), nx, ny, nz, nb, per, vpc,
+                               st.data_ptr(), None)
+    assert rc == 0, lib.lb_last_error()
+    torch.cuda.synchronize()
+    _, ref, _ = U.conv3d_backward(X, np.zeros((cout, taps, cin)), G, (per & 1, (per >> 1) & 1, (per >> 2) & 1), taps)
+    assert int(st[0].item()) == 0
+    assert np.abs(dW.cpu().numpy() - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(1e-30, np.linalg.norm(np.ravel(b))))
+
+
+def test_unet_forward_and_gradients_match_reference():
+    import torch
+    from paper_2405_14551_gb300 import surrogate as S
+    rng = np.random.default_rng(5)
+    net = S.UNet(base=16, seed=3)
+    specs = U.layer_specs(cin=16, base=16, cout=16)
+    params = {}
+    for name, ci, co, taps, relu in specs:
+        w = _bf(rng.standard_normal((co, taps, ci)) * np.sqrt(2.0 / (taps * ci)))
+        b = 0.05 * rng.standard_normal(co)
+        params[name] = (w, b)
+    net.load_parameters(params)
+    shape = (16, 16, 16, 1)
+    x = _bf(rng.standard_normal((1, 16, 16, 16, 16)))
+    t = rng.standard_normal((1, 16, 16, 16, 16))
+    dev = torch.device("cuda")
+    xd = torch.from_numpy(x.reshape(-1, 16).astype(np.float32)).to(torch.bfloat16).to(dev)
+    y = net.forward(xd, shape)
+    per = (1, 0, 1)
+    yr, cache = U.forward(params, x, per, specs)
+    yg = y.cpu().numpy().reshape(yr.shape)
+    assert _rel(yg, yr) < 4e-2
+    loss, gy = U.mse(yr, t, 5, np.ones(16))
+    gyd = torch.from_numpy(gy.reshape(-1, 16).astype(np.float32)).to(dev)
+    net.backward(gyd)
+    torch.cuda.synchronize()
+    net.check_status()
+    grads = U.backward(params, cache, gy, per, specs)
+    for name in grads:
+        gw = net.gw[name].cpu().numpy()
+        gb = net.gb[name].cpu().numpy()
+        assert _rel(gw, grads[name][0]) < 4e-2, name
+        assert _rel(gb, grads[name][1]) < 4e-2, name
+
+
+def test_training_lowers_the_loss():
+    import torch
+    from paper_2405_14551_gb300 import surrogate as S
+    torch.manual_seed(0)
+    shape = (32, 32, 32)
+    rng = np.random.default_rng(0)
+    dev = torch.device("cuda")
+    f0 = torch.zeros((5, 32 * 32 * 32), dtype=torch.float32, device=dev)
+    z, yy, xx = np.meshgrid(np.arange(32), np.arange(32), np.arange(32), indexing="ij")
+    phi0 = np.tanh((8 - np.sqrt((xx - 16) ** 2 + (yy - 16) ** 2 + (z - 14) ** 2)) / 1.5)
+    phi1 = np.tanh((8 - np.sqrt((xx - 16) ** 2 + (yy - 16) ** 2 + (z - 16) ** 2)) / 1.5)
+    f0[0] = torch.from_numpy(phi0.reshape(-1).astype(np.float32))
+    f0[1] = 1.0
+    f1 = f0.clone()
+    f1[0] = torch.from_numpy(phi1.reshape(-1).astype(np.float32))
+    net = S.UNet(base=16, seed=1)
+    hist = S.train(net, [[f0, f1]], shape, iters=40, lr=2e-3, log_every=39)
+    assert hist[-1][1] < 0.5 * hist[0][1], hist

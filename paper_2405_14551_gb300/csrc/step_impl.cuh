@@ -387,11 +387,29 @@ __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const
   }
 }
 
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32>
+// Colour gradients of the tile's own nodes, computed once into shared memory
+// (gt[k][lz][ty][tx], k = x, y, z) so that near-contact scans whose target
+// lies inside the tile read them instead of recomputing them.
+template <typename R, int TX, int TY, int TZ, bool WALLFREE>
+__device__ __forceinline__ void own_grad_fill(const R* sp, R* gt, int H, int SX, int SXY) {
+  for (int lz = 0; lz < TZ; ++lz) {
+    const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + H);
+    R gr[3];
+    tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
+    const int o = (lz * TY + threadIdx.y) * TX + threadIdx.x;
+    gt[o] = gr[0];
+    gt[TX * TY * TZ + o] = gr[1];
+    gt[2 * TX * TY * TZ + o] = gr[2];
+  }
+}
+
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32, bool GT>
 __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O, const InitBuf& init, const Geo& g,
                                            const Phys& P, typename Store<ST>::R* __restrict__ fields,
-                                           unsigned* __restrict__ status, const typename Store<ST>::R* sp, int H,
+                                           unsigned* __restrict__ status, const typename Store<ST>::R* sp,
+                                           const typename Store<ST>::R* gt, int H,
                                            int SX, int SXY, int x0, int y0, int z0) {
+  constexpr int TN = TX * TY * TZ;
   using R = typename Store<ST>::R;
   using I = typename std::conditional<IDX32, unsigned, size_t>::type;
   const R tau_a = R(P.tau_a), tau_b = R(P.tau_b);
@@ -430,11 +448,18 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       if (cz(p)) j2 += R(cz(p)) * d;
     }
 
-    // colour gradient from the tile
+    // colour gradient from the tile (or from the tile's gradient cache)
     const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + H);
     const R phx = sp[c];
     R gr[3];
-    tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
+    if constexpr (GT) {
+      const int o = (lz * TY + threadIdx.y) * TX + threadIdx.x;
+      gr[0] = gt[o];
+      gr[1] = gt[TN + o];
+      gr[2] = gt[2 * TN + o];
+    } else {
+      tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
+    }
     const R gg = rsqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
 
     // near-contact scan (Eqs. stress_jump, near_cont_force): from an interface
@@ -459,7 +484,18 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
         const R phy = sp[cy_];
         if (!(fabs(phy) < phi_I)) continue;
         R gy_[3];
-        tile_grad<R, WALLFREE>(sp, cy_, SX, SXY, gy_);
+        bool cached = false;
+        if constexpr (GT) {
+          const int tx = (int)threadIdx.x + dx, ty = (int)threadIdx.y + dy, tz = lz + dz;
+          if ((unsigned)tx < (unsigned)TX && (unsigned)ty < (unsigned)TY && (unsigned)tz < (unsigned)TZ) {
+            const int o = (tz * TY + ty) * TX + tx;
+            gy_[0] = gt[o];
+            gy_[1] = gt[TN + o];
+            gy_[2] = gt[2 * TN + o];
+            cached = true;
+          }
+        }
+        if (!cached) tile_grad<R, WALLFREE>(sp, cy_, SX, SXY, gy_);
         const R gm2 = gy_[0] * gy_[0] + gy_[1] * gy_[1] + gy_[2] * gy_[2];
         if (gm2 < R(NC_GRAD_MIN) * R(NC_GRAD_MIN)) continue;
         const R dot = gr[0] * gy_[0] + gr[1] * gy_[1] + gr[2] * gy_[2];
@@ -622,19 +658,36 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
   }
   // a tile whose halo holds no solid node needs no bounce-back or wall tests
   const bool wallfree = !__syncthreads_or(any_solid);
-  if (wallfree)
-    step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32>(S, O, init, g, P, fields, status, sp, H, SX, SXY, x0, y0,
-                                                          z0);
-  else
-    step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32>(S, O, init, g, P, fields, status, sp, H, SX, SXY, x0,
-                                                           y0, z0);
+  if (P.A_h != 0.0) {
+    // near contact: the tile's own gradients are cached for the scan
+    R* gt = sp + (size_t)SXY * SZ;
+    if (wallfree) own_grad_fill<R, TX, TY, TZ, true>(sp, gt, H, SX, SXY);
+    else own_grad_fill<R, TX, TY, TZ, false>(sp, gt, H, SX, SXY);
+    __syncthreads();
+    if (wallfree)
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, true>(S, O, init, g, P, fields, status, sp, gt, H, SX,
+                                                                    SXY, x0, y0, z0);
+    else
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, true>(S, O, init, g, P, fields, status, sp, gt, H, SX,
+                                                                     SXY, x0, y0, z0);
+  } else {
+    if (wallfree)
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, false>(S, O, init, g, P, fields, status, sp, nullptr, H,
+                                                                     SX, SXY, x0, y0, z0);
+    else
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, false>(S, O, init, g, P, fields, status, sp, nullptr,
+                                                                      H, SX, SXY, x0, y0, z0);
+  }
   __syncthreads();
 }
 
-// Shared memory of one fused-step tile: the phi tile with halo H.
+// Shared memory of one fused-step tile: the phi tile with halo H and, with
+// near contact (H > 1), the gradient cache of the tile's own nodes.
 template <typename R>
 inline size_t step_smem_bytes(int TX, int TY, int TZ, int H) {
-  return sizeof(R) * (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
+  size_t n = (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
+  if (H > 1) n += 3 * (size_t)TX * TY * TZ;
+  return sizeof(R) * n;
 }
 
 template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32, int MINB = 2>

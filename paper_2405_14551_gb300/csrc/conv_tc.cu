@@ -320,17 +320,25 @@ __global__ void __launch_bounds__(128, 1)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// Dynamic shared memory of a conv CTA: the staged operands, rounded up to a
-// floor of 200 KiB so that every address a descriptor can form from the
-// staged tiles' strides lies inside the CTA's allocation.
-constexpr size_t CONV_SMEM_FLOOR = 200 * 1024;
+// Dynamic shared memory of a conv CTA: the staged operands, raised where
+// needed so that no more CTAs share an SM than their tensor-memory
+// allocations (ncols columns each, 512 per SM) fit side by side; an
+// allocation therefore never waits for another CTA's columns.
+static size_t conv_smem(size_t need, int cout) {
+  int ncols = 32;
+  while (ncols < cout) ncols <<= 1;
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int kmax = 512 / ncols;
+  const size_t floor_bytes = (size_t)per_sm / (size_t)(kmax + 1) + 64;  // kmax + 1 CTAs exceed the SM
+  return need > floor_bytes ? need : floor_bytes;
+}
 static size_t conv_fwd_smem(int Cout, int KC) {
-  const size_t need = 2 * (size_t)CONV_M * KC * 2 + 2 * (size_t)Cout * KC * 2 + 64;
-  return need > CONV_SMEM_FLOOR ? need : CONV_SMEM_FLOOR;
+  return conv_smem(2 * (size_t)CONV_M * KC * 2 + 2 * (size_t)Cout * KC * 2 + 64, Cout);
 }
 static size_t conv_wgrad_smem(int Cout) {
-  const size_t need = 2 * (size_t)CONV_M * 64 * 2 + 2 * (size_t)Cout * 64 * 2 + 64;
-  return need > CONV_SMEM_FLOOR ? need : CONV_SMEM_FLOOR;
+  return conv_smem(2 * (size_t)CONV_M * 64 * 2 + 2 * (size_t)Cout * 64 * 2 + 64, Cout);
 }
 
 static int pick_kc(int Cin) {

@@ -28,7 +28,7 @@ struct Phys {
   double phi_I;
   double g[3];
   int g_mode;
-  int halo;   // phi tile halo: 1 without near-contact, K + 1 with it
+  int halo;   // phi tile halo of the near-contact pass: K + 1 (1 without near contact)
 };
 
 // Device pointers of one population lattice.  Two-set storage: f holds
@@ -56,6 +56,7 @@ struct RunDesc {
   Phys p;
   StateBuf S[2];
   void* phi;
+  unsigned char* hnc;  // near-contact distance per node
   int tiles_x, tiles_y, tiles_z;
   long long tile_begin;   // first work item of this run in the step list
   long long chunk_begin;  // first 256-node chunk of this run in the phase-field list
@@ -76,17 +77,23 @@ bool storage_is_f64(int storage);
 // --- step_kernels.cu -------------------------------------------------------
 // phase-field pass: phi[N] (float, or double for FP64 storage) from pulled populations
 cudaError_t launch_phi(int storage, const Geo& g, const StateBuf& in, void* phi, cudaStream_t st);
+// near-contact pass: hnc[N] from phi; launches nothing when p.A_h == 0.
+// variant indexes the near-contact tile shapes (kNcTiles).
+cudaError_t launch_nc(int storage, int variant, const Geo& g, const Phys& p, const void* phi, unsigned char* hnc,
+                      cudaStream_t st);
+constexpr int NUM_NC_VARIANTS = 4;
 // fused step; tile index into kTiles (only tile 0 for non-hot variants)
 cudaError_t launch_step(int storage, int loader, bool write_state, bool write_fields, int tile, const Geo& g,
-                        const Phys& p, const StateBuf& in, const InitBuf& init, const void* phi, StateBuf out,
-                        void* fields, unsigned* status, cudaStream_t st);
+                        const Phys& p, const StateBuf& in, const InitBuf& init, const void* phi,
+                        const unsigned char* hnc, StateBuf out, void* fields, unsigned* status, cudaStream_t st);
 // export pre-collision populations of a box, canonical order, as double
 cudaError_t launch_export(int storage, int loader, const Geo& g, const Phys& p, const StateBuf& in,
                           const InitBuf& init, int x0, int y0, int z0, int bx, int by, int bz, double* outA,
                           double* outB, cudaStream_t st);
 
-// batched step over runs[0..nruns): phase-field pass then fused pass, each a
-// persistent launch of blocks_per_sm x SMs CTAs; parity selects S[parity] as input
+// batched step over runs[0..nruns): phase-field pass, near-contact pass (when
+// halo_max > 1, i.e. some run has A_h != 0) and fused pass, each a persistent
+// launch of blocks_per_sm x SMs CTAs; parity selects S[parity] as input
 cudaError_t launch_batched(int storage, const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles,
                            int tile, int halo_max, long long max_nodes, int parity, int blocks_per_sm,
                            unsigned* status, cudaStream_t st);

@@ -83,6 +83,7 @@ struct lb_handle {
   StateBuf S[2]{};
   int cur = 0;
   void* phi = nullptr;      // R[N]
+  unsigned char* hnc = nullptr;  // near-contact distance per node (A_h != 0 only)
   float* init_phi = nullptr;
   float* init_rho = nullptr;
   float* init_u = nullptr;
@@ -97,6 +98,7 @@ struct lb_handle {
   bool initialised = false;
   int64_t t = 0;
   int tile = 0;
+  int nc_tile = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
@@ -195,17 +197,26 @@ int validate(const lb_grid* gr, const lb_params* p) {
   return LB_OK;
 }
 
+// Near-contact pass on the current phi (nothing without near contact).
+cudaError_t issue_nc(lb_handle* h) {
+  if (h->p.A_h == 0.0) return cudaSuccess;
+  g_launches += 1;
+  return launch_nc(h->storage, h->nc_tile, h->g, h->p, h->phi, h->hnc, h->stream);
+}
+
 // Issue one step (no graph).
 int issue_step(lb_handle* h) {
   const int nxt = h->cur ^ 1;
   if (h->mode == 0) {
+    LB_CUDA(issue_nc(h));
     LB_CUDA(launch_step(h->storage, LOAD_FIELDS, true, false, 0, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->S[nxt], nullptr, h->status, h->stream));
+                        h->hnc, h->S[nxt], nullptr, h->status, h->stream));
     g_launches += 1;
   } else {
     LB_CUDA(launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream));
+    LB_CUDA(issue_nc(h));
     LB_CUDA(launch_step(h->storage, LOAD_PULL, true, false, h->tile, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->S[nxt], nullptr, h->status, h->stream));
+                        h->hnc, h->S[nxt], nullptr, h->status, h->stream));
     g_launches += 2;
   }
   h->cur = nxt;
@@ -251,13 +262,15 @@ int compute_fields(lb_handle* h) {
   int rc = ensure_fields(h);
   if (rc) return rc;
   if (h->mode == 0) {
+    LB_CUDA(issue_nc(h));
     LB_CUDA(launch_step(h->storage, LOAD_FIELDS, false, true, 0, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->S[h->cur ^ 1], h->fields, h->status, h->stream));
+                        h->hnc, h->S[h->cur ^ 1], h->fields, h->status, h->stream));
     g_launches += 1;
   } else {
     LB_CUDA(launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream));
+    LB_CUDA(issue_nc(h));
     LB_CUDA(launch_step(h->storage, LOAD_PULL, false, true, 0, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->S[h->cur ^ 1], h->fields, h->status, h->stream));
+                        h->hnc, h->S[h->cur ^ 1], h->fields, h->status, h->stream));
     g_launches += 2;
   }
   return LB_OK;
@@ -337,6 +350,7 @@ int lb_create(const lb_grid* grid, const lb_params* params, const lb_alloc* allo
   const size_t N = (size_t)h->g.N;
   bool ok = alloc_state(h, h->S[0]) && alloc_state(h, h->S[1]);
   ok = ok && (h->phi = dev_alloc(h, N * real_bytes(h->storage))) != nullptr;
+  if (h->p.A_h != 0.0) ok = ok && (h->hnc = (unsigned char*)dev_alloc(h, N)) != nullptr;
   ok = ok && (h->init_phi = (float*)dev_alloc(h, N * sizeof(float))) != nullptr;
   ok = ok && (h->red = (double*)dev_alloc(h, ((size_t)reduce_blocks(h->g.N) * 8 + 16) * sizeof(double))) != nullptr;
   ok = ok && (h->status = (unsigned*)dev_alloc(h, 256)) != nullptr;
@@ -475,37 +489,50 @@ int lb_step_timed(lb_handle* h, int64_t nsteps, double* ms) {
   if (!h->initialised) return set_err(LB_ESTATE, "handle not initialised");
   int rc;
   if (h->mode == 0 && (rc = issue_step(h))) return rc;
-  std::vector<cudaEvent_t> ev((size_t)(3 * nsteps));
+  std::vector<cudaEvent_t> ev((size_t)(4 * nsteps));
   for (auto& e : ev) LB_CUDA(cudaEventCreate(&e));
   cudaError_t err = cudaSuccess;
   for (int64_t k = 0; k < nsteps && err == cudaSuccess; ++k) {
     const int nxt = h->cur ^ 1;
-    cudaEventRecord(ev[3 * k], h->stream);
+    cudaEventRecord(ev[4 * k], h->stream);
     err = launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream);
-    cudaEventRecord(ev[3 * k + 1], h->stream);
+    cudaEventRecord(ev[4 * k + 1], h->stream);
+    if (err == cudaSuccess) err = issue_nc(h);
+    cudaEventRecord(ev[4 * k + 2], h->stream);
     if (err == cudaSuccess)
       err = launch_step(h->storage, LOAD_PULL, true, false, h->tile, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->S[nxt], nullptr, h->status, h->stream);
-    cudaEventRecord(ev[3 * k + 2], h->stream);
+                        h->hnc, h->S[nxt], nullptr, h->status, h->stream);
+    cudaEventRecord(ev[4 * k + 3], h->stream);
     g_launches += 2;
     h->cur = nxt;
     h->t += 1;
   }
   if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
-  double s0 = 0, s1 = 0;
+  double s[3] = {0, 0, 0};
   for (int64_t k = 0; k < nsteps && err == cudaSuccess; ++k) {
-    float a = 0, b = 0;
-    err = cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]);
-    if (err == cudaSuccess) err = cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]);
-    s0 += a;
-    s1 += b;
+    for (int j = 0; j < 3 && err == cudaSuccess; ++j) {
+      float a = 0;
+      err = cudaEventElapsedTime(&a, ev[4 * k + j], ev[4 * k + j + 1]);
+      s[j] += a;
+    }
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (err != cudaSuccess) return cuda_err(err, "lb_step_timed");
-  ms[0] = s0 / (double)nsteps;
-  ms[1] = s1 / (double)nsteps;
+  ms[0] = s[0] / (double)nsteps;  // phase field
+  ms[1] = s[2] / (double)nsteps;  // fused step
+  ms[2] = s[1] / (double)nsteps;  // near-contact scan
   return LB_OK;
 }
+
+int lb_set_nc_tile(lb_handle* h, int variant) {
+  if (!h) return set_err(LB_EINVAL, "null handle");
+  if (variant < 0 || variant >= NUM_NC_VARIANTS) return set_err(LB_EINVAL, "near-contact tile index out of range");
+  if (variant != h->nc_tile) drop_graphs(h);
+  h->nc_tile = variant;
+  return LB_OK;
+}
+
+int lb_get_nc_tile(const lb_handle* h) { return h ? h->nc_tile : -1; }
 
 int lb_set_tile(lb_handle* h, int tile) {
   if (!h) return set_err(LB_EINVAL, "null handle");
@@ -788,6 +815,7 @@ int batch_descriptors(lb_batch* b) {
     d.S[0] = h->S[0];
     d.S[1] = h->S[1];
     d.phi = h->phi;
+    d.hnc = h->hnc;
     d.tiles_x = (h->g.nx + T.tx - 1) / T.tx;
     d.tiles_y = (h->g.ny + T.ty - 1) / T.ty;
     d.tiles_z = (h->g.nz + T.tz - 1) / T.tz;
@@ -810,7 +838,7 @@ int batch_descriptors(lb_batch* b) {
 int batch_issue(lb_batch* b, int parity) {
   LB_CUDA(launch_batched(b->storage, b->d_runs, (int)b->runs.size(), b->nchunks, b->ntiles, b->tile, b->halo_max,
                          b->max_nodes, parity, b->blocks_per_sm, b->runs[0]->status, b->stream));
-  g_launches += 2;
+  g_launches += b->halo_max > 1 ? 3 : 2;
   return LB_OK;
 }
 

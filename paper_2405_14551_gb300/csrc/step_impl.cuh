@@ -2,20 +2,24 @@
 // Device code of the fused time step of the two-component colour-gradient LB scheme on D3Q27
 // (arXiv 2405.14551, Sec. III.B-III.D) for sm_103a.
 //
-// A step is two passes over the population lattice:
+// A step is three passes over the lattice:
 //   1. k_phi: pull the populations of every node and write its phase field
 //      phi = (rhoA - rhoB)/(rhoA + rhoB) (Eq. order_param) to a side array.
 //      The colour gradient and the near-contact scan of a node need phi of
 //      the current time level up to h_max + 1 nodes away, which exists only
 //      after every neighbour has been pulled; this pass provides it.
-//   2. k_step: per CTA a tile of (TX x TY x TZ) nodes stages phi of the tile
-//      plus a halo in shared memory; every thread then pulls the 27 (x2)
-//      populations of its node (periodic wrap, halfway bounce-back at solid
-//      neighbours, Sec. III.D), takes the moments, the colour gradient from
-//      the tile, runs the near-contact scan along the outward normal in the
-//      tile, forms the Guo-shifted velocity, relaxes the total populations
-//      (BGK), adds the perturbation Omega^(2) and the forcing source,
-//      recolours (Eqs. ome3_1/2) and stores the post-collision state once.
+//   2. k_nc (only with near contact, A_h != 0): per CTA a tile of phi plus a
+//      halo of K + 1 nodes in shared memory; every interface node scans along
+//      its outward normal (Eqs. stress_jump, near_cont_force) and the found
+//      distance h (0: none) is written as one byte per node.
+//   3. k_step: per CTA a tile of (TX x TY x TZ) nodes stages phi of the tile
+//      plus a one-node halo in shared memory; every thread then pulls the 27
+//      (x2) populations of its node (periodic wrap, halfway bounce-back at
+//      solid neighbours, Sec. III.D), takes the moments, the colour gradient
+//      from the tile, the repulsion from h, forms the Guo-shifted velocity,
+//      relaxes the total populations (BGK), adds the perturbation Omega^(2)
+//      and the forcing source, recolours (Eqs. ome3_1/2) and stores the
+//      post-collision state once.
 // Populations are structure-of-arrays [dir][z][y][x]: for a fixed direction
 // consecutive threads read consecutive addresses (coalesced).
 #include <cstdio>
@@ -96,8 +100,8 @@ __device__ __forceinline__ typename Store<ST>::E encode(typename Store<ST>::R v,
   }
 }
 
-__device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
-__device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
+__device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
+__device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
 __device__ __forceinline__ float round_(float v) { return roundf(v); }  // half away from zero
 __device__ __forceinline__ double round_(double v) { return round(v); }
 __device__ __forceinline__ bool finite_(float v) { return isfinite(v); }
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(256) k_phi(View<ST> S, Geo g, typename Store<S
 }
 
 // ---------------------------------------------------------------------------
-// pass 2: fused step
+// passes 2 and 3: near-contact scan and fused step
 // ---------------------------------------------------------------------------
 // Colour gradient grad phi(p) = (1/cs2) sum_i w_i c_i phi(p + c_i) on the
 // shared tile; a solid neighbour contributes phi(p) (neutral wetting).  Tiles
@@ -403,17 +407,170 @@ __device__ __forceinline__ void own_grad_fill(const R* sp, R* gt, int H, int SX,
   }
 }
 
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32, bool GT>
-__device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O, const InitBuf& init, const Geo& g,
-                                           const Phys& P, typename Store<ST>::R* __restrict__ fields,
-                                           unsigned* __restrict__ status, const typename Store<ST>::R* sp,
-                                           const typename Store<ST>::R* gt, int H,
-                                           int SX, int SXY, int x0, int y0, int z0) {
+// Near-contact scan of one interface node (Eqs. stress_jump, near_cont_force):
+// step along the outward normal n_out = -grad phi/|grad phi| by round(k n_out),
+// k = 1..K; the first target that is an interface node (|phi| < phi_I,
+// |grad phi| >= NC_GRAD_MIN) with a normal antiparallel to the node's own
+// gives h = k; 0 when there is none.  The scan stops at a wall layer.  sp is
+// the phi tile with halo H >= K + 1, c the node's tile index, (tx, ty, tz)
+// its place among the tile's own nodes, gr and gg = |gr| its gradient.
+template <typename R, int TX, int TY, int TZ, bool WALLFREE, bool GT>
+__device__ __forceinline__ int nc_scan(const R* sp, const R* gt, int c, int tx, int ty, int tz, int x, int y, int z,
+                                       const Geo& g, const Phys& P, int SX, int SXY, const R gr[3], R gg) {
   constexpr int TN = TX * TY * TZ;
+  const R phi_I = R(P.phi_I);
+  const R inv = R(-1) / gg;
+  const R no0 = gr[0] * inv, no1 = gr[1] * inv, no2 = gr[2] * inv;
+  for (int k = 1; k <= P.K; ++k) {
+    // |n_out| = 1, so |d| <= k <= K < halo; the clamp also covers non-finite normals
+    const int dx = max(-k, min(k, (int)round_(R(k) * no0)));
+    const int dy = max(-k, min(k, (int)round_(R(k) * no1)));
+    const int dz = max(-k, min(k, (int)round_(R(k) * no2)));
+    if constexpr (!WALLFREE) {
+      if (g.wx && (x + dx <= 0 || x + dx >= g.nx - 1)) break;
+      if (g.wy && (y + dy <= 0 || y + dy >= g.ny - 1)) break;
+      if (g.wz && (z + dz <= 0 || z + dz >= g.nz - 1)) break;
+    }
+    const int ct = c + dx + SX * dy + SXY * dz;
+    const R pt = sp[ct];
+    if (!(fabs(pt) < phi_I)) continue;
+    R gt_[3];
+    bool cached = false;
+    if constexpr (GT) {
+      const int ux = tx + dx, uy = ty + dy, uz = tz + dz;
+      if ((unsigned)ux < (unsigned)TX && (unsigned)uy < (unsigned)TY && (unsigned)uz < (unsigned)TZ) {
+        const int o = (uz * TY + uy) * TX + ux;
+        gt_[0] = gt[o];
+        gt_[1] = gt[TN + o];
+        gt_[2] = gt[2 * TN + o];
+        cached = true;
+      }
+    }
+    if (!cached) tile_grad<R, WALLFREE>(sp, ct, SX, SXY, gt_);
+    const R gm2 = gt_[0] * gt_[0] + gt_[1] * gt_[1] + gt_[2] * gt_[2];
+    if (gm2 < R(NC_GRAD_MIN) * R(NC_GRAD_MIN)) continue;
+    const R dot = gr[0] * gt_[0] + gr[1] * gt_[1] + gr[2] * gt_[2];
+    if (dot < -R(NC_COS_TOL) * gg * sqrt_(gm2)) return k;
+  }
+  return 0;
+}
+
+// Stage phi of a tile (TX x TY x SZ - 2H own nodes) plus a halo of H nodes
+// in shared memory, one (y, z) row per thread row: solid and beyond-wall
+// nodes get the marker PHI_SOLID; periodic axes wrap.  Returns (to every
+// thread) whether the staged block holds no solid node.
+template <typename R, int TX, int TY>
+__device__ __forceinline__ bool stage_phi(const R* __restrict__ phi, const Geo& g, int H, int SZ, R* sp, int x0,
+                                          int y0, int z0) {
+  const int SX = TX + 2 * H, SY = TY + 2 * H;
+  const int SXY = SX * SY;
+  bool any_solid = false;
+  for (int row = threadIdx.y; row < SY * SZ; row += TY) {
+    const int ly = row % SY, lz = row / SY;
+    int gy = y0 - H + ly, gz = z0 - H + lz;
+    bool rsolid = false;
+    if (g.wy) rsolid |= (gy <= 0 || gy >= g.ny - 1);
+    else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
+    if (g.wz) rsolid |= (gz <= 0 || gz >= g.nz - 1);
+    else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
+    const long long rbase = (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
+    R* srow = sp + (size_t)lz * SXY + (size_t)ly * SX;
+    for (int lx = threadIdx.x; lx < SX; lx += TX) {
+      int gx = x0 - H + lx;
+      bool solid = rsolid;
+      if (g.wx) solid |= (gx <= 0 || gx >= g.nx - 1);
+      else if ((unsigned)gx >= (unsigned)g.nx) gx = ((gx % g.nx) + g.nx) % g.nx;
+      any_solid |= solid;
+      srow[lx] = solid ? R(PHI_SOLID) : phi[rbase + gx];
+    }
+  }
+  return !__syncthreads_or(any_solid);
+}
+
+template <typename R, int TX, int TY, int TZ, bool WALLFREE, bool GT>
+__device__ __forceinline__ void nc_nodes(const R* sp, const R* gt, int H, const Geo& g, const Phys& P,
+                                         unsigned char* __restrict__ hout, int x0, int y0, int z0) {
+  const int SX = TX + 2 * H, SXY = SX * (TY + 2 * H);
+  const R phi_I = R(P.phi_I);
+  for (int lz = 0; lz < TZ; ++lz) {
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
+    if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
+    const int self = x + g.nx * (y + g.ny * z);
+    const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + H);
+    const R phx = sp[c];  // PHI_SOLID on solid nodes: never an interface node
+    int h = 0;
+    if (fabs(phx) < phi_I) {
+      R gr[3];
+      if constexpr (GT) {
+        const int o = (lz * TY + threadIdx.y) * TX + threadIdx.x;
+        gr[0] = gt[o];
+        gr[1] = gt[TX * TY * TZ + o];
+        gr[2] = gt[2 * TX * TY * TZ + o];
+      } else {
+        tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
+      }
+      const R gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+      if (gg >= R(NC_GRAD_MIN))
+        h = nc_scan<R, TX, TY, TZ, WALLFREE, GT>(sp, gt, c, threadIdx.x, threadIdx.y, lz, x, y, z, g, P, SX, SXY, gr,
+                                                 gg);
+    }
+    hout[self] = (unsigned char)h;
+  }
+}
+
+// One tile of the near-contact pass.  Ends with a barrier, so the caller may
+// reuse the shared tile.
+template <typename R, int TX, int TY, int TZ, bool GT>
+__device__ __forceinline__ void nc_tile(const R* __restrict__ phi, const Geo& g, const Phys& P,
+                                        unsigned char* __restrict__ hout, R* sp, int x0, int y0, int z0) {
+  const int H = P.halo;
+  const int SZ = TZ + 2 * H;
+  const bool wallfree = stage_phi<R, TX, TY>(phi, g, H, SZ, sp, x0, y0, z0);
+  R* gt = sp + (size_t)(TX + 2 * H) * (TY + 2 * H) * SZ;
+  const int SX = TX + 2 * H, SXY = SX * (TY + 2 * H);
+  if constexpr (GT) {
+    if (wallfree) own_grad_fill<R, TX, TY, TZ, true>(sp, gt, H, SX, SXY);
+    else own_grad_fill<R, TX, TY, TZ, false>(sp, gt, H, SX, SXY);
+    __syncthreads();
+  }
+  if (wallfree) nc_nodes<R, TX, TY, TZ, true, GT>(sp, gt, H, g, P, hout, x0, y0, z0);
+  else nc_nodes<R, TX, TY, TZ, false, GT>(sp, gt, H, g, P, hout, x0, y0, z0);
+  __syncthreads();
+}
+
+// Shared memory of one near-contact tile: phi with halo H and, with GT, the
+// gradients of the tile's own nodes.
+template <typename R>
+inline size_t nc_smem_bytes(int TX, int TY, int TZ, int H, bool gt) {
+  size_t n = (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
+  if (gt) n += 3 * (size_t)TX * TY * TZ;
+  return sizeof(R) * n;
+}
+
+// (templated on the storage format, not only on R, so that every translation
+// unit instantiates kernels of its own)
+template <int ST, int TX, int TY, int TZ, bool GT>
+__global__ void __launch_bounds__(TX* TY) k_nc(const typename Store<ST>::R* __restrict__ phi, Geo g, Phys P,
+                                               unsigned char* __restrict__ hout) {
+  using R = typename Store<ST>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  nc_tile<R, TX, TY, TZ, GT>(phi, g, P, hout, reinterpret_cast<R*>(smem_raw), blockIdx.x * TX, blockIdx.y * TY,
+                             blockIdx.z * TZ);
+}
+
+// The nodes of one fused-step tile; sp holds phi of the tile with a one-node
+// halo, hnc the near-contact distance of every node (read when A_h != 0).
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32>
+__device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O, const InitBuf& init, const Geo& g,
+                                           const Phys& P, const unsigned char* __restrict__ hnc,
+                                           typename Store<ST>::R* __restrict__ fields,
+                                           unsigned* __restrict__ status, const typename Store<ST>::R* sp, int x0,
+                                           int y0, int z0) {
+  constexpr int SX = TX + 2, SXY = SX * (TY + 2);
   using R = typename Store<ST>::R;
   using I = typename std::conditional<IDX32, unsigned, size_t>::type;
   const R tau_a = R(P.tau_a), tau_b = R(P.tau_b);
-  const R A2 = R(P.A2), beta = R(P.beta), A_h = R(P.A_h), phi_I = R(P.phi_I);
+  const R A2 = R(P.A2), beta = R(P.beta), A_h = R(P.A_h);
   const I N = (I)g.N;
   const size_t NF = (size_t)g.N;
 
@@ -448,62 +605,16 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       if (cz(p)) j2 += R(cz(p)) * d;
     }
 
-    // colour gradient from the tile (or from the tile's gradient cache)
-    const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + H);
+    // colour gradient from the tile; near-contact distance from the scan pass
+    const int c = (lz + 1) * SXY + (threadIdx.y + 1) * SX + (threadIdx.x + 1);
     const R phx = sp[c];
     R gr[3];
-    if constexpr (GT) {
-      const int o = (lz * TY + threadIdx.y) * TX + threadIdx.x;
-      gr[0] = gt[o];
-      gr[1] = gt[TN + o];
-      gr[2] = gt[2 * TN + o];
-    } else {
-      tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
-    }
-    const R gg = rsqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-
-    // near-contact scan (Eqs. stress_jump, near_cont_force): from an interface
-    // node step along n_out = -grad phi/|grad phi| by round(k n_out),
-    // k = 1..K; the first interface node with an antiparallel normal sets h.
+    tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
+    const R gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
     int h = 0;
     R Ahh = R(0);
-    if (A_h != R(0) && fabs(phx) < phi_I && gg >= R(NC_GRAD_MIN)) {
-      const R inv = R(-1) / gg;
-      const R no0 = gr[0] * inv, no1 = gr[1] * inv, no2 = gr[2] * inv;
-      for (int k = 1; k <= P.K; ++k) {
-        // |n_out| = 1, so |d| <= k <= K < halo; the clamp also covers non-finite normals
-        const int dx = max(-k, min(k, (int)round_(R(k) * no0)));
-        const int dy = max(-k, min(k, (int)round_(R(k) * no1)));
-        const int dz = max(-k, min(k, (int)round_(R(k) * no2)));
-        if constexpr (!WALLFREE) {
-          if (g.wx && (x + dx <= 0 || x + dx >= g.nx - 1)) break;
-          if (g.wy && (y + dy <= 0 || y + dy >= g.ny - 1)) break;
-          if (g.wz && (z + dz <= 0 || z + dz >= g.nz - 1)) break;
-        }
-        const int cy_ = c + dx + SX * dy + SXY * dz;
-        const R phy = sp[cy_];
-        if (!(fabs(phy) < phi_I)) continue;
-        R gy_[3];
-        bool cached = false;
-        if constexpr (GT) {
-          const int tx = (int)threadIdx.x + dx, ty = (int)threadIdx.y + dy, tz = lz + dz;
-          if ((unsigned)tx < (unsigned)TX && (unsigned)ty < (unsigned)TY && (unsigned)tz < (unsigned)TZ) {
-            const int o = (tz * TY + ty) * TX + tx;
-            gy_[0] = gt[o];
-            gy_[1] = gt[TN + o];
-            gy_[2] = gt[2 * TN + o];
-            cached = true;
-          }
-        }
-        if (!cached) tile_grad<R, WALLFREE>(sp, cy_, SX, SXY, gy_);
-        const R gm2 = gy_[0] * gy_[0] + gy_[1] * gy_[1] + gy_[2] * gy_[2];
-        if (gm2 < R(NC_GRAD_MIN) * R(NC_GRAD_MIN)) continue;
-        const R dot = gr[0] * gy_[0] + gr[1] * gy_[1] + gr[2] * gy_[2];
-        if (dot < -R(NC_COS_TOL) * gg * rsqrt_(gm2)) {
-          h = k;
-          break;
-        }
-      }
+    if (A_h != R(0)) {
+      h = hnc[self];
       if (h > 0) {
         const R hk = R(h);
         if (hk <= R(P.h_min)) Ahh = A_h;
@@ -623,80 +734,39 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
   }
 }
 
-// One tile of the fused step: stage phi of the tile + halo in shared memory
-// (one (y,z) row per thread row; solid and beyond-wall nodes get the marker;
-// periodic wrap only outside the box), then update the tile's nodes.  Ends
-// with a barrier, so the caller may reuse the shared tile.
+// One tile of the fused step: stage phi of the tile + a one-node halo, then
+// update the tile's nodes.  Ends with a barrier, so the caller may reuse the
+// shared tile.
 template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32>
 __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, const InitBuf& init,
-                                          const typename Store<ST>::R* __restrict__ phi, const Geo& g, const Phys& P,
+                                          const typename Store<ST>::R* __restrict__ phi,
+                                          const unsigned char* __restrict__ hnc, const Geo& g, const Phys& P,
                                           typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status,
                                           typename Store<ST>::R* sp, int x0, int y0, int z0) {
   using R = typename Store<ST>::R;
-  const int H = P.halo;
-  const int SX = TX + 2 * H, SY = TY + 2 * H, SZ = TZ + 2 * H;
-  const int SXY = SX * SY;
-  bool any_solid = false;
-  for (int row = threadIdx.y; row < SY * SZ; row += TY) {
-    const int ly = row % SY, lz = row / SY;
-    int gy = y0 - H + ly, gz = z0 - H + lz;
-    bool rsolid = false;
-    if (g.wy) rsolid |= (gy <= 0 || gy >= g.ny - 1);
-    else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
-    if (g.wz) rsolid |= (gz <= 0 || gz >= g.nz - 1);
-    else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
-    const long long rbase = (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
-    R* srow = sp + (size_t)lz * SXY + (size_t)ly * SX;
-    for (int lx = threadIdx.x; lx < SX; lx += TX) {
-      int gx = x0 - H + lx;
-      bool solid = rsolid;
-      if (g.wx) solid |= (gx <= 0 || gx >= g.nx - 1);
-      else if ((unsigned)gx >= (unsigned)g.nx) gx = ((gx % g.nx) + g.nx) % g.nx;
-      any_solid |= solid;
-      srow[lx] = solid ? R(PHI_SOLID) : phi[rbase + gx];
-    }
-  }
   // a tile whose halo holds no solid node needs no bounce-back or wall tests
-  const bool wallfree = !__syncthreads_or(any_solid);
-  if (P.A_h != 0.0) {
-    // near contact: the tile's own gradients are cached for the scan
-    R* gt = sp + (size_t)SXY * SZ;
-    if (wallfree) own_grad_fill<R, TX, TY, TZ, true>(sp, gt, H, SX, SXY);
-    else own_grad_fill<R, TX, TY, TZ, false>(sp, gt, H, SX, SXY);
-    __syncthreads();
-    if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, true>(S, O, init, g, P, fields, status, sp, gt, H, SX,
-                                                                    SXY, x0, y0, z0);
-    else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, true>(S, O, init, g, P, fields, status, sp, gt, H, SX,
-                                                                     SXY, x0, y0, z0);
-  } else {
-    if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, false>(S, O, init, g, P, fields, status, sp, nullptr, H,
-                                                                     SX, SXY, x0, y0, z0);
-    else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, false>(S, O, init, g, P, fields, status, sp, nullptr,
-                                                                      H, SX, SXY, x0, y0, z0);
-  }
+  const bool wallfree = stage_phi<R, TX, TY>(phi, g, 1, TZ + 2, sp, x0, y0, z0);
+  if (wallfree)
+    step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32>(S, O, init, g, P, hnc, fields, status, sp, x0, y0, z0);
+  else
+    step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32>(S, O, init, g, P, hnc, fields, status, sp, x0, y0, z0);
   __syncthreads();
 }
 
-// Shared memory of one fused-step tile: the phi tile with halo H and, with
-// near contact (H > 1), the gradient cache of the tile's own nodes.
+// Shared memory of one fused-step tile: phi with a one-node halo.
 template <typename R>
-inline size_t step_smem_bytes(int TX, int TY, int TZ, int H) {
-  size_t n = (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
-  if (H > 1) n += 3 * (size_t)TX * TY * TZ;
-  return sizeof(R) * n;
+inline size_t step_smem_bytes(int TX, int TY, int TZ) {
+  return sizeof(R) * (size_t)(TX + 2) * (TY + 2) * (TZ + 2);
 }
 
 template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32, int MINB = 2>
 __global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : MINB)
-    k_step(View<ST> S, View<ST> O, InitBuf init, const typename Store<ST>::R* __restrict__ phi, Geo g, Phys P,
-           typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status) {
+    k_step(View<ST> S, View<ST> O, InitBuf init, const typename Store<ST>::R* __restrict__ phi,
+           const unsigned char* __restrict__ hnc, Geo g, Phys P, typename Store<ST>::R* __restrict__ fields,
+           unsigned* __restrict__ status) {
   using R = typename Store<ST>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  step_tile<ST, LOADER, WS, WF, TX, TY, TZ, IDX32>(S, O, init, phi, g, P, fields, status,
+  step_tile<ST, LOADER, WS, WF, TX, TY, TZ, IDX32>(S, O, init, phi, hnc, g, P, fields, status,
                                                    reinterpret_cast<R*>(smem_raw), blockIdx.x * TX, blockIdx.y * TY,
                                                    blockIdx.z * TZ);
 }
@@ -749,8 +819,27 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     const Geo g = d.g;
     const Phys P = d.p;
     step_tile<ST, LOAD_PULL, true, false, TX, TY, TZ, IDX32>(
-        view<ST>(d.S[parity]), view<ST>(d.S[parity ^ 1]), none, reinterpret_cast<const R*>(d.phi), g, P, nullptr,
-        status, sp, bx * TX, by * TY, bz * TZ);
+        view<ST>(d.S[parity]), view<ST>(d.S[parity ^ 1]), none, reinterpret_cast<const R*>(d.phi), d.hnc, g, P,
+        nullptr, status, sp, bx * TX, by * TY, bz * TZ);
+  }
+}
+
+// Near-contact pass of a batch over the same (run, tile) items; runs without
+// near contact are skipped (their step never reads h).
+template <int ST, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX* TY) k_nc_batched(const RunDesc* __restrict__ runs, int nruns, long long ntiles) {
+  using R = typename Store<ST>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sp = reinterpret_cast<R*>(smem_raw);
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int r = find_run(runs, nruns, t, true);
+    const RunDesc& d = runs[r];
+    if (d.p.A_h == 0.0) continue;
+    const long long lt = t - d.tile_begin;
+    const int bx = (int)(lt % d.tiles_x);
+    const int by = (int)((lt / d.tiles_x) % d.tiles_y);
+    const int bz = (int)(lt / ((long long)d.tiles_x * d.tiles_y));
+    nc_tile<R, TX, TY, TZ, true>(reinterpret_cast<const R*>(d.phi), d.g, d.p, d.hnc, sp, bx * TX, by * TY, bz * TZ);
   }
 }
 

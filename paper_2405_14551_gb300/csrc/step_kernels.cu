@@ -8,9 +8,12 @@ const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 8, 4}, {64, 4, 4}};
 template <int ST>
 cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st);
 template <int ST>
+cudaError_t launch_nc_t(int variant, const Geo& g, const Phys& p, const void* phi, unsigned char* hnc,
+                        cudaStream_t st);
+template <int ST>
 cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, const Phys& p, const StateBuf& in,
-                          const InitBuf& init, const void* phi, StateBuf out, void* fields, unsigned* status,
-                          cudaStream_t st);
+                          const InitBuf& init, const void* phi, const unsigned char* hnc, StateBuf out, void* fields,
+                          unsigned* status, cudaStream_t st);
 template <int ST>
 cudaError_t launch_batched_t(const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles, int tile,
                              int halo_max, long long max_nodes, int parity, int blocks_per_sm, unsigned* status,
@@ -29,14 +32,25 @@ cudaError_t launch_phi(int storage, const Geo& g, const StateBuf& in, void* phi,
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step(int storage, int loader, bool write_state, bool write_fields, int tile, const Geo& g,
-                        const Phys& p, const StateBuf& in, const InitBuf& init, const void* phi, StateBuf out,
-                        void* fields, unsigned* status, cudaStream_t st) {
+cudaError_t launch_nc(int storage, int variant, const Geo& g, const Phys& p, const void* phi, unsigned char* hnc,
+                      cudaStream_t st) {
   switch (storage) {
-    case 0: return launch_step_s<0>(loader, write_state, write_fields, tile, g, p, in, init, phi, out, fields, status, st);
-    case 1: return launch_step_s<1>(loader, write_state, write_fields, tile, g, p, in, init, phi, out, fields, status, st);
-    case 2: return launch_step_s<2>(loader, write_state, write_fields, tile, g, p, in, init, phi, out, fields, status, st);
-    case 3: return launch_step_s<3>(loader, write_state, write_fields, tile, g, p, in, init, phi, out, fields, status, st);
+    case 0: return launch_nc_t<0>(variant, g, p, phi, hnc, st);
+    case 1: return launch_nc_t<1>(variant, g, p, phi, hnc, st);
+    case 2: return launch_nc_t<2>(variant, g, p, phi, hnc, st);
+    case 3: return launch_nc_t<3>(variant, g, p, phi, hnc, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(int storage, int loader, bool write_state, bool write_fields, int tile, const Geo& g,
+                        const Phys& p, const StateBuf& in, const InitBuf& init, const void* phi,
+                        const unsigned char* hnc, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
+  switch (storage) {
+    case 0: return launch_step_s<0>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
+    case 1: return launch_step_s<1>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
+    case 2: return launch_step_s<2>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
+    case 3: return launch_step_s<3>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
   }
   return cudaErrorInvalidValue;
 }

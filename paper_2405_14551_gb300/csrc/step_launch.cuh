@@ -15,25 +15,68 @@ inline int sm_count() {
   return n;
 }
 
+// CTAs of a kernel that fit on one SM at once (computed once per kernel).
+template <typename K>
+inline int resident_ctas(K kern, int threads, size_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem) != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b;
+}
+
 template <int ST>
 cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  const long long blocks_needed = (g.N + 255) / 256;
-  const long long cap = (long long)sm_count() * 8;
-  const int blocks = (int)(blocks_needed < cap ? blocks_needed : cap);
+  static const int occ32 = resident_ctas(k_phi<ST, true>, 256, 0);
+  static const int occ64 = resident_ctas(k_phi<ST, false>, 256, 0);
   const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
+  // one wave of resident CTAs striding over the lattice: no second, partial wave
+  const long long blocks_needed = (g.N + 255) / 256;
+  const long long cap = (long long)sm_count() * (idx32 ? occ32 : occ64);
+  const int blocks = (int)(blocks_needed < cap ? blocks_needed : cap);
   auto kern = idx32 ? k_phi<ST, true> : k_phi<ST, false>;
   trace_kernel("k_phi", kern, dim3(blocks), dim3(256), 0);
   kern<<<blocks, 256, 0, st>>>(view<ST>(in), g, reinterpret_cast<R*>(phi));
   return cudaGetLastError();
 }
 
+template <int ST, int TX, int TY, int TZ, bool GT>
+inline cudaError_t launch_nc_tt(const Geo& g, const Phys& p, const void* phi, unsigned char* hnc, cudaStream_t st) {
+  using R = typename Store<ST>::R;
+  const size_t smem = nc_smem_bytes<R>(TX, TY, TZ, p.halo, GT);
+  auto kern = k_nc<ST, TX, TY, TZ, GT>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
+  trace_kernel("k_nc", kern, grid, dim3(TX, TY), smem);
+  kern<<<grid, dim3(TX, TY), smem, st>>>(reinterpret_cast<const R*>(phi), g, p, hnc);
+  return cudaGetLastError();
+}
+
+// Near-contact tile shapes: 32x8x4 and 32x8x8 with the gradient cache,
+// 32x8x8 without it, 32x4x8 with it.
+template <int ST>
+cudaError_t launch_nc_t(int variant, const Geo& g, const Phys& p, const void* phi, unsigned char* hnc,
+                        cudaStream_t st) {
+  if (p.A_h == 0.0) return cudaSuccess;
+  switch (variant) {
+    case 1: return launch_nc_tt<ST, 32, 8, 8, true>(g, p, phi, hnc, st);
+    case 2: return launch_nc_tt<ST, 32, 8, 8, false>(g, p, phi, hnc, st);
+    case 3: return launch_nc_tt<ST, 32, 4, 8, true>(g, p, phi, hnc, st);
+    default: return launch_nc_tt<ST, 32, 8, 4, true>(g, p, phi, hnc, st);
+  }
+}
+
 template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int MINB = 2>
 inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
-                                 const void* phi, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
+                                 const void* phi, const unsigned char* hnc, StateBuf out, void* fields,
+                                 unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  const int H = p.halo;
-  const size_t smem = step_smem_bytes<R>(TX, TY, TZ, H);
+  const size_t smem = step_smem_bytes<R>(TX, TY, TZ);
   // 32-bit population offsets when every offset of the lattice fits
   const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
   auto kern = idx32 ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, true, MINB> : k_step<ST, LOADER, WS, WF, TX, TY, TZ, false, MINB>;
@@ -44,37 +87,38 @@ inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
   dim3 block(TX, TY, 1);
   trace_kernel("k_step", kern, grid, block, smem);
-  kern<<<grid, block, smem, st>>>(view<ST>(in), view<ST>(out), init, reinterpret_cast<const R*>(phi), g, p,
+  kern<<<grid, block, smem, st>>>(view<ST>(in), view<ST>(out), init, reinterpret_cast<const R*>(phi), hnc, g, p,
                                   reinterpret_cast<R*>(fields), status);
   return cudaGetLastError();
 }
 
 template <int ST, int LOADER, bool WS, bool WF>
 inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
-                                     const void* phi, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
+                                     const void* phi, const unsigned char* hnc, StateBuf out, void* fields,
+                                     unsigned* status, cudaStream_t st) {
   if constexpr (LOADER == LOAD_PULL && WS && !WF) {
     switch (tile) {
-      case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8>(g, p, in, init, phi, out, fields, status, st);
-      case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, 3>(g, p, in, init, phi, out, fields, status, st);
-      case 3: return launch_step_t<ST, LOADER, WS, WF, 64, 4, 4>(g, p, in, init, phi, out, fields, status, st);
+      case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8>(g, p, in, init, phi, hnc, out, fields, status, st);
+      case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, 3>(g, p, in, init, phi, hnc, out, fields, status, st);
+      case 3: return launch_step_t<ST, LOADER, WS, WF, 64, 4, 4>(g, p, in, init, phi, hnc, out, fields, status, st);
       default: break;
     }
   }
-  return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4>(g, p, in, init, phi, out, fields, status, st);
+  return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4>(g, p, in, init, phi, hnc, out, fields, status, st);
 }
 
 template <int ST>
-cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, const Phys& p,
-                                 const StateBuf& in, const InitBuf& init, const void* phi, StateBuf out, void* fields,
-                                 unsigned* status, cudaStream_t st) {
+cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, const Phys& p, const StateBuf& in,
+                          const InitBuf& init, const void* phi, const unsigned char* hnc, StateBuf out, void* fields,
+                          unsigned* status, cudaStream_t st) {
   if (loader == LOAD_PULL) {
-    if (ws && !wf) return launch_step_tiles<ST, LOAD_PULL, true, false>(tile, g, p, in, init, phi, out, fields, status, st);
-    if (ws && wf) return launch_step_tiles<ST, LOAD_PULL, true, true>(0, g, p, in, init, phi, out, fields, status, st);
-    if (!ws && wf) return launch_step_tiles<ST, LOAD_PULL, false, true>(0, g, p, in, init, phi, out, fields, status, st);
+    if (ws && !wf) return launch_step_tiles<ST, LOAD_PULL, true, false>(tile, g, p, in, init, phi, hnc, out, fields, status, st);
+    if (ws && wf) return launch_step_tiles<ST, LOAD_PULL, true, true>(0, g, p, in, init, phi, hnc, out, fields, status, st);
+    if (!ws && wf) return launch_step_tiles<ST, LOAD_PULL, false, true>(0, g, p, in, init, phi, hnc, out, fields, status, st);
   } else {
-    if (ws && !wf) return launch_step_tiles<ST, LOAD_FIELDS, true, false>(0, g, p, in, init, phi, out, fields, status, st);
-    if (ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, true, true>(0, g, p, in, init, phi, out, fields, status, st);
-    if (!ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, false, true>(0, g, p, in, init, phi, out, fields, status, st);
+    if (ws && !wf) return launch_step_tiles<ST, LOAD_FIELDS, true, false>(0, g, p, in, init, phi, hnc, out, fields, status, st);
+    if (ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, true, true>(0, g, p, in, init, phi, hnc, out, fields, status, st);
+    if (!ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, false, true>(0, g, p, in, init, phi, hnc, out, fields, status, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -97,7 +141,19 @@ template <int ST, int TX, int TY, int TZ, bool IDX32, int MINB = 2>
 inline cudaError_t launch_batched_step_t(const RunDesc* d_runs, int nruns, long long ntiles, int halo_max,
                                          int parity, int blocks, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  const size_t smem = step_smem_bytes<R>(TX, TY, TZ, halo_max);
+  if (halo_max > 1) {  // some run has near contact
+    const size_t nsmem = nc_smem_bytes<R>(TX, TY, TZ, halo_max, true);
+    auto nk = k_nc_batched<ST, TX, TY, TZ>;
+    if (nsmem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(nk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsmem);
+      if (e != cudaSuccess) return e;
+    }
+    trace_kernel("k_nc_batched", nk, dim3(blocks), dim3(TX, TY), nsmem);
+    nk<<<blocks, dim3(TX, TY), nsmem, st>>>(d_runs, nruns, ntiles);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const size_t smem = step_smem_bytes<R>(TX, TY, TZ);
   auto kern = k_step_batched<ST, TX, TY, TZ, IDX32, MINB>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -124,9 +180,11 @@ cudaError_t launch_batched_t(const RunDesc* d_runs, int nruns, long long nchunks
                              int halo_max, long long max_nodes, int parity, int blocks_per_sm, unsigned* status,
                              cudaStream_t st) {
   const int blocks = sm_count() * (blocks_per_sm > 0 ? blocks_per_sm : 2);
-  const int pblocks = sm_count() * 8;
   const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)max_nodes < (1ull << 32);
   auto pk = idx32 ? k_phi_batched<ST, true> : k_phi_batched<ST, false>;
+  static const int pocc32 = resident_ctas(k_phi_batched<ST, true>, 256, 0);
+  static const int pocc64 = resident_ctas(k_phi_batched<ST, false>, 256, 0);
+  const int pblocks = sm_count() * (idx32 ? pocc32 : pocc64);
   trace_kernel("k_phi_batched", pk, dim3(pblocks), dim3(256), 0);
   pk<<<pblocks, 256, 0, st>>>(d_runs, nruns, nchunks, parity);
   cudaError_t e = cudaGetLastError();

@@ -68,6 +68,8 @@ _SIGS = {
                                       ctypes.c_int, ctypes.c_int]),
     "lb_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "lb_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lb_set_nc_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lb_get_nc_tile": (ctypes.c_int, [ctypes.c_void_p]),
     "lb_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "lb_get_tile": (ctypes.c_int, [ctypes.c_void_p]),
     "lb_time": (ctypes.c_int64, [ctypes.c_void_p]),
@@ -241,10 +243,19 @@ def lb_step(h, nsteps: int):
 
 
 def lb_step_timed(h, nsteps: int):
-    """(mean ms of the phase-field pass, mean ms of the fused step kernel)."""
-    ms = np.zeros(2)
+    """(mean ms of the phase-field pass, of the fused step kernel, of the
+    near-contact scan)."""
+    ms = np.zeros(3)
     _check(load_library().lb_step_timed(h, int(nsteps), ms.ctypes.data), "lb_step_timed")
-    return float(ms[0]), float(ms[1])
+    return float(ms[0]), float(ms[1]), float(ms[2])
+
+
+def lb_set_nc_tile(h, variant: int):
+    _check(load_library().lb_set_nc_tile(h, int(variant)), "lb_set_nc_tile")
+
+
+def lb_get_nc_tile(h) -> int:
+    return int(load_library().lb_get_nc_tile(h))
 
 
 def lb_set_tile(h, tile: int):

@@ -84,3 +84,5 @@ def test_null_handle_rejected(lib):
     assert lib.lb_check(None) == L.LB_EINVAL
     assert lib.lb_destroy(None) == L.LB_OK
     assert lib.lb_time(None) == -1
+    assert lib.lb_set_nc_tile(None, 0) == L.LB_EINVAL
+    assert lib.lb_get_nc_tile(None) == -1

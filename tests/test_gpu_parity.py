@@ -112,12 +112,16 @@ def test_degenerate_grids(shape, walls):
 
 
 def test_tile_shapes_give_identical_results():
+    """Every tile of the fused kernel and of the near-contact scan (paired
+    differently) gives bitwise the same fields."""
     import paper_2405_14551_gb300.lbcg as L
     wl = W.droplet_pair(48, 40, 56, R=8.0, sep=20.0)
     ref = None
     for tile in range(4):
         s = make_gpu(wl)
         L.lb_set_tile(s.h, tile)
+        L.lb_set_nc_tile(s.h, (tile + 1) % 4)
+        assert L.lb_get_nc_tile(s.h) == (tile + 1) % 4
         s.step(37)
         f = s.fields(("phi", "ux", "h"))
         if ref is None:

@@ -39,11 +39,12 @@ def parse():
     ap.add_argument("--storage", default="twoset_f32")
     ap.add_argument("--no-extra", action="store_true", help="skip the other storage formats")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep measurement")
     ap.add_argument("--shape", default=None, help="nx,ny,nz of a smaller emulsion (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-tune", action="store_true", help="use --tile without autotuning")
     ap.add_argument("--tile", type=int, default=0, help="tile of the fused kernel when --no-tune is given")
-    ap.add_argument("--nc-tile", type=int, default=1, help="tile of the near-contact scan when --no-tune is given")
+    ap.add_argument("--nc-tile", type=int, default=0, help="tile of the near-contact scan when --no-tune is given")
     return ap.parse_args()
 
 
@@ -225,6 +226,40 @@ def other_storages(args, L, make, stream, tile, nc_tile, world, nodes, maxall, p
     return extra
 
 
+def batch_extra(args, L, W, stream):
+    """The batched sweep: 64 independent runs (grids 48^3..128^3, seeded
+    parameters and droplets) stepped together by the persistent kernels under a
+    CUDA graph with the autotuned tile, against the same runs one at a time."""
+    import torch
+    runs = W.batch_sweep()
+    b = L.Batch(runs, stream=stream)
+    tile, bps, tune_ms, _ = b.autotune(steps=4, use_cache=False)
+    steps = 64
+    b.step(16)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mb = e0.elapsed_time(e1)
+    e0.record(stream)
+    b.step_sequential(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    b.check()
+    nodes = b.nodes
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    return {"workload": f"batch_sweep_{len(runs)}_runs", "nodes": int(nodes), "steps": steps,
+            "tile": int(tile), "ctas_per_sm": int(bps),
+            "MLUPS_batched": round(nodes * steps / (mb / 1e3) / 1e6, 1),
+            "MLUPS_one_at_a_time": round(nodes * steps / (ms_seq / 1e3) / 1e6, 1),
+            "speedup": round(ms_seq / mb, 3)}
+
+
 def cpu_baseline(wl):
     cores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
@@ -342,6 +377,8 @@ def main():
     del sim
     torch.cuda.empty_cache()
     extra = {} if args.no_extra else other_storages(args, L, make, stream, best_tile, best_nc, world, nodes, maxall, peak)
+    if not args.no_batch and not args.shape:
+        extra["batch"] = batch_extra(args, L, W, stream)
     cpu = cpu_baseline(wl) if (rank == 0 and world == 1 and not args.no_cpu) else None
 
     if rank == 0:

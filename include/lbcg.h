@@ -148,9 +148,9 @@ int lb_step(lb_handle* h, int64_t nsteps);
 int lb_set_tile(lb_handle* h, int tile);
 int lb_get_tile(const lb_handle* h);
 
-/* Choose the tile shape of the near-contact scan kernel (0..3: 32x8x4 and
- * 32x8x8 with the tile's own gradients cached in shared memory, 32x8x8
- * without the cache, 32x4x8 with it); used by the autotuner.  Results do not
+/* Choose the tile shape of the near-contact scan kernel (0..3: 32x8x8,
+ * 32x8x4, 32x8x16, 32x4x16 nodes per CTA; FP64 storage always uses 32x8x4);
+ * used by the autotuner.  Results do not
  * depend on it.  LB_EINVAL outside 0..3; lb_get_nc_tile returns the index. */
 int lb_set_nc_tile(lb_handle* h, int variant);
 int lb_get_nc_tile(const lb_handle* h);

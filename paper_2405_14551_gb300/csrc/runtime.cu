@@ -100,6 +100,7 @@ struct lb_handle {
   int tile = 0;
   int nc_tile = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  uint64_t graph_launches = 0;  // kernel launches in one replay
 };
 
 namespace {
@@ -237,6 +238,7 @@ int build_graph(lb_handle* h, int parity) {
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   h->cur = save_cur;
   h->t = save_t;
+  h->graph_launches = g_launches.load() - save_l;
   g_launches = save_l;
   if (rc != LB_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -474,7 +476,7 @@ int lb_step(lb_handle* h, int64_t nsteps) {
     const int par = h->cur;
     if (!h->graph[par] && (rc = build_graph(h, par))) return rc;
     LB_CUDA(cudaGraphLaunch(h->graph[par], h->stream));
-    g_launches += 2 * STEPS_PER_GRAPH;
+    g_launches += h->graph_launches;
     h->t += STEPS_PER_GRAPH;  // even number of steps: parity unchanged
     nsteps -= STEPS_PER_GRAPH;
   }
@@ -787,6 +789,7 @@ struct lb_batch {
   int tile = 0;
   int blocks_per_sm = 2;
   bool dirty = true;
+  uint64_t graph_launches = 0;  // kernel launches in one replay
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
@@ -849,6 +852,7 @@ int batch_build_graph(lb_batch* b, int parity) {
   int rc = LB_OK;
   for (int k = 0; k < BATCH_STEPS_PER_GRAPH && rc == LB_OK; ++k) rc = batch_issue(b, parity ^ (k & 1));
   cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  b->graph_launches = g_launches.load() - save_l;
   g_launches = save_l;
   if (rc != LB_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -1023,7 +1027,7 @@ int lb_batch_step(lb_batch* b, int64_t nsteps) {
     const int par = b->runs[0]->cur;
     if (!b->graph[par] && (rc = batch_build_graph(b, par))) return rc;
     LB_CUDA(cudaGraphLaunch(b->graph[par], b->stream));
-    g_launches += 2 * BATCH_STEPS_PER_GRAPH;
+    g_launches += b->graph_launches;
     batch_advance(b, BATCH_STEPS_PER_GRAPH);
     nsteps -= BATCH_STEPS_PER_GRAPH;
   }

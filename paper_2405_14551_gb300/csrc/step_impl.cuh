@@ -319,24 +319,51 @@ __global__ void __launch_bounds__(256) k_phi(View<ST> S, Geo g, typename Store<S
 // ---------------------------------------------------------------------------
 // Colour gradient grad phi(p) = (1/cs2) sum_i w_i c_i phi(p + c_i) on the
 // shared tile; a solid neighbour contributes phi(p) (neutral wetting).  Tiles
-// whose halo holds no solid node skip the solid test (WALLFREE).
+// whose halo holds no solid node skip the solid test (WALLFREE).  The D3Q27
+// weights factor: for c_a = +-1, w(c) = v(c_b) v(c_c) / 216 with v(0) = 4,
+// v(+-1) = 1 on the two other axes, so each component is the central
+// difference along its axis smoothed by (1, 4, 1) x (1, 4, 1) across the
+// others, times 3/216 = 1/72.  Evaluated one z plane of the 3x3x3 block at a
+// time.
 template <typename R, bool WALLFREE>
 __device__ __forceinline__ void tile_grad(const R* sp, int c, int SX, int SXY, R gr[3]) {
   const R p0 = sp[c];
   R gx = R(0), gy = R(0), gz = R(0);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (i == REST) continue;
-    R v = sp[c + cx(i) + SX * cy(i) + SXY * cz(i)];
-    if constexpr (!WALLFREE) v = (v > R(0.5) * R(PHI_SOLID)) ? p0 : v;
-    const R wv = wgt<R>(i) * v;
-    if (cx(i)) gx += R(cx(i)) * wv;
-    if (cy(i)) gy += R(cy(i)) * wv;
-    if (cz(i)) gz += R(cz(i)) * wv;
+  for (int dz = -1; dz <= 1; ++dz) {
+    R p[3][3];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (dz == 0 && dy == 0 && dx == 0) {
+          p[1][1] = p0;
+          continue;
+        }
+        R v = sp[c + dx + SX * dy + SXY * dz];
+        if constexpr (!WALLFREE) v = (v > R(0.5) * R(PHI_SOLID)) ? p0 : v;
+        p[dy + 1][dx + 1] = v;
+      }
+    }
+    // x differences smoothed over y, y differences smoothed over x
+    const R ex = (p[0][2] - p[0][0]) + (p[2][2] - p[2][0]) + R(4) * (p[1][2] - p[1][0]);
+    const R ey = (p[2][0] - p[0][0]) + (p[2][2] - p[0][2]) + R(4) * (p[2][1] - p[0][1]);
+    if (dz == 0) {
+      gx += R(4) * ex;
+      gy += R(4) * ey;
+    } else {
+      gx += ex;
+      gy += ey;
+      // the plane smoothed over x and y enters the z difference
+      const R sm = (p[0][0] + p[0][2] + R(4) * p[0][1]) + (p[2][0] + p[2][2] + R(4) * p[2][1]) +
+                   R(4) * (p[1][0] + p[1][2] + R(4) * p[1][1]);
+      gz += dz > 0 ? sm : -sm;
+    }
   }
-  gr[0] = R(3) * gx;
-  gr[1] = R(3) * gy;
-  gr[2] = R(3) * gz;
+  constexpr R k72 = R(1) / R(72);
+  gr[0] = gx * k72;
+  gr[1] = gy * k72;
+  gr[2] = gz * k72;
 }
 
 // Pull for the hot path: totals f_i and component densities.  WALLFREE: no
@@ -391,78 +418,15 @@ __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const
   }
 }
 
-// Colour gradients of the tile's own nodes, computed once into shared memory
-// (gt[k][lz][ty][tx], k = x, y, z) so that near-contact scans whose target
-// lies inside the tile read them instead of recomputing them.
-template <typename R, int TX, int TY, int TZ, bool WALLFREE>
-__device__ __forceinline__ void own_grad_fill(const R* sp, R* gt, int H, int SX, int SXY) {
-  for (int lz = 0; lz < TZ; ++lz) {
-    const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + H);
-    R gr[3];
-    tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
-    const int o = (lz * TY + threadIdx.y) * TX + threadIdx.x;
-    gt[o] = gr[0];
-    gt[TX * TY * TZ + o] = gr[1];
-    gt[2 * TX * TY * TZ + o] = gr[2];
-  }
-}
-
-// Near-contact scan of one interface node (Eqs. stress_jump, near_cont_force):
-// step along the outward normal n_out = -grad phi/|grad phi| by round(k n_out),
-// k = 1..K; the first target that is an interface node (|phi| < phi_I,
-// |grad phi| >= NC_GRAD_MIN) with a normal antiparallel to the node's own
-// gives h = k; 0 when there is none.  The scan stops at a wall layer.  sp is
-// the phi tile with halo H >= K + 1, c the node's tile index, (tx, ty, tz)
-// its place among the tile's own nodes, gr and gg = |gr| its gradient.
-template <typename R, int TX, int TY, int TZ, bool WALLFREE, bool GT>
-__device__ __forceinline__ int nc_scan(const R* sp, const R* gt, int c, int tx, int ty, int tz, int x, int y, int z,
-                                       const Geo& g, const Phys& P, int SX, int SXY, const R gr[3], R gg) {
-  constexpr int TN = TX * TY * TZ;
-  const R phi_I = R(P.phi_I);
-  const R inv = R(-1) / gg;
-  const R no0 = gr[0] * inv, no1 = gr[1] * inv, no2 = gr[2] * inv;
-  for (int k = 1; k <= P.K; ++k) {
-    // |n_out| = 1, so |d| <= k <= K < halo; the clamp also covers non-finite normals
-    const int dx = max(-k, min(k, (int)round_(R(k) * no0)));
-    const int dy = max(-k, min(k, (int)round_(R(k) * no1)));
-    const int dz = max(-k, min(k, (int)round_(R(k) * no2)));
-    if constexpr (!WALLFREE) {
-      if (g.wx && (x + dx <= 0 || x + dx >= g.nx - 1)) break;
-      if (g.wy && (y + dy <= 0 || y + dy >= g.ny - 1)) break;
-      if (g.wz && (z + dz <= 0 || z + dz >= g.nz - 1)) break;
-    }
-    const int ct = c + dx + SX * dy + SXY * dz;
-    const R pt = sp[ct];
-    if (!(fabs(pt) < phi_I)) continue;
-    R gt_[3];
-    bool cached = false;
-    if constexpr (GT) {
-      const int ux = tx + dx, uy = ty + dy, uz = tz + dz;
-      if ((unsigned)ux < (unsigned)TX && (unsigned)uy < (unsigned)TY && (unsigned)uz < (unsigned)TZ) {
-        const int o = (uz * TY + uy) * TX + ux;
-        gt_[0] = gt[o];
-        gt_[1] = gt[TN + o];
-        gt_[2] = gt[2 * TN + o];
-        cached = true;
-      }
-    }
-    if (!cached) tile_grad<R, WALLFREE>(sp, ct, SX, SXY, gt_);
-    const R gm2 = gt_[0] * gt_[0] + gt_[1] * gt_[1] + gt_[2] * gt_[2];
-    if (gm2 < R(NC_GRAD_MIN) * R(NC_GRAD_MIN)) continue;
-    const R dot = gr[0] * gt_[0] + gr[1] * gt_[1] + gr[2] * gt_[2];
-    if (dot < -R(NC_COS_TOL) * gg * sqrt_(gm2)) return k;
-  }
-  return 0;
-}
-
-// Stage phi of a tile (TX x TY x SZ - 2H own nodes) plus a halo of H nodes
-// in shared memory, one (y, z) row per thread row: solid and beyond-wall
-// nodes get the marker PHI_SOLID; periodic axes wrap.  Returns (to every
-// thread) whether the staged block holds no solid node.
+// Stage phi of a tile (TX x TY x SZ - 2H own nodes) plus a halo of HX nodes
+// along x and H along y and z in shared memory (row length TX + 2 HX), one
+// (y, z) row per thread row: solid and beyond-wall nodes get the marker
+// PHI_SOLID; periodic axes wrap.  Returns (to every thread) whether the
+// staged block holds no solid node.
 template <typename R, int TX, int TY>
-__device__ __forceinline__ bool stage_phi(const R* __restrict__ phi, const Geo& g, int H, int SZ, R* sp, int x0,
-                                          int y0, int z0) {
-  const int SX = TX + 2 * H, SY = TY + 2 * H;
+__device__ __forceinline__ bool stage_phi(const R* __restrict__ phi, const Geo& g, int HX, int H, int SZ, R* sp,
+                                          int x0, int y0, int z0) {
+  const int SX = TX + 2 * HX, SY = TY + 2 * H;
   const int SXY = SX * SY;
   bool any_solid = false;
   for (int row = threadIdx.y; row < SY * SZ; row += TY) {
@@ -476,7 +440,7 @@ __device__ __forceinline__ bool stage_phi(const R* __restrict__ phi, const Geo& 
     const long long rbase = (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
     R* srow = sp + (size_t)lz * SXY + (size_t)ly * SX;
     for (int lx = threadIdx.x; lx < SX; lx += TX) {
-      int gx = x0 - H + lx;
+      int gx = x0 - HX + lx;
       bool solid = rsolid;
       if (g.wx) solid |= (gx <= 0 || gx >= g.nx - 1);
       else if ((unsigned)gx >= (unsigned)g.nx) gx = ((gx % g.nx) + g.nx) % g.nx;
@@ -487,75 +451,200 @@ __device__ __forceinline__ bool stage_phi(const R* __restrict__ phi, const Geo& 
   return !__syncthreads_or(any_solid);
 }
 
-template <typename R, int TX, int TY, int TZ, bool WALLFREE, bool GT>
-__device__ __forceinline__ void nc_nodes(const R* sp, const R* gt, int H, const Geo& g, const Phys& P,
+// The same staging with 16-byte loads and stores, for a lattice whose rows
+// are whole 16-byte vectors (nx a multiple of V = 16 / sizeof(R)) and a tile
+// whose x halo HX and start x0 are multiples of V: every vector then lies
+// wholly inside or wholly outside the box along x.  The block is walked as
+// one flat list of vectors, so no lane idles on a short row remainder.
+template <typename R, int TX, int TY, int HX, int H, int SZ>
+__device__ __forceinline__ bool stage_phi_vec(const R* __restrict__ phi, const Geo& g, R* sp, int x0, int y0,
+                                              int z0) {
+  constexpr int V = 16 / sizeof(R);
+  static_assert(HX % V == 0 && TX % V == 0, "vector staging needs aligned rows");
+  constexpr int SX = TX + 2 * HX, SY = TY + 2 * H, QR = SX / V, NQ = QR * SY * SZ;
+  using VT = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+  bool any_solid = false;
+  for (int q = threadIdx.y * TX + threadIdx.x; q < NQ; q += TX * TY) {
+    const int qx = q % QR, row = q / QR;
+    const int ly = row % SY, lz = row / SY;
+    int gy = y0 - H + ly, gz = z0 - H + lz;
+    bool rsolid = false;
+    if (g.wy) rsolid |= (gy <= 0 || gy >= g.ny - 1);
+    else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
+    if (g.wz) rsolid |= (gz <= 0 || gz >= g.nz - 1);
+    else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
+    const int gx0 = x0 - HX + qx * V;  // first x of the vector
+    R v[V];
+    bool vsolid[V];
+    bool inside = gx0 >= 0 && gx0 < g.nx;
+    int gxl = gx0;
+    if (!inside && !g.wx) {  // periodic wrap of a whole vector
+      gxl = ((gx0 % g.nx) + g.nx) % g.nx;
+      inside = true;
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int xj = gx0 + j;
+      vsolid[j] = rsolid || (g.wx && (xj <= 0 || xj >= g.nx - 1));
+    }
+    if (inside && !rsolid) {
+      const long long rbase = (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
+      const VT w = *reinterpret_cast<const VT*>(phi + rbase + gxl);
+      const R* wr = reinterpret_cast<const R*>(&w);
+#pragma unroll
+      for (int j = 0; j < V; ++j) v[j] = wr[j];
+    }
+    VT o;
+    R* orr = reinterpret_cast<R*>(&o);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      orr[j] = vsolid[j] ? R(PHI_SOLID) : v[j];
+      any_solid |= vsolid[j];
+    }
+    *reinterpret_cast<VT*>(sp + (size_t)row * SX + qx * V) = o;
+  }
+  return !__syncthreads_or(any_solid);
+}
+
+// Near-contact scan of one interface node (Eqs. stress_jump, near_cont_force):
+// step along the outward normal n_out = -grad phi/|grad phi| by round(k n_out),
+// k = 1..K (K = H - 1); the first target that is an interface node
+// (|phi| < phi_I, |grad phi| >= NC_GRAD_MIN) with a normal antiparallel to
+// the node's own gives h = k; 0 when there is none.  The scan stops at a
+// wall layer.  sp is the phi tile with halo H, c the node's tile index, gr
+// and gg = |gr| its gradient.
+template <typename R, bool WALLFREE, int H, int SX, int SXY>
+__device__ __forceinline__ int nc_scan(const R* sp, int c, int x, int y, int z, const Geo& g, const Phys& P,
+                                       const R gr[3], R gg) {
+  const R phi_I = R(P.phi_I);
+  const R inv = R(-1) / gg;
+  const R no0 = gr[0] * inv, no1 = gr[1] * inv, no2 = gr[2] * inv;
+#pragma unroll 1
+  for (int k = 1; k < H; ++k) {
+    // |n_out| = 1, so |d| <= k <= K < H; the clamp also covers non-finite normals
+    const int dx = max(-k, min(k, (int)round_(R(k) * no0)));
+    const int dy = max(-k, min(k, (int)round_(R(k) * no1)));
+    const int dz = max(-k, min(k, (int)round_(R(k) * no2)));
+    if constexpr (!WALLFREE) {
+      if (g.wx && (x + dx <= 0 || x + dx >= g.nx - 1)) break;
+      if (g.wy && (y + dy <= 0 || y + dy >= g.ny - 1)) break;
+      if (g.wz && (z + dz <= 0 || z + dz >= g.nz - 1)) break;
+    }
+    const int ct = c + dx + SX * dy + SXY * dz;
+    if (!(fabs(sp[ct]) < phi_I)) continue;
+    R gt[3];
+    tile_grad<R, WALLFREE>(sp, ct, SX, SXY, gt);
+    const R gm2 = gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2];
+    if (gm2 < R(NC_GRAD_MIN) * R(NC_GRAD_MIN)) continue;
+    const R dot = gr[0] * gt[0] + gr[1] * gt[1] + gr[2] * gt[2];
+    if (dot < -R(NC_COS_TOL) * gg * sqrt_(gm2)) return k;
+  }
+  return 0;
+}
+
+// Scan every queued interface node of the tile; threads take queue entries
+// in turn, so no lane idles on a bulk-phase node.
+template <typename R, int TX, int TY, int TZ, int H, int HX, bool WALLFREE>
+__device__ __forceinline__ void nc_queue(const R* sp, const unsigned short* queue, int n, const Geo& g, const Phys& P,
                                          unsigned char* __restrict__ hout, int x0, int y0, int z0) {
-  const int SX = TX + 2 * H, SXY = SX * (TY + 2 * H);
+  constexpr int SX = TX + 2 * HX, SXY = SX * (TY + 2 * H);
+  for (int q = threadIdx.y * TX + threadIdx.x; q < n; q += TX * TY) {
+    const int o = queue[q];
+    const int lx = o % TX, ly = (o / TX) % TY, lz = o / (TX * TY);
+    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+    const int c = (lz + H) * SXY + (ly + H) * SX + (lx + HX);
+    R gr[3];
+    tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
+    const R gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+    int h = 0;
+    if (gg >= R(NC_GRAD_MIN)) h = nc_scan<R, WALLFREE, H, SX, SXY>(sp, c, x, y, z, g, P, gr, gg);
+    hout[x + g.nx * (y + g.ny * z)] = (unsigned char)h;
+  }
+}
+
+// x halo of the near-contact tile: H rounded up to whole 16-byte vectors.
+template <typename R, int H>
+constexpr int nc_halo_x() {
+  constexpr int V = 16 / (int)sizeof(R);
+  return (H + V - 1) / V * V;
+}
+
+// One tile of the near-contact pass (halo H = K + 1; HX along x): stage phi,
+// queue the tile's interface nodes (|phi| < phi_I; solid nodes hold PHI_SOLID
+// and are never queued) by warp-aggregated appends, write h = 0 for the
+// others, then scan the queue.  Ends with a barrier, so the caller may reuse
+// the shared memory.  Shared memory: phi tile, a 16-byte counter, TX*TY*TZ
+// queue slots.
+template <typename R, int TX, int TY, int TZ, int H>
+__device__ __forceinline__ void nc_tile(const R* __restrict__ phi, const Geo& g, const Phys& P,
+                                        unsigned char* __restrict__ hout, R* sp, int x0, int y0, int z0) {
+  constexpr int HX = nc_halo_x<R, H>();
+  constexpr int SX = TX + 2 * HX, SY = TY + 2 * H, SZ = TZ + 2 * H, SXY = SX * SY;
+  int* count = reinterpret_cast<int*>(sp + (size_t)SXY * SZ);
+  unsigned short* queue = reinterpret_cast<unsigned short*>(count + 4);
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  if (tid == 0) *count = 0;
+  // both stagings end with a barrier
+  const bool wallfree = (g.nx % (16 / (int)sizeof(R)) == 0)
+                            ? stage_phi_vec<R, TX, TY, HX, H, SZ>(phi, g, sp, x0, y0, z0)
+                            : stage_phi<R, TX, TY>(phi, g, HX, H, SZ, sp, x0, y0, z0);
+  const int lane = tid & 31;
   const R phi_I = R(P.phi_I);
   for (int lz = 0; lz < TZ; ++lz) {
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
-    if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
-    const int self = x + g.nx * (y + g.ny * z);
-    const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + H);
-    const R phx = sp[c];  // PHI_SOLID on solid nodes: never an interface node
-    int h = 0;
-    if (fabs(phx) < phi_I) {
-      R gr[3];
-      if constexpr (GT) {
-        const int o = (lz * TY + threadIdx.y) * TX + threadIdx.x;
-        gr[0] = gt[o];
-        gr[1] = gt[TX * TY * TZ + o];
-        gr[2] = gt[2 * TX * TY * TZ + o];
-      } else {
-        tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
-      }
-      const R gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-      if (gg >= R(NC_GRAD_MIN))
-        h = nc_scan<R, TX, TY, TZ, WALLFREE, GT>(sp, gt, c, threadIdx.x, threadIdx.y, lz, x, y, z, g, P, SX, SXY, gr,
-                                                 gg);
+    const bool in = x < g.nx && y < g.ny && z < g.nz;
+    const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + HX);
+    const bool iface = in && fabs(sp[c]) < phi_I;
+    if (in && !iface) hout[x + g.nx * (y + g.ny * z)] = 0;
+    const unsigned m = __ballot_sync(0xffffffffu, iface);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(count, __popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (iface) queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned short)((lz * TY + threadIdx.y) * TX + threadIdx.x);
     }
-    hout[self] = (unsigned char)h;
   }
-}
-
-// One tile of the near-contact pass.  Ends with a barrier, so the caller may
-// reuse the shared tile.
-template <typename R, int TX, int TY, int TZ, bool GT>
-__device__ __forceinline__ void nc_tile(const R* __restrict__ phi, const Geo& g, const Phys& P,
-                                        unsigned char* __restrict__ hout, R* sp, int x0, int y0, int z0) {
-  const int H = P.halo;
-  const int SZ = TZ + 2 * H;
-  const bool wallfree = stage_phi<R, TX, TY>(phi, g, H, SZ, sp, x0, y0, z0);
-  R* gt = sp + (size_t)(TX + 2 * H) * (TY + 2 * H) * SZ;
-  const int SX = TX + 2 * H, SXY = SX * (TY + 2 * H);
-  if constexpr (GT) {
-    if (wallfree) own_grad_fill<R, TX, TY, TZ, true>(sp, gt, H, SX, SXY);
-    else own_grad_fill<R, TX, TY, TZ, false>(sp, gt, H, SX, SXY);
-    __syncthreads();
-  }
-  if (wallfree) nc_nodes<R, TX, TY, TZ, true, GT>(sp, gt, H, g, P, hout, x0, y0, z0);
-  else nc_nodes<R, TX, TY, TZ, false, GT>(sp, gt, H, g, P, hout, x0, y0, z0);
+  __syncthreads();
+  const int n = *count;
+  if (wallfree) nc_queue<R, TX, TY, TZ, H, HX, true>(sp, queue, n, g, P, hout, x0, y0, z0);
+  else nc_queue<R, TX, TY, TZ, H, HX, false>(sp, queue, n, g, P, hout, x0, y0, z0);
   __syncthreads();
 }
 
-// Shared memory of one near-contact tile: phi with halo H and, with GT, the
-// gradients of the tile's own nodes.
+// Shared memory of one near-contact tile with halo H (x halo rounded up to
+// whole 16-byte vectors).
 template <typename R>
-inline size_t nc_smem_bytes(int TX, int TY, int TZ, int H, bool gt) {
-  size_t n = (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
-  if (gt) n += 3 * (size_t)TX * TY * TZ;
-  return sizeof(R) * n;
+inline size_t nc_smem_bytes(int TX, int TY, int TZ, int H) {
+  const int V = 16 / (int)sizeof(R);
+  const int HX = (H + V - 1) / V * V;
+  return sizeof(R) * (size_t)(TX + 2 * HX) * (TY + 2 * H) * (TZ + 2 * H) + 16 + 2 * (size_t)TX * TY * TZ;
+}
+
+// Calls f with the near-contact halo H = K + 1 (2..7) as a compile-time
+// constant.
+template <typename F>
+__host__ __device__ __forceinline__ void with_halo(int halo, F&& f) {
+  switch (halo) {
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    default: break;
+  }
 }
 
 // (templated on the storage format, not only on R, so that every translation
 // unit instantiates kernels of its own)
-template <int ST, int TX, int TY, int TZ, bool GT>
+template <int ST, int TX, int TY, int TZ, int H>
 __global__ void __launch_bounds__(TX* TY) k_nc(const typename Store<ST>::R* __restrict__ phi, Geo g, Phys P,
                                                unsigned char* __restrict__ hout) {
   using R = typename Store<ST>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  nc_tile<R, TX, TY, TZ, GT>(phi, g, P, hout, reinterpret_cast<R*>(smem_raw), blockIdx.x * TX, blockIdx.y * TY,
-                             blockIdx.z * TZ);
+  nc_tile<R, TX, TY, TZ, H>(phi, g, P, hout, reinterpret_cast<R*>(smem_raw), blockIdx.x * TX, blockIdx.y * TY,
+                            blockIdx.z * TZ);
 }
 
 // The nodes of one fused-step tile; sp holds phi of the tile with a one-node
@@ -745,7 +834,7 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
                                           typename Store<ST>::R* sp, int x0, int y0, int z0) {
   using R = typename Store<ST>::R;
   // a tile whose halo holds no solid node needs no bounce-back or wall tests
-  const bool wallfree = stage_phi<R, TX, TY>(phi, g, 1, TZ + 2, sp, x0, y0, z0);
+  const bool wallfree = stage_phi<R, TX, TY>(phi, g, 1, 1, TZ + 2, sp, x0, y0, z0);
   if (wallfree)
     step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32>(S, O, init, g, P, hnc, fields, status, sp, x0, y0, z0);
   else
@@ -839,7 +928,10 @@ __global__ void __launch_bounds__(TX* TY) k_nc_batched(const RunDesc* __restrict
     const int bx = (int)(lt % d.tiles_x);
     const int by = (int)((lt / d.tiles_x) % d.tiles_y);
     const int bz = (int)(lt / ((long long)d.tiles_x * d.tiles_y));
-    nc_tile<R, TX, TY, TZ, true>(reinterpret_cast<const R*>(d.phi), d.g, d.p, d.hnc, sp, bx * TX, by * TY, bz * TZ);
+    with_halo(d.p.halo, [&](auto hc) {
+      nc_tile<R, TX, TY, TZ, decltype(hc)::value>(reinterpret_cast<const R*>(d.phi), d.g, d.p, d.hnc, sp, bx * TX,
+                                                  by * TY, bz * TZ);
+    });
   }
 }
 

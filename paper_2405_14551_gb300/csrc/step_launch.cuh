@@ -42,32 +42,39 @@ cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream
   return cudaGetLastError();
 }
 
-template <int ST, int TX, int TY, int TZ, bool GT>
+template <int ST, int TX, int TY, int TZ>
 inline cudaError_t launch_nc_tt(const Geo& g, const Phys& p, const void* phi, unsigned char* hnc, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  const size_t smem = nc_smem_bytes<R>(TX, TY, TZ, p.halo, GT);
-  auto kern = k_nc<ST, TX, TY, TZ, GT>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
-  trace_kernel("k_nc", kern, grid, dim3(TX, TY), smem);
-  kern<<<grid, dim3(TX, TY), smem, st>>>(reinterpret_cast<const R*>(phi), g, p, hnc);
-  return cudaGetLastError();
+  if (p.halo != p.K + 1 || p.halo < 2 || p.halo > 7) return cudaErrorInvalidValue;
+  const size_t smem = nc_smem_bytes<R>(TX, TY, TZ, p.halo);
+  const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
+  cudaError_t e = cudaSuccess;
+  with_halo(p.halo, [&](auto hc) {
+    auto kern = k_nc<ST, TX, TY, TZ, decltype(hc)::value>;
+    if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return;
+    trace_kernel("k_nc", kern, grid, dim3(TX, TY), smem);
+    kern<<<grid, dim3(TX, TY), smem, st>>>(reinterpret_cast<const R*>(phi), g, p, hnc);
+    e = cudaGetLastError();
+  });
+  return e;
 }
 
-// Near-contact tile shapes: 32x8x4 and 32x8x8 with the gradient cache,
-// 32x8x8 without it, 32x4x8 with it.
+// Near-contact tile shapes (x, y threads, z nodes per thread): 32x8x8,
+// 32x8x4, 32x8x16, 32x4x16.  FP64 storage (parity runs) uses 32x8x4 only.
 template <int ST>
 cudaError_t launch_nc_t(int variant, const Geo& g, const Phys& p, const void* phi, unsigned char* hnc,
                         cudaStream_t st) {
   if (p.A_h == 0.0) return cudaSuccess;
-  switch (variant) {
-    case 1: return launch_nc_tt<ST, 32, 8, 8, true>(g, p, phi, hnc, st);
-    case 2: return launch_nc_tt<ST, 32, 8, 8, false>(g, p, phi, hnc, st);
-    case 3: return launch_nc_tt<ST, 32, 4, 8, true>(g, p, phi, hnc, st);
-    default: return launch_nc_tt<ST, 32, 8, 4, true>(g, p, phi, hnc, st);
+  if constexpr (ST == 3) {
+    return launch_nc_tt<ST, 32, 8, 4>(g, p, phi, hnc, st);
+  } else {
+    switch (variant) {
+      case 1: return launch_nc_tt<ST, 32, 8, 4>(g, p, phi, hnc, st);
+      case 2: return launch_nc_tt<ST, 32, 8, 16>(g, p, phi, hnc, st);
+      case 3: return launch_nc_tt<ST, 32, 4, 16>(g, p, phi, hnc, st);
+      default: return launch_nc_tt<ST, 32, 8, 8>(g, p, phi, hnc, st);
+    }
   }
 }
 
@@ -142,7 +149,7 @@ inline cudaError_t launch_batched_step_t(const RunDesc* d_runs, int nruns, long 
                                          int parity, int blocks, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
   if (halo_max > 1) {  // some run has near contact
-    const size_t nsmem = nc_smem_bytes<R>(TX, TY, TZ, halo_max, true);
+    const size_t nsmem = nc_smem_bytes<R>(TX, TY, TZ, halo_max);
     auto nk = k_nc_batched<ST, TX, TY, TZ>;
     if (nsmem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(nk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsmem);

@@ -99,6 +99,24 @@ def test_walls_body_force_unequal_tau(storage, tol):
         assert max(e.values()) <= tol, (o.t, e)
 
 
+@pytest.mark.parametrize("tau_a,tau_b", [(0.6, 1.0), (1.0, 0.6)])
+@pytest.mark.parametrize("storage,tol", [("twoset_f32", 1e-5), ("twoset_f64", 1e-11)])
+def test_viscosity_ratio_five(storage, tol, tau_a, tau_b):
+    """Unequal viscosities with ratio 5 (nu = (tau - 1/2)/3: 1/30 against 1/6)
+    mixed harmonically across the interface (Eq. sigmaA), in a walled channel
+    under a uniform body force with near contact on, both ways round."""
+    p = dict(W.BASE, A_h=0.1, h_min=3.0, h_max=3.0, g=(0.0, 0.0, 2e-5), g_mode=1, tau_a=tau_a, tau_b=tau_b)
+    wl = W.Workload("visc5", (24, 22, 40), 0b010, p, 60,
+                    centres=np.array([[12.0, 11.0, 11.0], [12.5, 11.0, 27.0]]), radii=np.array([5.5, 5.5]))
+    o = make_oracle(wl)
+    s = make_gpu(wl, storage=storage)
+    for n in (3, 12, 25):
+        o.step(n)
+        s.step(n)
+        e = field_errors(s.fields(f64=True), o.fields(), CMP_FIELDS)
+        assert max(e.values()) <= tol, (o.t, e)
+
+
 @pytest.mark.parametrize("shape,walls", [((1, 1, 1), 0), ((3, 3, 3), 0b111), ((5, 3, 4), 0b010), ((2, 7, 3), 0b100)])
 def test_degenerate_grids(shape, walls):
     wl = W.Workload("tiny", shape, walls, dict(W.BASE, A_h=0.1, g=(1e-4, 2e-4, -1e-4), g_mode=1), 10,

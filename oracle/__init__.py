@@ -40,6 +40,7 @@ class OrcParams(ctypes.Structure):
         ("phi_I", ctypes.c_double),
         ("g", ctypes.c_double * 3),
         ("g_mode", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
     ]
 
 
@@ -89,6 +90,7 @@ def lib():
             L.orc_tau_bar.argtypes = [ctypes.c_double] * 4
             L.orc_recolour.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
             L.orc_node_collide.argtypes = [ctypes.POINTER(OrcParams), dp, dp, dp, dp, dp, dp, dp]
+            L.orc_regularise.argtypes = [dp, dp, dp]
             _lib = L
         return _lib
 
@@ -99,13 +101,14 @@ def _dp(a: np.ndarray):
 
 
 def make_params(nx, ny, nz, walls=0, tau_a=1.0, tau_b=1.0, A_a=0.01, A_b=0.01, beta=0.7,
-                A_h=0.0, h_min=3.0, h_max=3.0, phi_I=0.9, g=(0.0, 0.0, 0.0), g_mode=0) -> OrcParams:
+                A_h=0.0, h_min=3.0, h_max=3.0, phi_I=0.9, g=(0.0, 0.0, 0.0), g_mode=0, collision=0) -> OrcParams:
     p = OrcParams()
     p.nx, p.ny, p.nz, p.walls = int(nx), int(ny), int(nz), int(walls)
     p.tau_a, p.tau_b, p.A_a, p.A_b, p.beta = tau_a, tau_b, A_a, A_b, beta
     p.A_h, p.h_min, p.h_max, p.phi_I = A_h, h_min, h_max, phi_I
     p.g[0], p.g[1], p.g[2] = g
     p.g_mode = int(g_mode)
+    p.collision = int(collision)
     return p
 
 
@@ -151,6 +154,14 @@ def recolour(beta, rhoA, rhoB, fstar, grad):
                        _dp(np.ascontiguousarray(fstar, dtype=np.float64)),
                        _dp(np.ascontiguousarray(grad, dtype=np.float64)), _dp(oa), _dp(ob))
     return oa, ob
+
+
+def regularise(f, feq):
+    """Non-equilibrium part of f projected on Hermite orders 1 and 2."""
+    out = np.zeros(Q)
+    lib().orc_regularise(_dp(np.ascontiguousarray(f, dtype=np.float64)),
+                         _dp(np.ascontiguousarray(feq, dtype=np.float64)), _dp(out))
+    return out
 
 
 def node_collide(params: OrcParams, fA, fB, grad, F):

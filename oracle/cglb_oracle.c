@@ -15,7 +15,8 @@
  *
  * Readings of the paper where it is silent or garbled: lattice order and weights, isotropic gradient stencil, neutral
  * wetting of phi at walls, B_i = w_i(|c_i|^2 - 2/3), omega_bar = 2/(6 nu_bar + 1),
- * Guo forcing, Latva-Kokko f^{eq,0} = w_i rho, the near-contact scan along the
+ * Guo forcing, Latva-Kokko f^{eq,0} = w_i rho, the regularised collision as
+ * the projection of the non-equilibrium part on Hermite orders 1 and 2, the near-contact scan along the
  * outward normal with lround() steps, F_rep = (A_h/2) grad(phi), halfway
  * bounce-back walls, the sharp droplet initial condition.
  *
@@ -99,6 +100,7 @@ typedef struct {
   double phi_I;
   double g[3];
   int32_t g_mode; /* 0 none, 1 rho*g, 2 s(z)*rhoA*g (mirror-opposite halves) */
+  int32_t collision; /* 0 BGK, 1 regularised (non-equilibrium projected on Hermite orders 1 and 2) */
 } orc_params;
 
 #define GRAD_EPS 1e-12
@@ -169,6 +171,37 @@ double orc_tau_bar(double tau_a, double tau_b, double rhoA, double rhoB) {
   return 3.0 * nu + 0.5;
 }
 
+/* Regularised non-equilibrium part (the regularised colour-gradient collision
+ * that Sec. III.C.1 cites for filtering the non-hydrodynamic "ghost" modes;
+ * the paper gives no formula, the reading is the Hermite projection of the
+ * regularised LB method): the non-equilibrium part fneq_i = f_i - feq_i of the
+ * total is replaced by its projection on the Hermite polynomials of orders 1
+ * and 2,
+ *   fneq_reg_i = w_i [ c_i.J / cs2 + (c_i c_i - cs2 I) : Pi / (2 cs2^2) ],
+ *   J = sum_i c_i fneq_i,   Pi = sum_i c_i c_i fneq_i,
+ * which keeps the moments of orders 0, 1 and 2 of fneq (J = -F/2 with the
+ * half-force velocity shift) and removes every higher-order part. */
+void orc_regularise(const double f[Q], const double feq[Q], double out[Q]) {
+  lattice_build();
+  const double cs2 = 1.0 / 3.0;
+  double J[3] = {0, 0, 0}, Pi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int i = 0; i < Q; ++i) {
+    double d = f[i] - feq[i];
+    for (int a = 0; a < 3; ++a) {
+      J[a] += LC[i][a] * d;
+      for (int b = 0; b < 3; ++b) Pi[a][b] += LC[i][a] * LC[i][b] * d;
+    }
+  }
+  for (int i = 0; i < Q; ++i) {
+    double cj = 0.0, qp = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      cj += LC[i][a] * J[a];
+      for (int b = 0; b < 3; ++b) qp += (LC[i][a] * LC[i][b] - (a == b ? cs2 : 0.0)) * Pi[a][b];
+    }
+    out[i] = LW[i] * (cj / cs2 + qp / (2.0 * cs2 * cs2));
+  }
+}
+
 /* Latva-Kokko recolouring, Eqs. ome3_1 / ome3_2, with f^{eq,0}_i = w_i rho and
  * cos(theta_i) = c_i.n/|c_i| (0 for the rest direction). */
 void orc_recolour(double beta, double rhoA, double rhoB, const double fstar[Q], const double grad[3],
@@ -219,7 +252,14 @@ void orc_node_collide(const orc_params* p, const double fA[Q], const double fB[Q
   orc_feq(rho, u, feq);
   orc_omega2(p->A_a, p->A_b, grad, om2);
   orc_guo(tau, u, F, S);
-  for (int i = 0; i < Q; ++i) fstar[i] = f[i] + (feq[i] - f[i]) / tau + om2[i] + S[i];
+  if (p->collision == 1) {
+    /* regularised: f* = feq + (1 - 1/tau) fneq_reg + Omega2 + S */
+    double fr[Q];
+    orc_regularise(f, feq, fr);
+    for (int i = 0; i < Q; ++i) fstar[i] = feq[i] + (1.0 - 1.0 / tau) * fr[i] + om2[i] + S[i];
+  } else {
+    for (int i = 0; i < Q; ++i) fstar[i] = f[i] + (feq[i] - f[i]) / tau + om2[i] + S[i];
+  }
   orc_recolour(p->beta, rhoA, rhoB, fstar, grad, outA, outB);
 }
 

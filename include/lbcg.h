@@ -92,6 +92,9 @@ typedef struct {
   double g[3];            /* body-force vector */
   int32_t g_mode;         /* 0 none; 1 F = rho g; 2 F = s(z) rhoA g, s = +1 below nz/2, -1 above, 0 at z = 0, nz/2 */
   int32_t storage;        /* LB_STORAGE_* */
+  int32_t collision;      /* 0: BGK on the total (Sec. III.B); 1: regularised colour-gradient collision (the
+                             ghost-mode filtering Sec. III.C.1 cites): the non-equilibrium part of the total is
+                             projected on Hermite orders 1 and 2 before relaxation; moments up to order 2 as BGK */
 } lb_params;
 
 /* Optional device allocator (for example PyTorch's caching allocator).  With
@@ -203,6 +206,14 @@ int lb_check(lb_handle* h);
  * format version.  lb_load requires a handle of the same grid and storage. */
 int lb_save(lb_handle* h, const char* path);
 int lb_load(lb_handle* h, const char* path);
+
+/* Copy the state of src into dst (same grid, walls and storage; parameters
+ * may differ): the population lattice, or the initial fields if src has not
+ * stepped yet, and the step counter.  Waits for src's stream, then copies
+ * device to device on dst's stream (asynchronous for dst).  LB_EINVAL if the
+ * handles differ in grid or storage, LB_ESTATE if src is not initialised.
+ * Used to start a plain-LB judge run from the exact state of a run. */
+int lb_copy_state(lb_handle* dst, lb_handle* src);
 
 /* Number of kernels this library has launched in this process (graph replays
  * count every kernel node). */

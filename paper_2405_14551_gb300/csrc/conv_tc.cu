@@ -14,6 +14,7 @@
 // gives up sets bit 4 of the status word.
 #include <cuda_bf16.h>
 
+#include <cstdlib>
 #include <string>
 
 #include "../../include/lbcg.h"
@@ -157,6 +158,189 @@ __global__ void __launch_bounds__(128, 1)
       float acc[16];
       tc::tmem_ld16(lane_base + (uint32_t)col, acc);
       if (valid) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          float vv = acc[k] + (bias ? bias[col + k] : 0.0f);
+          acc[k] = relu ? fmaxf(vv, 0.0f) : vv;
+        }
+        if (Y) {
+          uint4* yp = reinterpret_cast<uint4*>(Y + v * ldy + col);
+          yp[0] = make_uint4(pack_bf16(acc[0], acc[1]), pack_bf16(acc[2], acc[3]), pack_bf16(acc[4], acc[5]),
+                             pack_bf16(acc[6], acc[7]));
+          yp[1] = make_uint4(pack_bf16(acc[8], acc[9]), pack_bf16(acc[10], acc[11]), pack_bf16(acc[12], acc[13]),
+                             pack_bf16(acc[14], acc[15]));
+        }
+        if (Yf) {
+          float4* fp = reinterpret_cast<float4*>(Yf + v * ldy + col);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) fp[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+      }
+    }
+  } else if (t == 0) {
+    atomicOr(status, CONV_TIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// forward / input gradient, spatially tiled (3x3x3 taps)
+// ---------------------------------------------------------------------------
+// A CTA owns an output block of 8 (x) x 16 (y) x TZ (z) voxels and all Cout
+// channels: TZ accumulators of 128 rows x Cout columns in tensor memory.  Per
+// channel chunk of KC channels it stages the input block with a one-voxel halo
+// (10 x 18 x (TZ + 2) voxels) once, in the layout
+//   piece (cg, zz, yy, xx) of 8 channels at ((cg * SZH + zz) * 18 + yy) * 10 + xx,
+// so that for every tap the 128 output rows of one z plane read 16 core
+// matrices of 8 consecutive x voxels (128 contiguous bytes) 160 bytes apart:
+// the A operand of a tap is the same staged block at a shifted start address,
+// and the input is read once per chunk instead of once per tap.  Weights of
+// one (chunk, tap) step (Cout x KC) stream through a ring of NS buffers.  All
+// 128 threads copy with cp.async (zero fill for padded voxels); one thread
+// issues the UMMAs of a step (TZ planes x KC/16) and commits them to the
+// step's ring barrier, and after the last tap of a chunk to the halo buffer's
+// barrier, before a buffer is refilled.  Every wait is bounded.
+constexpr int TCONV_NS = 5;  // weight ring depth
+constexpr int TCONV_D = 3;   // steps loaded ahead; the slot refilled was read two steps before
+
+__device__ __forceinline__ int wrap_or_pad(int c, int n, int periodic) {
+  if (c >= 0 && c < n) return c;
+  if (!periodic) return -1;
+  return c < 0 ? c + n : c - n;
+}
+
+template <int TZ>
+__global__ void __launch_bounds__(128, 1)
+    k_conv_fwd_tiled(const __nv_bfloat16* __restrict__ X, int Cin, const __nv_bfloat16* __restrict__ W,
+                     const float* __restrict__ bias, __nv_bfloat16* __restrict__ Y, float* __restrict__ Yf, int Cout,
+                     int ldy, int KC, ConvGeo g, int relu, unsigned* __restrict__ status) {
+  constexpr int SZH = TZ + 2;
+  constexpr int HV = 10 * 18 * SZH;  // staged voxels
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  const size_t halo_bytes = (size_t)HV * KC * 2, w_bytes = (size_t)Cout * KC * 2;
+  const int nhalo = Cin > KC ? 2 : 1;  // one chunk needs one input buffer
+  unsigned char* sH[2] = {smem, smem + (nhalo - 1) * halo_bytes};
+  unsigned char* sW = smem + nhalo * halo_bytes;
+  uint64_t* bar_w = reinterpret_cast<uint64_t*>(sW + TCONV_NS * w_bytes);
+  uint64_t* bar_h = bar_w + TCONV_NS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_h + 2);
+  uint32_t ncols = 32;
+  while ((int)ncols < TZ * Cout) ncols <<= 1;
+
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, ncols);
+    tc::tmem_relinquish();
+  }
+  if (t == 0) {
+    for (int k = 0; k < TCONV_NS; ++k) tc::mbar_init(&bar_w[k], 1);
+    tc::mbar_init(&bar_h[0], 1);
+    tc::mbar_init(&bar_h[1], 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  const int bxs = g.nx / 8, bys = g.ny / 16, bzs = g.nz / TZ;
+  int blk = blockIdx.x;
+  const int x0 = (blk % bxs) * 8;
+  blk /= bxs;
+  const int y0 = (blk % bys) * 16;
+  blk /= bys;
+  const int z0 = (blk % bzs) * TZ;
+  const int b = blk / bzs;
+
+  const int nchunks = Cin / KC;
+  const int nks = nchunks * 27;  // (chunk, tap) steps
+  const int cgs = KC / 8;
+  const uint32_t a_lbo = (uint32_t)HV * 16, a_sbo = 160;
+  const uint32_t b_lbo = (uint32_t)Cout * 16, b_sbo = 128;
+  const uint32_t idesc = tc::idesc_bf16(CONV_M, Cout, false, false);
+
+  // issue the copies of step s (weights; the input block too at a chunk's first tap)
+  auto load_step = [&](int s) {
+    const int c = s / 27, tap = s % 27, c0 = c * KC;
+    unsigned char* wdst = sW + (size_t)(s % TCONV_NS) * w_bytes;
+    for (int p = t; p < Cout * cgs; p += 128) {
+      const int co = p % Cout, kg = p / Cout;
+      tc::cp_async16(wdst + ((size_t)kg * Cout + co) * 16, W + ((size_t)co * 27 + tap) * Cin + c0 + kg * 8, true);
+    }
+    if (tap == 0) {
+      unsigned char* hdst = sH[c & 1];
+      for (int p = t; p < HV * cgs; p += 128) {
+        const int xx = p % 10, r = p / 10;
+        const int yy = r % 18, r2 = r / 18;
+        const int zz = r2 % SZH, cg = r2 / SZH;
+        const int gx = wrap_or_pad(x0 - 1 + xx, g.nx, g.px);
+        const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
+        const int gz = wrap_or_pad(z0 - 1 + zz, g.nz, g.pz);
+        const bool ok = gx >= 0 && gy >= 0 && gz >= 0;
+        const long long v = ok ? (((long long)b * g.nz + gz) * g.ny + gy) * g.nx + gx : 0;
+        tc::cp_async16(hdst + (size_t)p * 16, X + v * Cin + c0 + cg * 8, ok);
+      }
+    }
+  };
+
+  bool ok = true;
+  for (int s = 0; s < TCONV_D && s < nks; ++s) {
+    load_step(s);
+    tc::cp_async_commit();
+  }
+  for (int s = 0; s < nks; ++s) {
+    // refill: step s + D goes into the ring slot of step s + D - NS = s - 2 (and,
+    // at a chunk's first tap, into the input buffer of chunk c - 2), so the
+    // UMMAs that read it were issued two iterations ago
+    const int pf = s + TCONV_D;
+    bool wok = true;
+    if (pf < nks) {
+      if (pf >= TCONV_NS) wok = tc::mbar_wait(&bar_w[pf % TCONV_NS], (uint32_t)(((pf / TCONV_NS) - 1) & 1), 1u << 22);
+      const int pc = pf / 27;
+      if (wok && pf % 27 == 0 && pc >= 2) wok = tc::mbar_wait(&bar_h[pc & 1], (uint32_t)(((pc / 2) - 1) & 1), 1u << 22);
+    }
+    ok = __syncthreads_and(ok && wok);
+    if (!ok) break;
+    if (pf < nks) load_step(pf);
+    tc::cp_async_commit();
+    tc::cp_async_wait<TCONV_D>();  // step s has landed (this thread's copies)
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc::fence_after_sync();
+      const int c = s / 27, tap = s % 27;
+      const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;  // offsets + 1
+      const uint32_t h0 = tc::smem_u32(sH[c & 1]) + (uint32_t)((dz * 18 + dy) * 10 + dx) * 16;
+      const uint32_t w0 = tc::smem_u32(sW + (size_t)(s % TCONV_NS) * w_bytes);
+      for (int z = 0; z < TZ; ++z) {
+        for (int j = 0; j < KC / 16; ++j) {
+          const uint64_t ad = tc::smem_desc(h0 + (uint32_t)z * 180 * 16 + (uint32_t)j * 2 * a_lbo, a_lbo, a_sbo);
+          const uint64_t bd = tc::smem_desc(w0 + (uint32_t)j * 2 * b_lbo, b_lbo, b_sbo);
+          tc::mma_bf16(tmem + (uint32_t)(z * Cout), ad, bd, idesc, (s > 0 || j > 0) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(&bar_w[s % TCONV_NS]);
+      if (tap == 26) tc::mma_commit(&bar_h[c & 1]);
+    }
+  }
+  tc::cp_async_wait<0>();
+  // the last commit covers every UMMA issued before it
+  const int last = nks - 1;
+  bool done = tc::mbar_wait(&bar_w[last % TCONV_NS], (uint32_t)((last / TCONV_NS) & 1), 1u << 22);
+  if (!done) done = tc::mbar_wait(&bar_w[last % TCONV_NS], (uint32_t)((last / TCONV_NS) & 1), 1u << 22);
+  ok = __syncthreads_and(ok && done);
+  tc::fence_after_sync();
+  if (ok) {
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const int x = x0 + (t & 7), y = y0 + (t >> 3);
+    for (int z = 0; z < TZ; ++z) {
+      const long long v = (((long long)b * g.nz + z0 + z) * g.ny + y) * g.nx + x;
+      for (int col = 0; col < Cout; col += 16) {
+        float acc[16];
+        tc::tmem_ld16(lane_base + (uint32_t)(z * Cout + col), acc);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           float vv = acc[k] + (bias ? bias[col + k] : 0.0f);
@@ -341,6 +525,27 @@ static size_t conv_wgrad_smem(int Cout) {
   return conv_smem(2 * (size_t)CONV_M * 64 * 2 + 2 * (size_t)Cout * 64 * 2 + 64, Cout);
 }
 
+// Shared memory of the tiled forward kernel: two input blocks, the weight
+// ring, barriers and the tensor-memory slot, raised where needed so that the
+// CTAs sharing an SM never ask for more than its 512 tensor-memory columns.
+static size_t conv_tiled_smem(int tz, int Cin, int Cout, int KC) {
+  const size_t halo = (size_t)10 * 18 * (tz + 2) * KC * 2;
+  const size_t nhalo = Cin > KC ? 2 : 1;
+  const size_t need = nhalo * halo + (size_t)TCONV_NS * Cout * KC * 2 + 8 * (TCONV_NS + 2) + 16;
+  return conv_smem(need, Cout * tz);
+}
+
+// LBNN_CONV_UNTILED=1 routes every forward convolution through the per-voxel
+// gather kernel (used to compare the two kernels).
+static bool conv_tiled_disabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("LBNN_CONV_UNTILED");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
 static int pick_kc(int Cin) {
   if (Cin % 64 == 0) return 64;
   if (Cin % 32 == 0) return 32;
@@ -368,10 +573,32 @@ int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, con
   if (((uintptr_t)x | (uintptr_t)w | (uintptr_t)y | (uintptr_t)yf) & 15)
     return report_error(LB_EINVAL, "tensors must be 16-byte aligned");
   ConvGeo g{nx, ny, nz, nb, (int)(periodic & 1u), (int)((periodic >> 1) & 1u), (int)((periodic >> 2) & 1u)};
+  cudaStream_t st = (cudaStream_t)stream;
+  if (taps == 27 && nx % 8 == 0 && ny % 16 == 0 && !conv_tiled_disabled()) {
+    // spatially tiled kernel: TZ planes per CTA with TZ x Cout accumulator columns <= 512
+    const int KCt = cin % 32 == 0 ? 32 : 16;
+    int tz = 4;
+    while (tz > 1 && (tz * cout > 512 || nz % tz)) tz >>= 1;
+    const size_t smem = conv_tiled_smem(tz, cin, cout, KCt);
+    cudaError_t e = cudaSuccess;
+    auto launch = [&](auto kern) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return;
+      const unsigned blocks = (unsigned)((nx / 8) * (ny / 16) * (nz / tz) * nb);
+      kern<<<blocks, CONV_M, smem, st>>>((const __nv_bfloat16*)x, cin, (const __nv_bfloat16*)w, bias,
+                                         (__nv_bfloat16*)y, yf, cout, ldy, KCt, g, relu, status);
+      e = cudaGetLastError();
+    };
+    if (tz == 4) launch(k_conv_fwd_tiled<4>);
+    else if (tz == 2) launch(k_conv_fwd_tiled<2>);
+    else launch(k_conv_fwd_tiled<1>);
+    if (e != cudaSuccess) return report_error(LB_ECUDA, std::string("conv fwd (tiled): ") + cudaGetErrorString(e));
+    count_launches(1);
+    return LB_OK;
+  }
   const int KC = pick_kc(cin);
   const size_t smem = conv_fwd_smem(cout, KC);
   const unsigned blocks = (unsigned)((nvox + CONV_M - 1) / CONV_M);
-  cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (taps == 27) {
     e = cudaFuncSetAttribute(k_conv_fwd<27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -29,6 +29,7 @@ struct Phys {
   double g[3];
   int g_mode;
   int halo;   // phi tile halo of the near-contact pass: K + 1 (1 without near contact)
+  int collision;  // 0 BGK, 1 regularised
 };
 
 // Device pointers of one population lattice.  Two-set storage: f holds

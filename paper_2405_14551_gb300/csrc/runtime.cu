@@ -28,7 +28,7 @@ namespace {
 
 constexpr int STEPS_PER_GRAPH = 16;
 constexpr uint32_t CKPT_MAGIC = 0x4742434cu;  // "LCBG"
-constexpr uint32_t CKPT_VERSION = 1;
+constexpr uint32_t CKPT_VERSION = 2;  // 2: lb_params carries the collision model
 
 std::atomic<uint64_t> g_launches{0};
 thread_local std::string g_last_error;
@@ -195,6 +195,7 @@ int validate(const lb_grid* gr, const lb_params* p) {
   if (!fin(p->g[0]) || !fin(p->g[1]) || !fin(p->g[2])) return set_err(LB_EINVAL, "g must be finite");
   if (p->g_mode < 0 || p->g_mode > 2) return set_err(LB_EINVAL, "g_mode must be 0, 1 or 2");
   if (p->storage < 0 || p->storage > 3) return set_err(LB_EINVAL, "unknown storage format");
+  if (p->collision < 0 || p->collision > 1) return set_err(LB_EINVAL, "collision must be 0 (BGK) or 1 (regularised)");
   return LB_OK;
 }
 
@@ -339,6 +340,7 @@ int lb_create(const lb_grid* grid, const lb_params* params, const lb_alloc* allo
   for (int a = 0; a < 3; ++a) p.g[a] = params->g[a];
   p.g_mode = params->g_mode;
   p.halo = params->A_h != 0.0 ? p.K + 1 : 1;
+  p.collision = params->collision;
   if (alloc && alloc->alloc && alloc->free) {
     h->alloc = *alloc;
     h->have_alloc = true;
@@ -769,6 +771,49 @@ int lb_load(lb_handle* h, const char* path) {
   }
   h->t = t;
   h->initialised = true;
+  return LB_OK;
+}
+
+int lb_copy_state(lb_handle* dst, lb_handle* src) {
+  if (!dst || !src) return set_err(LB_EINVAL, "null handle");
+  if (dst == src) return LB_OK;
+  if (!src->initialised) return set_err(LB_ESTATE, "source handle not initialised");
+  if (src->grid.nx != dst->grid.nx || src->grid.ny != dst->grid.ny || src->grid.nz != dst->grid.nz ||
+      src->grid.walls != dst->grid.walls || src->storage != dst->storage)
+    return set_err(LB_EINVAL, "handles differ in grid or storage");
+  const size_t N = (size_t)src->g.N;
+  cudaError_t e = cudaStreamSynchronize(src->stream);
+  if (e == cudaSuccess && src->mode == 1) {
+    const StateBuf& a = src->S[src->cur];
+    const StateBuf& b = dst->S[dst->cur];
+    if (storage_is_twoset(src->storage)) {
+      e = cudaMemcpyAsync(b.f, a.f, state_bytes(src), cudaMemcpyDeviceToDevice, dst->stream);
+    } else {
+      const size_t fb = (size_t)Q * N * elem_bytes(src->storage);
+      e = cudaMemcpyAsync(b.f, a.f, fb, cudaMemcpyDeviceToDevice, dst->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b.sv, a.sv, N * sizeof(float4), cudaMemcpyDeviceToDevice, dst->stream);
+    }
+  } else if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(dst->init_phi, src->init_phi, N * sizeof(float), cudaMemcpyDeviceToDevice, dst->stream);
+    if (e == cudaSuccess && src->use_rho) {
+      if (!dst->init_rho && !(dst->init_rho = (float*)dev_alloc(dst, N * sizeof(float))))
+        return set_err(LB_ENOMEM, "field buffer allocation failed");
+      e = cudaMemcpyAsync(dst->init_rho, src->init_rho, N * sizeof(float), cudaMemcpyDeviceToDevice, dst->stream);
+    }
+    if (e == cudaSuccess && src->use_u) {
+      if (!dst->init_u && !(dst->init_u = (float*)dev_alloc(dst, 3 * N * sizeof(float))))
+        return set_err(LB_ENOMEM, "field buffer allocation failed");
+      e = cudaMemcpyAsync(dst->init_u, src->init_u, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, dst->stream);
+    }
+    if (e == cudaSuccess) e = launch_phi_from_init(dst->storage, dst->g, dst->init_phi, dst->phi, dst->stream);
+  }
+  if (e != cudaSuccess) return cuda_err(e, "copy state");
+  dst->mode = src->mode;
+  dst->use_rho = src->use_rho;
+  dst->use_u = src->use_u;
+  dst->regularised = src->regularised;
+  dst->t = src->t;
+  dst->initialised = true;
   return LB_OK;
 }
 

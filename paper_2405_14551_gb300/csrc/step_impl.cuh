@@ -274,7 +274,7 @@ __device__ __forceinline__ void fields_node(const InitBuf& I, const Geo& g, cons
 // pass 1: phase field
 // ---------------------------------------------------------------------------
 // pull_fast is defined with the fused step below
-template <int ST, bool WALLFREE, bool IDX32>
+template <int ST, bool WALLFREE, bool IDX32, bool TOTALS>
 __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const Nbr& n, int self,
                                           typename Store<ST>::R f[Q], typename Store<ST>::R& rA,
                                           typename Store<ST>::R& rB);
@@ -301,9 +301,9 @@ __device__ __forceinline__ void phi_node(const View<ST>& S, const Geo& g, long l
   make_nbr(g, x, y, z, n);
   R f[Q], rA, rB;
   if (near_wall(g, x, y, z))
-    pull_fast<ST, false, IDX32>(S, g, n, (int)idx, f, rA, rB);
+    pull_fast<ST, false, IDX32, false>(S, g, n, (int)idx, f, rA, rB);
   else
-    pull_fast<ST, true, IDX32>(S, g, n, (int)idx, f, rA, rB);
+    pull_fast<ST, true, IDX32, false>(S, g, n, (int)idx, f, rA, rB);
   phi[idx] = (rA - rB) / (rA + rB);
 }
 
@@ -368,8 +368,10 @@ __device__ __forceinline__ void tile_grad(const R* sp, int c, int SX, int SXY, R
 
 // Pull for the hot path: totals f_i and component densities.  WALLFREE: no
 // neighbour of the node is solid (no bounce-back test).  IDX32: every
-// population offset fits in 32 bits.
-template <int ST, bool WALLFREE, bool IDX32>
+// population offset fits in 32 bits.  TOTALS (reduced storage): only the
+// totals f_i; the neighbours' colour scalars are not read and rA, rB are left
+// to the caller.
+template <int ST, bool WALLFREE, bool IDX32, bool TOTALS>
 __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const Nbr& n, int self,
                                           typename Store<ST>::R f[Q], typename Store<ST>::R& rA,
                                           typename Store<ST>::R& rB) {
@@ -400,6 +402,8 @@ __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const
       f[i] = va + vb;
       rA += va;
       rB += vb;
+    } else if constexpr (TOTALS) {
+      f[i] = decode<ST>(S.f[dir * N + (I)src], i);
     } else {
       const R fs = decode<ST>(S.f[dir * N + (I)src], i);
       const float4 sv = S.sv[src];
@@ -649,7 +653,7 @@ __global__ void __launch_bounds__(TX* TY) k_nc(const typename Store<ST>::R* __re
 
 // The nodes of one fused-step tile; sp holds phi of the tile with a one-node
 // halo, hnc the near-contact distance of every node (read when A_h != 0).
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32>
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32, bool REG>
 __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O, const InitBuf& init, const Geo& g,
                                            const Phys& P, const unsigned char* __restrict__ hnc,
                                            typename Store<ST>::R* __restrict__ fields,
@@ -676,8 +680,22 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
     Nbr n;
     make_nbr(g, x, y, z, n);
     R f[Q], rA, rB;
+    const int c = (lz + 1) * SXY + (threadIdx.y + 1) * SX + (threadIdx.x + 1);
+    const R phx = sp[c];
     if constexpr (LOADER == LOAD_PULL) {
-      pull_fast<ST, WALLFREE, IDX32>(S, g, n, self, f, rA, rB);
+      if constexpr (Store<ST>::TWOSET) {
+        pull_fast<ST, WALLFREE, IDX32, false>(S, g, n, self, f, rA, rB);
+      } else {
+        // reduced state: the component densities follow from the total and
+        // this time level's phase field phi = (rhoA - rhoB)/rho (the tile),
+        // so the neighbours' colour scalars need not be read again
+        pull_fast<ST, WALLFREE, IDX32, true>(S, g, n, self, f, rA, rB);
+        R rt = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rt += f[i];
+        rA = R(0.5) * rt * (R(1) + phx);
+        rB = rt - rA;
+      }
     } else {
       fields_node<R, false>(init, g, P, n, (long long)self, f, rA, rB, nullptr, nullptr);
     }
@@ -695,8 +713,6 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
     }
 
     // colour gradient from the tile; near-contact distance from the scan pass
-    const int c = (lz + 1) * SXY + (threadIdx.y + 1) * SX + (threadIdx.x + 1);
-    const R phx = sp[c];
     R gr[3];
     tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
     const R gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
@@ -780,9 +796,38 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
     const R r45 = R(4.5) * rho;
     const R r3 = R(3) * rho;
     const R g9 = R(9) * guo, g3 = R(3) * guo, gm3uF = -R(3) * guo * uF;
+    // BGK relaxes f towards feq: keep f + omega feq.  The regularised
+    // collision (collision == 1) keeps feq and relaxes the non-equilibrium
+    // part projected on Hermite orders 1 and 2:
+    //   feq + keep w [3 c.J + 4.5 (c.Pi.c - tr(Pi)/3)],
+    //   J = j - rho u = -F/2,  Pi = sum_i c c f_i - rho (u u + I/3).
+    constexpr bool reg = REG;
+    const R wf = reg ? R(1) : omega;
+    R Pxx = R(0), Pyy = R(0), Pzz = R(0), Pxy = R(0), Pxz = R(0), Pyz = R(0), trP = R(0);
+    if constexpr (reg) {
+#pragma unroll
+      for (int p = 0; p < REST; ++p) {
+        const R sp2 = f[p] + f[opp(p)];
+        if (cx(p)) Pxx += sp2;
+        if (cy(p)) Pyy += sp2;
+        if (cz(p)) Pzz += sp2;
+        if (cx(p) && cy(p)) Pxy += R(cx(p) * cy(p)) * sp2;
+        if (cx(p) && cz(p)) Pxz += R(cx(p) * cz(p)) * sp2;
+        if (cy(p) && cz(p)) Pyz += R(cy(p) * cz(p)) * sp2;
+      }
+      const R r3rd = rho * (R(1) / R(3));
+      Pxx -= rho * u0 * u0 + r3rd;
+      Pyy -= rho * u1 * u1 + r3rd;
+      Pzz -= rho * u2 * u2 + r3rd;
+      Pxy -= rho * u0 * u1;
+      Pxz -= rho * u0 * u2;
+      Pyz -= rho * u1 * u2;
+      trP = Pxx + Pyy + Pzz;
+    }
     {  // rest direction
       const R W = wgt<R>(REST);
-      const R fs = keep * f[REST] + omega * W * r0 - bweight<R>(REST) * A2g + W * gm3uF;
+      const R rel = reg ? R(-1.5) * W * trP : f[REST];
+      const R fs = keep * rel + wf * W * r0 - bweight<R>(REST) * A2g + W * gm3uF;
       if constexpr (Store<ST>::TWOSET) {
         const R fa = sA * fs;
         O.f[(I)REST * N + (I)self] = encode<ST>(fa, REST);
@@ -799,11 +844,25 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       if (cx(p)) { cu += R(cx(p)) * u0; cF += R(cx(p)) * F0; cg += R(cx(p)) * gr[0]; }
       if (cy(p)) { cu += R(cy(p)) * u1; cF += R(cy(p)) * F1; cg += R(cy(p)) * gr[1]; }
       if (cz(p)) { cu += R(cz(p)) * u2; cF += R(cz(p)) * F2; cg += R(cz(p)) * gr[2]; }
-      const R even = W * (omega * (r0 + r45 * cu * cu) + g9 * cu * cF + gm3uF + A2ig * cg * cg) -
-                     bweight<R>(p) * A2g;
-      const R odd = W * (omega * r3 * cu + g3 * cF);
-      const R fsp = keep * f[p] + even + odd;
-      const R fsq = keep * f[q] + even - odd;
+      R even = W * (wf * (r0 + r45 * cu * cu) + g9 * cu * cF + gm3uF + A2ig * cg * cg) - bweight<R>(p) * A2g;
+      R odd = W * (wf * r3 * cu + g3 * cF);
+      R bp = f[p], bq = f[q];
+      if constexpr (reg) {
+        // c.Pi.c and c.J = -(c.F)/2 for this pair's velocity
+        R cpc = R(0);
+        if (cx(p)) cpc += Pxx;
+        if (cy(p)) cpc += Pyy;
+        if (cz(p)) cpc += Pzz;
+        if (cx(p) && cy(p)) cpc += R(2 * cx(p) * cy(p)) * Pxy;
+        if (cx(p) && cz(p)) cpc += R(2 * cx(p) * cz(p)) * Pxz;
+        if (cy(p) && cz(p)) cpc += R(2 * cy(p) * cz(p)) * Pyz;
+        even += keep * W * R(4.5) * (cpc - trP * (R(1) / R(3)));
+        odd += keep * W * R(-1.5) * cF;
+        bp = R(0);
+        bq = R(0);
+      }
+      const R fsp = keep * bp + even + odd;
+      const R fsq = keep * bq + even - odd;
       if constexpr (Store<ST>::TWOSET) {
         const R seg = segamp * W * inv_norm<R>(p) * cg;
         const R fap = sA * fsp + seg;
@@ -835,10 +894,21 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
   using R = typename Store<ST>::R;
   // a tile whose halo holds no solid node needs no bounce-back or wall tests
   const bool wallfree = stage_phi<R, TX, TY>(phi, g, 1, 1, TZ + 2, sp, x0, y0, z0);
-  if (wallfree)
-    step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32>(S, O, init, g, P, hnc, fields, status, sp, x0, y0, z0);
-  else
-    step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32>(S, O, init, g, P, hnc, fields, status, sp, x0, y0, z0);
+  if (P.collision == 1) {  // regularised collision
+    if (wallfree)
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, true>(S, O, init, g, P, hnc, fields, status, sp, x0,
+                                                                    y0, z0);
+    else
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, true>(S, O, init, g, P, hnc, fields, status, sp, x0,
+                                                                     y0, z0);
+  } else {
+    if (wallfree)
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, false>(S, O, init, g, P, hnc, fields, status, sp, x0,
+                                                                     y0, z0);
+    else
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, false>(S, O, init, g, P, hnc, fields, status, sp, x0,
+                                                                      y0, z0);
+  }
   __syncthreads();
 }
 

@@ -45,6 +45,7 @@ class lb_params(ctypes.Structure):
         ("g", ctypes.c_double * 3),
         ("g_mode", ctypes.c_int32),
         ("storage", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
     ]
 
 
@@ -69,6 +70,7 @@ _SIGS = {
     "lb_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "lb_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lb_set_nc_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lb_copy_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lb_get_nc_tile": (ctypes.c_int, [ctypes.c_void_p]),
     "lb_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "lb_get_tile": (ctypes.c_int, [ctypes.c_void_p]),
@@ -182,7 +184,7 @@ def make_grid(nx, ny, nz, walls=0) -> lb_grid:
 
 
 def make_params(tau_a=1.0, tau_b=1.0, A_a=0.01, A_b=0.01, beta=0.7, A_h=0.0, h_min=3.0, h_max=3.0, phi_I=0.9,
-                g=(0.0, 0.0, 0.0), g_mode=0, storage="twoset_f32") -> lb_params:
+                g=(0.0, 0.0, 0.0), g_mode=0, storage="twoset_f32", collision=0) -> lb_params:
     st = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p = lb_params()
     p.tau_a, p.tau_b, p.A_a, p.A_b, p.beta = tau_a, tau_b, A_a, A_b, beta
@@ -190,6 +192,7 @@ def make_params(tau_a=1.0, tau_b=1.0, A_a=0.01, A_b=0.01, beta=0.7, A_h=0.0, h_m
     p.g[0], p.g[1], p.g[2] = g
     p.g_mode = int(g_mode)
     p.storage = st
+    p.collision = int(collision)
     return p
 
 
@@ -248,6 +251,10 @@ def lb_step_timed(h, nsteps: int):
     ms = np.zeros(3)
     _check(load_library().lb_step_timed(h, int(nsteps), ms.ctypes.data), "lb_step_timed")
     return float(ms[0]), float(ms[1]), float(ms[2])
+
+
+def lb_copy_state(dst, src):
+    _check(load_library().lb_copy_state(dst, src), "lb_copy_state")
 
 
 def lb_set_nc_tile(h, variant: int):

@@ -349,13 +349,19 @@ def train(net, trajs, shape, iters=300, lr=1e-3, seed=0, stream=None, wch=(4.0, 
 class Controller:
     """Alternate K plain LB steps with one surrogate jump of K steps.
 
-    After a jump the candidate fields are checked on a monitor lattice: the
-    droplet count must not change, the dispersed volume sum((1+phi)/2) must
-    stay within vol_tol (relative) and phi within [-1, 1] + phi_tol.  An
-    accepted jump re-initialises the lattice by regularised reconstruction;
-    a rejected one is replaced by K plain LB steps (fallback)."""
+    Every candidate is checked on a monitor lattice: the droplet count must
+    not change, the dispersed volume sum((1+phi)/2) must stay within vol_tol
+    (relative), and phi is clamped to [-1, 1].  Every judge_every-th jump
+    (and the first) is also judged by the plain LB: the same K steps run from
+    the exact pre-jump state on a shadow lattice (lb_copy_state), and the
+    surrogate's mean |phi_sur - phi_LB| must not exceed phi_tol.  A rejected
+    candidate is replaced by the LB result (the judge's lattice when it ran,
+    else K plain steps); a failed judgement also suspends the surrogate for
+    backoff cycles.  An accepted jump re-initialises the lattice by
+    regularised reconstruction."""
 
-    def __init__(self, sim, net, shape, K=50, vol_tol=0.02, phi_tol=0.05, stream=None):
+    def __init__(self, sim, net, shape, K=50, vol_tol=0.02, phi_tol=1e-2, judge_every=4, backoff=8,
+                 stream=None):
         import torch
         self.torch = torch
         self.sim, self.net, self.K = sim, net, K
@@ -365,43 +371,80 @@ class Controller:
         N = nx * ny * nz
         p = workload_params()
         self.monitor = L.Sim(nx, ny, nz, walls=0b010, stream=self.stream, storage="reduced_f16", **p)
+        self.shadow = L.Sim(nx, ny, nz, walls=0b010, stream=self.stream, storage=sim.storage, **p)
         self.x = torch.empty((N, CIN), dtype=torch.bfloat16, device=net.dev)
         self.out = torch.empty((5, N), dtype=torch.float32, device=net.dev)
         self.vol_tol, self.phi_tol = vol_tol, phi_tol
+        self.judge_every, self.backoff = judge_every, backoff
         self.accepted = 0
         self.rejected = 0
+        self.judged = []       # (cycle, mean |phi_sur - phi_LB|, max)
+        self.suspended = 0
+        self.cycle = 0
+        self.jumps = 0
 
     def jump(self):
-        """One surrogate jump; returns (accepted, info)."""
+        """One surrogate jump (or its LB replacement); returns (accepted, info)."""
+        # every tensor operation on the library's stream: its allocations and
+        # arithmetic are then ordered with the kernels that fill and read them
+        with self.torch.cuda.stream(self.stream):
+            return self._jump()
+
+    def _jump(self):
         nx, ny, nz = self.shape
+        judge = self.jumps % self.judge_every == 0
+        self.jumps += 1
+        if judge:
+            L.lb_copy_state(self.shadow.h, self.sim.h)
+            self.shadow.step(self.K)
         f0 = self.sim.fields_device(FIELD_MASK).reshape(5, -1)
         count0 = self.sim.droplet_count()
         vol0 = float(self.sim.reduce()[5])
         pack_input(f0, self.x, self.stream)
         y = self.net.forward(self.x, (nx, ny, nz, 1))
         unpack_output(f0, y, self.out, self.stream)
-        # monitors on the candidate
         self.monitor.init_fields(self.out[0], self.out[1], self.out[2:5], regularised=False)
         count1 = self.monitor.droplet_count()
         vol1 = float(self.monitor.reduce()[5])
-        phi_ok = True  # unpack clamps phi to [-1, 1]
-        ok = count1 == count0 and abs(vol1 - vol0) <= self.vol_tol * max(vol0, 1.0) and phi_ok
-        info = {"count0": count0, "count1": count1, "vol_rel": (vol1 - vol0) / max(vol0, 1.0)}
+        ok = count1 == count0 and abs(vol1 - vol0) <= self.vol_tol * max(vol0, 1.0)
+        info = {"count0": count0, "count1": count1, "vol_rel": (vol1 - vol0) / max(vol0, 1.0), "judged": judge}
+        if judge:
+            phi_lb = self.shadow.fields_device(1).reshape(-1)
+            d = (self.out[0] - phi_lb).abs()
+            err, emax = float(d.mean()), float(d.max())
+            self.judged.append((self.cycle, err, emax))
+            info["phi_err"], info["phi_err_max"] = err, emax
+            if err > self.phi_tol:
+                ok = False
+                self.suspended = self.backoff
         if ok:
             self.sim.init_fields(self.out[0], self.out[1], self.out[2:5], regularised=True)
             self.accepted += 1
         else:
-            self.sim.step(self.K)  # fallback: the plain method
+            if judge:
+                L.lb_copy_state(self.sim.h, self.shadow.h)  # the judge's exact LB result
+            else:
+                self.sim.step(self.K)  # fallback: the plain method
             self.rejected += 1
         return ok, info
 
     def run(self, cycles):
-        """cycles x (K LB steps + one jump of K steps)."""
+        """cycles x (K LB steps + one jump of K steps, or 2K LB steps while the
+        surrogate is suspended)."""
         infos = []
         for _ in range(cycles):
-            self.sim.step(self.K)
-            infos.append(self.jump())
+            with self.torch.cuda.stream(self.stream):
+                self.sim.step(self.K)
+            if self.suspended > 0:
+                with self.torch.cuda.stream(self.stream):
+                    self.sim.step(self.K)
+                self.suspended -= 1
+                infos.append((None, {"suspended": True}))
+            else:
+                infos.append(self.jump())
+            self.cycle += 1
         return infos
 
     def close(self):
         self.monitor.close()
+        self.shadow.close()

@@ -221,6 +221,33 @@ def test_checkpoint_resume_bitwise(tmp_path):
             np.testing.assert_array_equal(fa[k], fb[k])
 
 
+def test_copy_state_bitwise():
+    """lb_copy_state: a copy taken after 23 steps (odd parity on the source,
+    even on the target) and one taken before any step continue bitwise like
+    the source."""
+    import paper_2405_14551_gb300.lbcg as L
+    wl = W.droplet_pair(32, 32, 48, R=7.0, sep=17.0)
+    for storage in ("twoset_f32", "reduced_f16"):
+        a = make_gpu(wl, storage=storage)
+        c = make_gpu(wl, storage=storage)
+        c.step(2)
+        L.lb_copy_state(c.h, a.h)  # a has not stepped: the initial fields
+        a.step(23)
+        b = make_gpu(wl, storage=storage)
+        L.lb_copy_state(b.h, a.h)
+        assert b.t == 23
+        a.step(9)
+        b.step(9)
+        c.step(32)
+        fa, fb, fc = a.fields(), b.fields(), c.fields()
+        for k in fa:
+            np.testing.assert_array_equal(fa[k], fb[k])
+            np.testing.assert_array_equal(fa[k], fc[k])
+    other = make_gpu(W.droplet_pair(32, 32, 40, R=7.0, sep=17.0))
+    with pytest.raises(L.LBError):
+        L.lb_copy_state(other.h, a.h)
+
+
 def test_regularised_reconstruction_matches_oracle():
     nx, ny, nz = 12, 10, 14
     rng = np.random.default_rng(3)
@@ -240,3 +267,28 @@ def test_regularised_reconstruction_matches_oracle():
         ga, gb = s.populations()
         assert np.abs(ga.reshape(27, -1) - oa).max() < tol
         assert np.abs(gb.reshape(27, -1) - ob).max() < tol
+
+
+@pytest.mark.parametrize("storage,tol", [("twoset_f32", 1e-5), ("reduced_f32", 1e-5), ("reduced_f16", None),
+                                         ("twoset_f64", 1e-11)])
+def test_regularised_collision_matches_oracle(storage, tol):
+    """The regularised collision (collision = 1) against the oracle's: small
+    droplet at tau 0.8 (where it differs from BGK) with a channel wall pair,
+    body force and near contact, 120 steps; the FP16-deviation storage is
+    reported against the same bounds as for BGK."""
+    wl = W.Workload("reg", (28, 26, 30), 0b010, dict(W.BASE, tau_a=0.8, tau_b=0.65, A_h=0.1, g=(0.0, 0.0, 2e-5),
+                                                       g_mode=1), 120,
+                    centres=np.array([[14.0, 13.0, 9.0], [14.5, 13.0, 21.0]]), radii=np.array([5.0, 5.0]))
+    o = make_oracle(wl, collision=1)
+    s = make_gpu(wl, storage=storage, collision=1)
+    o.step(120)
+    s.step(120)
+    e = field_errors(s.fields(f64=True), o.fields(), CMP_FIELDS)
+    print(storage, e)
+    if tol is None:
+        assert e["phi"] <= 5e-3 and max(e["rho"], e["ux"], e["uy"], e["uz"]) <= 1e-3
+    else:
+        assert max(e.values()) <= tol, e
+    b = make_oracle(wl)  # BGK differs at tau != 1: the flag reaches the collision
+    b.step(120)
+    assert field_errors(b.fields(), o.fields(), ("ux",))["ux"] > 1e-9

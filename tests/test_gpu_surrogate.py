@@ -55,6 +55,46 @@ def test_conv_forward(dims, cin, cout, taps, per, relu):
     assert np.abs(Yf.cpu().numpy() - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("dims,cin,cout,per,relu,ldy", [
+    ((8, 16, 4, 1), 16, 32, 7, 0, 0), ((16, 16, 4, 2), 32, 64, 5, 1, 0), ((8, 32, 2, 1), 96, 32, 2, 0, 0),
+    ((8, 16, 3, 1), 64, 128, 0, 1, 0), ((8, 16, 4, 1), 384, 128, 5, 1, 0), ((16, 16, 4, 1), 128, 256, 7, 0, 0),
+    ((8, 16, 8, 1), 32, 16, 7, 1, 0), ((8, 16, 4, 1), 32, 32, 5, 0, 64)])
+def test_conv_forward_tiled(dims, cin, cout, per, relu, ldy):
+    """Grids with nx % 8 == 0 and ny % 16 == 0 take the spatially tiled kernel
+    (input block staged once per channel chunk, TZ planes per CTA); the same
+    comparison as above, including a strided output (ldy > cout)."""
+    import torch
+    import paper_2405_14551_gb300.lbcg as L
+    lib = L.load_library()
+    rng = np.random.default_rng(cin * 5 + cout + dims[2])
+    nx, ny, nz, nb = dims
+    X = _bf(rng.standard_normal((nb, nz, ny, nx, cin)))
+    W = _bf(rng.standard_normal((cout, 27, cin)) / np.sqrt(27 * cin))
+    b = rng.standard_normal(cout).astype(np.float32)
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).to(dev)
+    Wd = torch.from_numpy(W.astype(np.float32)).to(torch.bfloat16).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    ld = ldy or cout
+    Yf = torch.full((nb, nz, ny, nx, ld), 7.0, dtype=torch.float32, device=dev)
+    Yb = torch.zeros((nb, nz, ny, nx, ld), dtype=torch.bfloat16, device=dev)
+    st = torch.zeros(4, dtype=torch.int32, device=dev)
+    rc = lib.lbnn_conv3d_fwd(Xd.data_ptr(), cin, Wd.data_ptr(), 27, bd.data_ptr(), Yb.data_ptr(), Yf.data_ptr(), cout,
+                             ldy, nx, ny, nz, nb, per, relu, st.data_ptr(), None)
+    assert rc == 0, lib.lb_last_error()
+    torch.cuda.synchronize()
+    ref = U.conv3d(X, W, b.astype(np.float64), (per & 1, (per >> 1) & 1, (per >> 2) & 1), 27)
+    if relu:
+        ref = np.maximum(ref, 0)
+    assert int(st[0].item()) == 0
+    got = Yf.cpu().numpy()
+    assert np.abs(got[..., :cout] - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+    if ld > cout:
+        assert np.all(got[..., cout:] == 7.0)  # columns beyond cout untouched
+    gb = Yb.float().cpu().numpy()[..., :cout]
+    assert np.abs(gb - ref).max() <= 1e-2 * max(1.0, np.abs(ref).max())  # BF16 copy of the same values
+
+
 @pytest.mark.parametrize("dims,cin,cout,taps,per,vpc", [
     ((8, 4, 4, 1), 16, 16, 1, 7, 64), ((8, 4, 4, 1), 16, 32, 27, 7, 64), ((8, 8, 8, 1), 32, 64, 27, 5, 128),
     ((8, 4, 8, 2), 96, 32, 27, 2, 64), ((8, 4, 4, 1), 128, 256, 27, 5, 64)])
@@ -137,3 +177,4 @@ def test_training_lowers_the_loss():
     net = S.UNet(base=16, seed=1)
     hist = S.train(net, [[f0, f1]], shape, iters=40, lr=2e-3, log_every=39)
     assert hist[-1][1] < 0.75 * hist[0][1], hist
+

@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the other storage formats")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep measurement")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate training and controller run")
     ap.add_argument("--shape", default=None, help="nx,ny,nz of a smaller emulsion (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-tune", action="store_true", help="use --tile without autotuning")
@@ -279,6 +280,83 @@ def batch_extra(args, L, W, stream):
             "speedup": round(ms_seq / mb, 3)}
 
 
+def surrogate_extra(L, stream, ntraj=8, iters=600, cycles=12):
+    """The learned surrogate on the 128x128x256 dense emulsion: trajectories
+    from the LB itself (seeded emulsions, 200 spin-up steps, snapshots 50 steps
+    apart), a bounded training run of the BF16 U-Net on the library's tcgen05
+    kernels, its per-jump phi error on held-out pairs against the persistence
+    forecast, and the controller (50 LB steps + one jump, plain-LB judge every
+    4th jump, phi tolerance 1e-2) timed against plain LB from the same state."""
+    import time
+    import torch
+    from paper_2405_14551_gb300 import surrogate as S
+    from paper_2405_14551_gb300 import workloads as W
+    shape = (128, 128, 256)
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    t0 = time.time()
+    with torch.cuda.stream(stream):
+        trajs = S.generate_pairs(range(ntraj), shape=shape, spinup=200, snaps=6, stream=stream)
+        test = S.generate_pairs([1000], shape=shape, spinup=200, snaps=6, stream=stream)
+        net = S.UNet(base=32, seed=0, stream=stream)
+        t1 = time.time()
+        S.train(net, trajs, shape, iters=iters, lr=1e-3, stream=stream, log_every=iters)
+        torch.cuda.synchronize()
+        t_train = time.time() - t1
+        x = torch.empty((n, S.CIN), dtype=torch.bfloat16, device="cuda")
+        out = torch.empty((5, n), dtype=torch.float32, device="cuda")
+        err, pers = [], []
+        for f0, f1 in zip(test[0][:-1], test[0][1:]):
+            S.pack_input(f0, x, stream)
+            y = net.forward(x, (nx, ny, nz, 1))
+            S.unpack_output(f0, y, out, stream)
+            err.append(float((out[0] - f1[0]).abs().mean()))
+            pers.append(float((f0[0] - f1[0]).abs().mean()))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            net.forward(x, (nx, ny, nz, 1))
+        e0.record(stream)
+        for _ in range(5):
+            net.forward(x, (nx, ny, nz, 1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / 5
+        del trajs, test
+        p = S.workload_params()
+        phi, _ = W.dense_emulsion_phi(shape, 0b010, 1001, device=torch.device("cuda"))
+        a = L.Sim(nx, ny, nz, walls=0b010, stream=stream, **p)
+        b = L.Sim(nx, ny, nz, walls=0b010, stream=stream, **p)
+        for s_ in (a, b):
+            s_.init_fields(phi)
+            s_.step(200)
+        ctl = S.Controller(a, net, shape, stream=stream)
+        torch.cuda.synchronize()
+        t2 = time.time()
+        ctl.run(cycles)
+        torch.cuda.synchronize()
+        t_ctl = time.time() - t2
+        t3 = time.time()
+        b.step(cycles * 100)
+        torch.cuda.synchronize()
+        t_lb = time.time() - t3
+        fa, fb = a.fields_device(1).reshape(-1), b.fields_device(1).reshape(-1)
+        final_err = float((fa - fb).abs().mean())
+        counts = (a.droplet_count(), b.droplet_count())
+        judged = [(c, round(e, 4)) for c, e, _ in ctl.judged]
+        acc, rej = ctl.accepted, ctl.rejected
+        ctl.close()
+        a.close()
+        b.close()
+    torch.cuda.empty_cache()
+    return {"workload": "dense_emulsion_128x128x256 surrogate, K = 50", "train_trajectories": ntraj,
+            "train_pairs": ntraj * 5, "train_iters": iters, "train_s": round(t_train, 1),
+            "unet_forward_ms": round(fwd_ms, 2), "lb_50_steps_ms": round(t_lb / (cycles * 2) * 1e3, 2),
+            "phi_err_per_jump": round(sum(err) / len(err), 4), "persistence_err": round(sum(pers) / len(pers), 4),
+            "phi_tol": 1e-2, "controller_cycles": cycles, "accepted": acc, "rejected": rej, "judged": judged,
+            "speedup_vs_plain_lb": round(t_lb / t_ctl, 3), "final_phi_err_vs_plain": round(final_err, 5),
+            "droplet_count_ctrl_plain": list(counts), "total_s": round(time.time() - t0, 1)}
+
+
 def cpu_baseline(wl):
     cores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
@@ -400,6 +478,8 @@ def main():
     extra = {} if args.no_extra else other_storages(args, L, make, stream, best_tile, best_nc, world, nodes, maxall, peak)
     if not args.no_batch and not args.shape:
         extra["batch"] = batch_extra(args, L, W, stream)
+    if not args.no_surrogate and not args.shape and world == 1:
+        extra["surrogate"] = surrogate_extra(L, stream)
     cpu = cpu_baseline(wl) if (rank == 0 and world == 1 and not args.no_cpu) else None
 
     if rank == 0:

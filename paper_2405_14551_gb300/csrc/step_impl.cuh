@@ -568,7 +568,7 @@ __device__ __forceinline__ void nc_queue(const R* sp, const unsigned short* queu
 
 // x halo of the near-contact tile: H rounded up to whole 16-byte vectors.
 template <typename R, int H>
-constexpr int nc_halo_x() {
+__host__ __device__ constexpr int nc_halo_x() {
   constexpr int V = 16 / (int)sizeof(R);
   return (H + V - 1) / V * V;
 }

@@ -144,9 +144,9 @@ int lb_init_fields(lb_handle* h, const float* phi, const float* rho, const float
  * are replayed from a captured CUDA graph. */
 int lb_step(lb_handle* h, int64_t nsteps);
 
-/* Choose the tile shape of the fused step kernel (0..3: 32x8x4, 32x8x8,
- * 32x8x4 with a register cap for 3 CTAs per SM, 64x4x4 nodes per CTA); used
- * by the autotuner.  Results do not
+/* Choose the tile shape of the fused step kernel (0..4: 32x8x4, 32x8x8,
+ * 32x8x4 with a register cap for 3 CTAs per SM, 64x4x4, 32x8x4 capped for 4
+ * CTAs per SM, nodes per CTA); used by the autotuner.  Results do not
  * depend on the tile.  lb_get_tile returns the current index. */
 int lb_set_tile(lb_handle* h, int tile);
 int lb_get_tile(const lb_handle* h);
@@ -250,7 +250,7 @@ int lb_batch_step(lb_batch* b, int64_t nsteps);
 /* The one-run-at-a-time baseline: lb_step on each run in turn. */
 int lb_batch_step_sequential(lb_batch* b, int64_t nsteps);
 
-/* Tile shape (0..3, as lb_set_tile) and persistent CTAs per SM (1..16). */
+/* Tile shape (0..4, as lb_set_tile) and persistent CTAs per SM (1..16). */
 int lb_batch_set_tile(lb_batch* b, int tile, int blocks_per_sm);
 
 /* Autotuner: time `steps` batched steps for every tile shape and CTAs-per-SM

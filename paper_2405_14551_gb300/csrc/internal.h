@@ -68,7 +68,7 @@ struct RunDesc {
 struct Tile {
   int tx, ty, tz;
 };
-constexpr int NUM_TILES = 4;
+constexpr int NUM_TILES = 5;
 extern const Tile kTiles[NUM_TILES];
 
 size_t elem_bytes(int storage);

@@ -3,7 +3,8 @@
 
 namespace lbcg {
 
-const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 8, 4}, {64, 4, 4}};  // tile 2: 3 CTAs/SM register cap
+// tiles 2 and 4: the 32x8x4 tile with registers capped for 3 and 4 CTAs per SM
+const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 8, 4}, {64, 4, 4}, {32, 8, 4}};
 
 template <int ST>
 cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st);

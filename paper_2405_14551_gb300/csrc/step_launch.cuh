@@ -108,6 +108,7 @@ inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, cons
       case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8>(g, p, in, init, phi, hnc, out, fields, status, st);
       case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, 3>(g, p, in, init, phi, hnc, out, fields, status, st);
       case 3: return launch_step_t<ST, LOADER, WS, WF, 64, 4, 4>(g, p, in, init, phi, hnc, out, fields, status, st);
+      case 4: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, 4>(g, p, in, init, phi, hnc, out, fields, status, st);
       default: break;
     }
   }
@@ -178,6 +179,7 @@ inline cudaError_t launch_batched_tiles(int tile, const RunDesc* d_runs, int nru
     case 1: return launch_batched_step_t<ST, 32, 8, 8, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
     case 2: return launch_batched_step_t<ST, 32, 8, 4, IDX32, 3>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
     case 3: return launch_batched_step_t<ST, 64, 4, 4, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
+    case 4: return launch_batched_step_t<ST, 32, 8, 4, IDX32, 4>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
     default: return launch_batched_step_t<ST, 32, 8, 4, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
   }
 }

@@ -351,12 +351,13 @@ class Controller:
 
     Every candidate is checked on a monitor lattice: the droplet count must
     not change, the dispersed volume sum((1+phi)/2) must stay within vol_tol
-    (relative), and phi is clamped to [-1, 1].  Every judge_every-th jump
-    (and the first) is also judged by the plain LB: the same K steps run from
-    the exact pre-jump state on a shadow lattice (lb_copy_state), and the
-    surrogate's mean |phi_sur - phi_LB| must not exceed phi_tol.  A rejected
-    candidate is replaced by the LB result (the judge's lattice when it ran,
-    else K plain steps); a failed judgement also suspends the surrogate for
+    (relative), and phi is clamped to [-1, 1].  Jumps are also judged by the
+    plain LB: the same K steps run from the exact pre-jump state on a shadow
+    lattice (lb_copy_state), and the surrogate's mean |phi_sur - phi_LB|
+    must not exceed phi_tol.  Every jump is judged until one passes; after
+    that every judge_every-th jump is.  A rejected candidate is replaced by
+    the LB result (the judge's lattice when it ran, else K plain steps); a
+    failed judgement withdraws the trust and suspends the surrogate for
     backoff cycles.  An accepted jump re-initialises the lattice by
     regularised reconstruction."""
 
@@ -382,6 +383,7 @@ class Controller:
         self.suspended = 0
         self.cycle = 0
         self.jumps = 0
+        self.trusted = False   # set by a passing judgement
 
     def jump(self):
         """One surrogate jump (or its LB replacement); returns (accepted, info)."""
@@ -392,7 +394,7 @@ class Controller:
 
     def _jump(self):
         nx, ny, nz = self.shape
-        judge = self.jumps % self.judge_every == 0
+        judge = (not self.trusted) or self.jumps % self.judge_every == 0
         self.jumps += 1
         if judge:
             L.lb_copy_state(self.shadow.h, self.sim.h)
@@ -416,7 +418,10 @@ class Controller:
             info["phi_err"], info["phi_err_max"] = err, emax
             if err > self.phi_tol:
                 ok = False
+                self.trusted = False
                 self.suspended = self.backoff
+            else:
+                self.trusted = True
         if ok:
             self.sim.init_fields(self.out[0], self.out[1], self.out[2:5], regularised=True)
             self.accepted += 1

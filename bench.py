@@ -3,9 +3,10 @@
 
 Default workload: the confined dense emulsion, 256x256x512 nodes, walls at
 y=0/255, 70 % dispersed phase, near-contact force on, FP32 two population
-sets.  A "step" is one full LB time step (phase-field pass + fused
-collide-recolour-force-stream pass) over the whole box; the state (14.5 GB)
-is far larger than L2 (129 MB), so no flush is needed between steps.
+sets.  A "step" is one full LB time step (phase-field pass, near-contact
+scan, fused collide-recolour-force-stream pass) over the whole box; the state
+(14.5 GB) is far larger than L2 (129 MB), so no flush is needed between
+steps.
 
 Prints one JSON line (rank 0).  With torchrun and N > 1 every rank advances
 its own replica (weak scaling, no data-path collective); the time is the max
@@ -47,6 +48,46 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="tile of the fused kernel when --no-tune is given")
     ap.add_argument("--nc-tile", type=int, default=0, help="tile of the near-contact scan when --no-tune is given")
     return ap.parse_args()
+
+
+class Ranks:
+    """The ranks of a torchrun launch (one replica per GPU, no data-path
+    collective): a barrier around the timed region and the maximum of the
+    ranks' times.  backend None: a single process."""
+
+    def __init__(self, backend=None, device=None):
+        import torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.dist = None
+        self.device = device if device is not None else torch.device("cpu")
+        if self.world > 1 and backend is not None:
+            import torch.distributed as dist
+            kw = {"device_id": device} if backend == "nccl" else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def maxall(self, v):
+        if self.dist is None:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def weak_scaling_value(nodes_per_rank, steps, ms_max, world):
+    """Whole-job MLUPS: every rank's node updates over the slowest rank's time."""
+    return world * nodes_per_rank * steps / (ms_max / 1e3) / 1e6
 
 
 def peaks():
@@ -411,11 +452,7 @@ def main():
     import paper_2405_14551_gb300.lbcg as L
 
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist_
-        dist_.init_process_group("nccl", device_id=torch.device("cuda", local))
-        dist = dist_
+    ranks = Ranks("nccl", torch.device("cuda", local))
 
     L.load_library()
     dev = torch.device("cuda", local)
@@ -432,16 +469,7 @@ def main():
         s.init_fields(wl.phi)
         return s
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def maxall(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, maxall = ranks.barrier, ranks.maxall
 
     sim = make(storage)
     # autotune the tiles of the fused kernel and of the near-contact scan
@@ -477,7 +505,7 @@ def main():
     launches = L.lb_launch_count() - launches0
     ms_max = maxall(ev0.elapsed_time(ev1))
     sim.check()
-    value = world * nodes * args.steps / (ms_max / 1e3) / 1e6
+    value = weak_scaling_value(nodes, args.steps, ms_max, world)
     clocks = clk.summary()
 
     # live per-kernel timing (CUDA events on the library's stream)
@@ -532,8 +560,7 @@ def main():
             "extra": extra,
         }
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":

@@ -35,9 +35,10 @@ def _inner(shape_zyx, cut_axes, margin):
 def one_step_check(sim, wl, box, cut_axes, tol, max_flip_frac=2e-3):
     x0, y0, z0, bx, by, bz = box
     fA, fB = sim.populations(box)
-    g0 = sim.fields()
+    names = CMP_FIELDS + ("h",)
+    g0 = sim.fields(names)
     sim.step(1)
-    g1 = sim.fields()
+    g1 = sim.fields(names)
     sl = (slice(z0, z0 + bz), slice(y0, y0 + by), slice(x0, x0 + bx))
     p = dict(wl.params)
     o = oracle.OracleSim(oracle.make_params(bx, by, bz, walls=wl.walls, **p))
@@ -94,3 +95,25 @@ def test_dense_emulsion_full_size_sampled(emulsion, storage, tol):
         e0, e1, flips, active = one_step_check(s, wl, box, (0, 2), tol)
         print(storage, box, e0, e1, "flips", flips, "active", active)
         assert max(e0.values()) <= tol and max(e1.values()) <= tol
+
+
+def test_lattice_beyond_32_bit_offsets():
+    """Maximum sizes: a 512x256x608 channel (79.7 M nodes, 2 x 27 x N > 2^32
+    population offsets, so every kernel takes its 64-bit indexing path; 69 GB
+    of lattices), 40 seeded droplets, near contact and a body force; one-step
+    check of a box at the far end of the lattice against the oracle."""
+    rng = np.random.default_rng(99)
+    shape = (512, 256, 608)
+    cen, rad = W.rsa_spheres(shape, 0b010, rng, 9.0, 12.0, gap=2.0, max_count=40)
+    # three close droplets inside the checked box (near contact across 2-3 node films)
+    cen = np.vstack([cen, [[463.4, 60.2, 583.7], [464.1, 83.5, 584.6], [462.8, 106.9, 583.1]]])
+    rad = np.concatenate([rad, [10.0, 10.5, 9.8]])
+    p = dict(W.BASE, A_h=0.1, h_min=3.0, h_max=3.0, g=(0.0, 0.0, 1e-6), g_mode=1)
+    wl = W.Workload("max_size", shape, 0b010, p, 20, centres=cen, radii=rad)
+    assert 2 * 27 * wl.nodes >= 2 ** 32
+    s = make_gpu(wl)
+    s.step(16)  # one graph replay
+    s.check()
+    e0, e1, flips, active = one_step_check(s, wl, (440, 0, 560, 48, 256, 48), (0, 2), 1e-5)
+    print("max size", e0, e1, "flips", flips, "active", active)
+    assert max(e0.values()) <= 1e-5 and max(e1.values()) <= 1e-5

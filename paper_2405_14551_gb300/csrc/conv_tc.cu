@@ -14,7 +14,6 @@
 // gives up sets bit 4 of the status word.
 #include <cuda_bf16.h>
 
-#include <cstdlib>
 #include <string>
 
 #include "../../include/lbcg.h"
@@ -535,17 +534,6 @@ static size_t conv_tiled_smem(int tz, int Cin, int Cout, int KC) {
   return conv_smem(need, Cout * tz);
 }
 
-// LBNN_CONV_UNTILED=1 routes every forward convolution through the per-voxel
-// gather kernel (used to compare the two kernels).
-static bool conv_tiled_disabled() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = std::getenv("LBNN_CONV_UNTILED");
-    v = (e && e[0] == '1') ? 1 : 0;
-  }
-  return v == 1;
-}
-
 static int pick_kc(int Cin) {
   if (Cin % 64 == 0) return 64;
   if (Cin % 32 == 0) return 32;
@@ -574,7 +562,7 @@ int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, con
     return report_error(LB_EINVAL, "tensors must be 16-byte aligned");
   ConvGeo g{nx, ny, nz, nb, (int)(periodic & 1u), (int)((periodic >> 1) & 1u), (int)((periodic >> 2) & 1u)};
   cudaStream_t st = (cudaStream_t)stream;
-  if (taps == 27 && nx % 8 == 0 && ny % 16 == 0 && !conv_tiled_disabled()) {
+  if (taps == 27 && nx % 8 == 0 && ny % 16 == 0) {
     // spatially tiled kernel: TZ planes per CTA with TZ x Cout accumulator columns <= 512
     const int KCt = cin % 32 == 0 ? 32 : 16;
     int tz = 4;

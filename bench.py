@@ -330,13 +330,14 @@ def batch_extra(args, L, W, stream):
             "speedup": round(ms_seq / mb, 3)}
 
 
-def surrogate_extra(L, stream, ntraj=8, iters=600, cycles=12):
+def surrogate_extra(L, stream, ntraj=16, iters=2000, cycles=20, spinup=2000):
     """The learned surrogate on the 128x128x256 dense emulsion: trajectories
-    from the LB itself (seeded emulsions, 200 spin-up steps, snapshots 50 steps
-    apart), a bounded training run of the BF16 U-Net on the library's tcgen05
-    kernels, its per-jump phi error on held-out pairs against the persistence
-    forecast, and the controller (50 LB steps + one jump, plain-LB judge every
-    4th jump, phi tolerance 1e-2) timed against plain LB from the same state."""
+    from the LB itself (seeded emulsions, 2000 spin-up steps, snapshots 50
+    steps apart: the slow, late-time regime of a long run), a training run of
+    the BF16 U-Net on the library's tcgen05 kernels, its per-jump phi error on
+    held-out pairs against the persistence forecast, and the controller (50 LB
+    steps + one jump, plain-LB judge until a jump passes and then every 4th,
+    phi tolerance 1e-2) timed against plain LB from the same state."""
     import time
     import torch
     from paper_2405_14551_gb300 import surrogate as S
@@ -346,8 +347,8 @@ def surrogate_extra(L, stream, ntraj=8, iters=600, cycles=12):
     n = nx * ny * nz
     t0 = time.time()
     with torch.cuda.stream(stream):
-        trajs = S.generate_pairs(range(ntraj), shape=shape, spinup=200, snaps=6, stream=stream)
-        test = S.generate_pairs([1000], shape=shape, spinup=200, snaps=6, stream=stream)
+        trajs = S.generate_pairs(range(ntraj), shape=shape, spinup=spinup, snaps=8, stream=stream)
+        test = S.generate_pairs([1000], shape=shape, spinup=spinup, snaps=8, stream=stream)
         net = S.UNet(base=32, seed=0, stream=stream)
         t1 = time.time()
         S.train(net, trajs, shape, iters=iters, lr=1e-3, stream=stream, log_every=iters)
@@ -378,7 +379,7 @@ def surrogate_extra(L, stream, ntraj=8, iters=600, cycles=12):
         b = L.Sim(nx, ny, nz, walls=0b010, stream=stream, **p)
         for s_ in (a, b):
             s_.init_fields(phi)
-            s_.step(200)
+            s_.step(spinup)
         ctl = S.Controller(a, net, shape, stream=stream)
         # one untimed cycle allocates the monitor and judge lattices and
         # captures their graphs; then the plain run restarts from the same state
@@ -406,8 +407,8 @@ def surrogate_extra(L, stream, ntraj=8, iters=600, cycles=12):
         a.close()
         b.close()
     torch.cuda.empty_cache()
-    return {"workload": "dense_emulsion_128x128x256 surrogate, K = 50", "train_trajectories": ntraj,
-            "train_pairs": ntraj * 5, "train_iters": iters, "train_s": round(t_train, 1),
+    return {"workload": "dense_emulsion_128x128x256 surrogate, K = 50", "spinup_steps": spinup,
+            "train_trajectories": ntraj, "train_pairs": ntraj * 7, "train_iters": iters, "train_s": round(t_train, 1),
             "unet_forward_ms": round(fwd_ms, 2), "lb_50_steps_ms": round(t_lb / (cycles * 2) * 1e3, 2),
             "phi_err_per_jump": round(sum(err) / len(err), 4), "persistence_err": round(sum(pers) / len(pers), 4),
             "phi_tol": 1e-2, "controller_cycles": cycles, "accepted": acc, "rejected": rej, "judged": judged,

@@ -198,6 +198,17 @@ int lb_laplace_f64(lb_handle* h, double cut, double* dp);
  * 6-connected, periodic on open axes.  Synchronises the stream. */
 int lb_droplet_count(lb_handle* h, int32_t* count);
 
+/* Drift monitors of a phase field that is not (yet) the handle's state, for
+ * example a surrogate's candidate: phi is a device array of nx*ny*nz floats
+ * on the handle's grid (x fastest).  *count receives the number of
+ * 6-connected phi > 0 components among fluid nodes (periodic on open axes,
+ * as lb_droplet_count) and *volume the dispersed volume, the sum over fluid
+ * nodes of (1 + phi)/2 in FP64 (the same sum, in the same order, as
+ * lb_reduce_f64's out[5]).  Uses the handle's scratch, leaves its state
+ * untouched and synchronises its stream.  LB_ETIMEOUT if the union-find gave
+ * up.  These are the drift monitors of the surrogate controller. */
+int lb_phi_monitor(lb_handle* h, const float* phi, int32_t* count, double* volume);
+
 /* Synchronise the stream and read the device status word: LB_OK or
  * LB_EUNSTABLE once any step met a non-finite or non-positive density. */
 int lb_check(lb_handle* h);

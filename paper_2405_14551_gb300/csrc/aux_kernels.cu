@@ -158,6 +158,23 @@ cudaError_t launch_reduce(int storage, const Geo& g, const void* fields, double*
   return cudaGetLastError();
 }
 
+// dispersed volume sum over fluid nodes of (1 + phi)/2 of a phase-field array,
+// in the partition and order of k_reduce_partial (same value as its v[5])
+__global__ void __launch_bounds__(RED_THREADS) k_phi_volume_partial(Geo g, const float* __restrict__ phi,
+                                                                    double* partials) {
+  __shared__ double s[1][RED_THREADS];
+  const long long chunk = (g.N + gridDim.x - 1) / gridDim.x;
+  const long long beg = (long long)blockIdx.x * chunk;
+  const long long end = beg + chunk < g.N ? beg + chunk : g.N;
+  double v[1] = {0};
+  for (long long i = beg + threadIdx.x; i < end; i += RED_THREADS) {
+    if (node_solid(g, i)) continue;
+    v[0] += 0.5 * (1.0 + (double)phi[i]);
+  }
+  block_tree<1>(s, v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s[0][0];
+}
+
 template <typename R>
 __global__ void __launch_bounds__(RED_THREADS) k_laplace_partial(Geo g, const R* __restrict__ fl, double cut,
                                                                  double* partials) {
@@ -281,6 +298,17 @@ cudaError_t launch_cc(int storage, const Geo& g, const void* fields, int* labels
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(count, 0, sizeof(int), st)) != cudaSuccess) return e;
   k_cc_count<<<blocks, 256, 0, st>>>(g, labels, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi_monitor(const Geo& g, const float* phi, int* labels, int* count, double* partials,
+                               double* volume, unsigned* status, cudaStream_t st) {
+  cudaError_t e = launch_cc(0, g, phi, labels, count, status, st);  // phi is the first (only) field
+  if (e != cudaSuccess) return e;
+  const int nb = reduce_blocks(g.N);
+  k_phi_volume_partial<<<nb, RED_THREADS, 0, st>>>(g, phi, partials);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_reduce_final<1><<<1, RED_THREADS, 0, st>>>(nb, partials, volume);
   return cudaGetLastError();
 }
 

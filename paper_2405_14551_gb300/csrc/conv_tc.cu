@@ -527,11 +527,14 @@ static size_t conv_wgrad_smem(int Cout) {
 // Shared memory of the tiled forward kernel: two input blocks, the weight
 // ring, barriers and the tensor-memory slot, raised where needed so that the
 // CTAs sharing an SM never ask for more than its 512 tensor-memory columns.
-static size_t conv_tiled_smem(int tz, int Cin, int Cout, int KC) {
+constexpr size_t CONV_TILED_SMEM_MAX = 225 * 1024;
+static size_t conv_tiled_smem_need(int tz, int Cin, int Cout, int KC) {
   const size_t halo = (size_t)10 * 18 * (tz + 2) * KC * 2;
   const size_t nhalo = Cin > KC ? 2 : 1;
-  const size_t need = nhalo * halo + (size_t)TCONV_NS * Cout * KC * 2 + 8 * (TCONV_NS + 2) + 16;
-  return conv_smem(need, Cout * tz);
+  return nhalo * halo + (size_t)TCONV_NS * Cout * KC * 2 + 8 * (TCONV_NS + 2) + 16;
+}
+static size_t conv_tiled_smem(int tz, int Cin, int Cout, int KC) {
+  return conv_smem(conv_tiled_smem_need(tz, Cin, Cout, KC), Cout * tz);
 }
 
 static int pick_kc(int Cin) {
@@ -563,10 +566,29 @@ int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, con
   ConvGeo g{nx, ny, nz, nb, (int)(periodic & 1u), (int)((periodic >> 1) & 1u), (int)((periodic >> 2) & 1u)};
   cudaStream_t st = (cudaStream_t)stream;
   if (taps == 27 && nx % 8 == 0 && ny % 16 == 0) {
-    // spatially tiled kernel: TZ planes per CTA with TZ x Cout accumulator columns <= 512
-    const int KCt = cin % 32 == 0 ? 32 : 16;
-    int tz = 4;
-    while (tz > 1 && (tz * cout > 512 || nz % tz)) tz >>= 1;
+    // spatially tiled kernel: TZ planes per CTA with TZ x Cout accumulator
+    // columns <= 512 and KC input channels per chunk; every (chunk, tap) step
+    // has a fixed cost, so take the fitting pair with the most work per step
+    // (largest KC x TZ, then the larger TZ)
+    int KCt = 0, tz = 0;
+    {
+      const int cands[7] = {128, 96, 64, 48, 32, 16, 0};
+      int best = 0;
+      for (int k = 0; cands[k]; ++k) {
+        const int kc = cands[k];
+        if (kc > cin || cin % kc) continue;
+        for (int t = 4; t >= 1; t >>= 1) {
+          if (t * cout > 512 || nz % t) continue;
+          if (conv_tiled_smem_need(t, cin, cout, kc) > CONV_TILED_SMEM_MAX) continue;
+          if (kc * t > best) {
+            best = kc * t;
+            KCt = kc;
+            tz = t;
+          }
+        }
+      }
+    }
+    if (!KCt) return report_error(LB_EINVAL, "conv fwd: no tiled configuration fits shared memory");
     const size_t smem = conv_tiled_smem(tz, cin, cout, KCt);
     cudaError_t e = cudaSuccess;
     auto launch = [&](auto kern) {

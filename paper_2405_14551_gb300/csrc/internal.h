@@ -112,6 +112,9 @@ cudaError_t launch_laplace(int storage, const Geo& g, const void* fields, double
                            double* out4, cudaStream_t st);
 cudaError_t launch_cc(int storage, const Geo& g, const void* fields, int* labels, int* count, unsigned* status,
                       cudaStream_t st);
+// droplet count and dispersed volume of a float phase-field array [N]
+cudaError_t launch_phi_monitor(const Geo& g, const float* phi, int* labels, int* count, double* partials,
+                               double* volume, unsigned* status, cudaStream_t st);
 
 // --- runtime.cu --------------------------------------------------------------
 // record code + message as the calling thread's last error; returns code

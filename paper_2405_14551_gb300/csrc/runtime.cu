@@ -672,6 +672,26 @@ int lb_droplet_count(lb_handle* h, int32_t* count) {
   return LB_OK;
 }
 
+int lb_phi_monitor(lb_handle* h, const float* phi, int32_t* count, double* volume) {
+  if (!h || !phi || !count || !volume) return set_err(LB_EINVAL, "null argument");
+  if (!h->labels && !(h->labels = (int*)dev_alloc(h, (size_t)h->g.N * sizeof(int))))
+    return set_err(LB_ENOMEM, "label buffer allocation failed");
+  double* vol_dev = h->red + (size_t)reduce_blocks(h->g.N) * 8;  // past the partials
+  LB_CUDA(launch_phi_monitor(h->g, phi, h->labels, h->count, h->red, vol_dev, h->status, h->stream));
+  g_launches += 5;
+  int c = 0;
+  unsigned st = 0;
+  double v = 0.0;
+  LB_CUDA(cudaMemcpyAsync(&c, h->count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(cudaMemcpyAsync(&v, vol_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(cudaStreamSynchronize(h->stream));
+  if (st & 2u) return set_err(LB_ETIMEOUT, "union-find gave up after its iteration limit");
+  *count = c;
+  *volume = v;
+  return LB_OK;
+}
+
 int lb_check(lb_handle* h) {
   if (!h) return set_err(LB_EINVAL, "null handle");
   unsigned st = 0;

@@ -314,6 +314,104 @@ __global__ void __launch_bounds__(256) k_phi(View<ST> S, Geo g, typename Store<S
     phi_node<ST, IDX32>(S, g, idx, phi);
 }
 
+// Reduced storage: the same pass over CTA tiles.  Every node combines the
+// colour scalars (s, v) of its 27 source nodes; the tile's scalars plus a
+// one-node halo are staged in shared memory once, so those reads leave the
+// L1/L2 path.  Same arithmetic in the same order as phi_node.
+template <int ST, bool WALLFREE, bool IDX32>
+__device__ __forceinline__ void pull_reduced_tile(const View<ST>& S, const Geo& g, const Nbr& n, int self,
+                                                  const float4* svt, int cl, int SX, int SXY,
+                                                  typename Store<ST>::R& rA, typename Store<ST>::R& rB) {
+  using R = typename Store<ST>::R;
+  using I = typename std::conditional<IDX32, unsigned, size_t>::type;
+  const I N = (I)g.N;
+  int rb[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rb[b][c] = g.nx * (n.ys[b] + g.ny * n.zs[c]);
+  rA = R(0);
+  rB = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int a = 1 - cx(i), b = 1 - cy(i), c = 1 - cz(i);
+    int src = n.xs[a] + rb[b][c];
+    int sl = cl - cx(i) - SX * cy(i) - SXY * cz(i);
+    I dir = (I)i;
+    bool bb = false;
+    if constexpr (!WALLFREE) {
+      bb = n.sx[a] | n.sy[b] | n.sz[c];
+      src = bb ? self : src;
+      sl = bb ? cl : sl;
+      dir = bb ? (I)opp(i) : dir;
+    }
+    const R fs = decode<ST>(S.f[dir * N + (I)src], i);
+    const float4 sv = svt[sl];
+    const R s = sv.x;
+    R cv = R(0);
+    if (cx(i)) cv += R(cx(i)) * R(sv.y);
+    if (cy(i)) cv += R(cy(i)) * R(sv.z);
+    if (cz(i)) cv += R(cz(i)) * R(sv.w);
+    R seg = wgt<R>(i) * inv_norm<R>(i) * cv;
+    if constexpr (!WALLFREE) seg = bb ? -seg : seg;
+    const R va = s * fs + seg;
+    rA += va;
+    rB += (fs - va);
+  }
+}
+
+template <int ST, int TX, int TY, int TZ, bool IDX32>
+__global__ void __launch_bounds__(TX* TY) k_phi_tiled(View<ST> S, Geo g, typename Store<ST>::R* __restrict__ phi) {
+  using R = typename Store<ST>::R;
+  extern __shared__ __align__(16) float4 svt[];
+  constexpr int SX = TX + 2, SY = TY + 2, SZ = TZ + 2, SXY = SX * SY;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  // stage (s, v) of the tile + halo: periodic axes wrap; beyond a wall the
+  // entry is never read (a solid source is replaced by the node itself)
+  for (int row = threadIdx.y; row < SY * SZ; row += TY) {
+    const int ly = row % SY, lz = row / SY;
+    int gy = y0 - 1 + ly, gz = z0 - 1 + lz;
+    bool out = false;
+    if ((unsigned)gy >= (unsigned)g.ny) {
+      if (g.wy) out = true;
+      else gy = ((gy % g.ny) + g.ny) % g.ny;
+    }
+    if ((unsigned)gz >= (unsigned)g.nz) {
+      if (g.wz) out = true;
+      else gz = ((gz % g.nz) + g.nz) % g.nz;
+    }
+    for (int lx = threadIdx.x; lx < SX; lx += TX) {
+      int gx = x0 - 1 + lx;
+      bool o = out;
+      if ((unsigned)gx >= (unsigned)g.nx) {
+        if (g.wx) o = true;
+        else gx = ((gx % g.nx) + g.nx) % g.nx;
+      }
+      svt[row * SX + lx] = o ? make_float4(0.f, 0.f, 0.f, 0.f)
+                             : S.sv[(size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * gz)];
+    }
+  }
+  __syncthreads();
+  for (int lz = 0; lz < TZ; ++lz) {
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
+    if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
+    const int self = x + g.nx * (y + g.ny * z);
+    if (is_solid(g, x, y, z)) {
+      phi[self] = R(0);
+      continue;
+    }
+    Nbr n;
+    make_nbr(g, x, y, z, n);
+    const int cl = (lz + 1) * SXY + (threadIdx.y + 1) * SX + (threadIdx.x + 1);
+    R rA, rB;
+    if (near_wall(g, x, y, z))
+      pull_reduced_tile<ST, false, IDX32>(S, g, n, self, svt, cl, SX, SXY, rA, rB);
+    else
+      pull_reduced_tile<ST, true, IDX32>(S, g, n, self, svt, cl, SX, SXY, rA, rB);
+    phi[self] = (rA - rB) / (rA + rB);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // passes 2 and 3: near-contact scan and fused step
 // ---------------------------------------------------------------------------

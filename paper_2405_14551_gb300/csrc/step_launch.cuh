@@ -29,6 +29,16 @@ inline int resident_ctas(K kern, int threads, size_t smem) {
 template <int ST>
 cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st) {
   using R = typename Store<ST>::R;
+  if constexpr (!Store<ST>::TWOSET) {  // reduced storage: tiles with staged colour scalars
+    constexpr int TX = 32, TY = 8, TZ = 4;
+    const bool idx32r = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
+    const size_t smem = sizeof(float4) * (TX + 2) * (TY + 2) * (TZ + 2);
+    const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
+    auto kern = idx32r ? k_phi_tiled<ST, TX, TY, TZ, true> : k_phi_tiled<ST, TX, TY, TZ, false>;
+    trace_kernel("k_phi_tiled", kern, grid, dim3(TX, TY), smem);
+    kern<<<grid, dim3(TX, TY), smem, st>>>(view<ST>(in), g, reinterpret_cast<R*>(phi));
+    return cudaGetLastError();
+  }
   static const int occ32 = resident_ctas(k_phi<ST, true>, 256, 0);
   static const int occ64 = resident_ctas(k_phi<ST, false>, 256, 0);
   const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);

@@ -71,6 +71,8 @@ _SIGS = {
     "lb_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lb_set_nc_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lb_copy_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lb_phi_monitor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_double)]),
     "lb_get_nc_tile": (ctypes.c_int, [ctypes.c_void_p]),
     "lb_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "lb_get_tile": (ctypes.c_int, [ctypes.c_void_p]),
@@ -251,6 +253,15 @@ def lb_step_timed(h, nsteps: int):
     ms = np.zeros(3)
     _check(load_library().lb_step_timed(h, int(nsteps), ms.ctypes.data), "lb_step_timed")
     return float(ms[0]), float(ms[1]), float(ms[2])
+
+
+def lb_phi_monitor(h, phi):
+    """(droplet count, dispersed volume) of a device float32 phase field of the
+    handle's grid."""
+    c, v = ctypes.c_int32(), ctypes.c_double()
+    _check(load_library().lb_phi_monitor(h, ctypes.c_void_p(phi.data_ptr()), ctypes.byref(c), ctypes.byref(v)),
+           "lb_phi_monitor")
+    return int(c.value), float(v.value)
 
 
 def lb_copy_state(dst, src):

@@ -349,7 +349,8 @@ def train(net, trajs, shape, iters=300, lr=1e-3, seed=0, stream=None, wch=(4.0, 
 class Controller:
     """Alternate K plain LB steps with one surrogate jump of K steps.
 
-    Every candidate is checked on a monitor lattice: the droplet count must
+    Every candidate is checked by the drift monitors (lb_phi_monitor on the
+    candidate phase field): the droplet count must
     not change, the dispersed volume sum((1+phi)/2) must stay within vol_tol
     (relative), and phi is clamped to [-1, 1].  Jumps are also judged by the
     plain LB: the same K steps run from the exact pre-jump state on a shadow
@@ -371,7 +372,6 @@ class Controller:
         nx, ny, nz = shape
         N = nx * ny * nz
         p = workload_params()
-        self.monitor = L.Sim(nx, ny, nz, walls=0b010, stream=self.stream, storage="reduced_f16", **p)
         self.shadow = L.Sim(nx, ny, nz, walls=0b010, stream=self.stream, storage=sim.storage, **p)
         self.x = torch.empty((N, CIN), dtype=torch.bfloat16, device=net.dev)
         self.out = torch.empty((5, N), dtype=torch.float32, device=net.dev)
@@ -400,14 +400,11 @@ class Controller:
             L.lb_copy_state(self.shadow.h, self.sim.h)
             self.shadow.step(self.K)
         f0 = self.sim.fields_device(FIELD_MASK).reshape(5, -1)
-        count0 = self.sim.droplet_count()
-        vol0 = float(self.sim.reduce()[5])
+        count0, vol0 = L.lb_phi_monitor(self.sim.h, f0[0])
         pack_input(f0, self.x, self.stream)
         y = self.net.forward(self.x, (nx, ny, nz, 1))
         unpack_output(f0, y, self.out, self.stream)
-        self.monitor.init_fields(self.out[0], self.out[1], self.out[2:5], regularised=False)
-        count1 = self.monitor.droplet_count()
-        vol1 = float(self.monitor.reduce()[5])
+        count1, vol1 = L.lb_phi_monitor(self.sim.h, self.out[0])
         ok = count1 == count0 and abs(vol1 - vol0) <= self.vol_tol * max(vol0, 1.0)
         info = {"count0": count0, "count1": count1, "vol_rel": (vol1 - vol0) / max(vol0, 1.0), "judged": judge}
         if judge:
@@ -451,5 +448,4 @@ class Controller:
         return infos
 
     def close(self):
-        self.monitor.close()
         self.shadow.close()

@@ -221,6 +221,24 @@ def test_checkpoint_resume_bitwise(tmp_path):
             np.testing.assert_array_equal(fa[k], fb[k])
 
 
+def test_phi_monitor_matches_count_and_reduction():
+    """lb_phi_monitor on the handle's own phase field gives the droplet count
+    of lb_droplet_count and, bitwise, the dispersed volume of lb_reduce_f64;
+    on a modified field it sees the change."""
+    import paper_2405_14551_gb300.lbcg as L
+    wl = _channel()
+    s = make_gpu(wl)
+    s.step(7)
+    phi = s.fields_device(1).reshape(-1).contiguous()
+    count, vol = L.lb_phi_monitor(s.h, phi)
+    assert count == s.droplet_count() >= 1
+    assert vol == s.reduce()[5]
+    phi2 = phi.clone()
+    phi2[:] = -1.0
+    c2, v2 = L.lb_phi_monitor(s.h, phi2)
+    assert c2 == 0 and v2 == 0.0
+
+
 def test_copy_state_bitwise():
     """lb_copy_state: a copy taken after 23 steps (odd parity on the source,
     even on the target) and one taken before any step continue bitwise like

@@ -58,7 +58,8 @@ def test_conv_forward(dims, cin, cout, taps, per, relu):
 @pytest.mark.parametrize("dims,cin,cout,per,relu,ldy", [
     ((8, 16, 4, 1), 16, 32, 7, 0, 0), ((16, 16, 4, 2), 32, 64, 5, 1, 0), ((8, 32, 2, 1), 96, 32, 2, 0, 0),
     ((8, 16, 3, 1), 64, 128, 0, 1, 0), ((8, 16, 4, 1), 384, 128, 5, 1, 0), ((16, 16, 4, 1), 128, 256, 7, 0, 0),
-    ((8, 16, 8, 1), 32, 16, 7, 1, 0), ((8, 16, 4, 1), 32, 32, 5, 0, 64)])
+    ((8, 16, 8, 1), 32, 16, 7, 1, 0), ((8, 16, 4, 1), 32, 32, 5, 0, 64), ((8, 16, 2, 1), 128, 64, 7, 1, 0),
+    ((16, 16, 2, 1), 192, 64, 5, 0, 0)])
 def test_conv_forward_tiled(dims, cin, cout, per, relu, ldy):
     """Grids with nx % 8 == 0 and ny % 16 == 0 take the spatially tiled kernel
     (input block staged once per channel chunk, TZ planes per CTA); the same

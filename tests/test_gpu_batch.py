@@ -22,7 +22,8 @@ def small_sweep(seed=11, n=6):
         walls = 0b010 if r == 2 else 0
         if walls:
             cen[:, 1] = np.clip(cen[:, 1], 6, L - 7)
-        p = dict(W.BASE, A_a=A, A_b=A, A_h=Ah, tau_a=0.8 + 0.1 * r, tau_b=1.0)
+        # odd runs use the regularised collision
+        p = dict(W.BASE, A_a=A, A_b=A, A_h=Ah, tau_a=0.8 + 0.1 * r, tau_b=1.0, collision=r % 2)
         runs.append(W.Workload(f"run{r}", (L, L + (r % 2), L - 1), walls, p, 100, centres=cen, radii=rad))
     return runs
 

@@ -401,7 +401,7 @@ def surrogate_extra(L, stream, ntraj=16, iters=2000, cycles=20, spinup=2000):
         fa, fb = a.fields_device(1).reshape(-1), b.fields_device(1).reshape(-1)
         final_err = float((fa - fb).abs().mean())
         counts = (a.droplet_count(), b.droplet_count())
-        judged = [(c, round(e, 4)) for c, e, _ in ctl.judged]
+        judged = [(c, round(e, 4)) for c, e in ctl.judged]
         acc, rej = ctl.accepted, ctl.rejected
         ctl.close()
         a.close()

@@ -209,6 +209,37 @@ int lb_droplet_count(lb_handle* h, int32_t* count);
  * up.  These are the drift monitors of the surrogate controller. */
 int lb_phi_monitor(lb_handle* h, const float* phi, int32_t* count, double* volume);
 
+/* Learned surrogate (an extension of the method: a network that
+ * advances (phi, rho, u) by K steps, with the plain LB as fallback and judge;
+ * populations rebuilt by the regularised reconstruction of Sec. IV.C).
+ *
+ * lb_surrogate_load: read a U-Net weight file written by
+ * paper_2405_14551_gb300.surrogate.UNet.save (4 levels, base 8..64 channels,
+ * 16 input and head channels, FP32 weights stored as BF16 on the device) and
+ * allocate its weights and activation buffers for the handle's grid through
+ * the handle's allocator (released by lb_destroy).  Every extent must be a
+ * multiple of 8.  LB_EIO for a missing or mismatched file, LB_ESTATE if a
+ * network is already loaded, LB_EINVAL for unsuitable extents.
+ *
+ * lb_surrogate_predict: the candidate state K steps ahead, [5][N] float
+ * (phi, rho, ux, uy, uz) into out (a device pointer, or NULL to keep it only
+ * inside the handle); the handle's state is not changed.  Synchronises the
+ * stream; LB_ETIMEOUT if a tensor-core kernel gave up a bounded wait.
+ *
+ * lb_surrogate_cycle: one jump of K steps on h.  The candidate is checked by
+ * the drift monitors (droplet count unchanged, dispersed volume within
+ * vol_tol relative, as lb_phi_monitor); with judge != NULL (a handle of the
+ * same grid and storage) the plain LB also advances the exact same state by
+ * K steps on judge and *phi_err receives mean |phi_candidate - phi_LB| over
+ * all nodes, which must not exceed phi_tol (else *phi_err = -1).  Accepted
+ * (*accepted = 1): h is re-initialised from the candidate by regularised
+ * reconstruction (step counter reset).  Rejected: h takes the judge's state,
+ * or steps K plain LB steps without a judge. */
+int lb_surrogate_load(lb_handle* h, const char* path);
+int lb_surrogate_predict(lb_handle* h, float* out);
+int lb_surrogate_cycle(lb_handle* h, lb_handle* judge, int32_t K, double vol_tol, double phi_tol, int32_t* accepted,
+                       double* phi_err);
+
 /* Synchronise the stream and read the device status word: LB_OK or
  * LB_EUNSTABLE once any step met a non-finite or non-positive density. */
 int lb_check(lb_handle* h);

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbcg.so")
 SOURCES = ["step_twoset_f32.cu", "step_reduced_f32.cu", "step_reduced_f16.cu", "step_twoset_f64.cu",
            "step_kernels.cu", "aux_kernels.cu", "runtime.cu", "noalloc.cu",
-           "conv_tc.cu", "nn_kernels.cu"]
+           "conv_tc.cu", "nn_kernels.cu", "surrogate_rt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

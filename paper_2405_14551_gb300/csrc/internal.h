@@ -116,9 +116,21 @@ cudaError_t launch_cc(int storage, const Geo& g, const void* fields, int* labels
 cudaError_t launch_phi_monitor(const Geo& g, const float* phi, int* labels, int* count, double* partials,
                                double* volume, unsigned* status, cudaStream_t st);
 
+// --- surrogate_rt.cu ---------------------------------------------------------
+struct SurrogateState;
+void destroy_surrogate(SurrogateState* s);
+
 // --- runtime.cu --------------------------------------------------------------
 // record code + message as the calling thread's last error; returns code
 int report_error(int code, const std::string& msg);
+}  // namespace lbcg
+struct lb_handle;
+namespace lbcg {
+// handle internals for the surrogate runtime
+cudaStream_t handle_stream(lb_handle* h);
+void handle_dims(const lb_handle* h, int* nx, int* ny, int* nz, uint32_t* walls);
+void* handle_alloc(lb_handle* h, size_t bytes);  // owned (freed) by the handle
+SurrogateState*& handle_surrogate(lb_handle* h);
 // add n to the library's kernel launch counter
 void count_launches(int n);
 

@@ -101,7 +101,25 @@ struct lb_handle {
   int nc_tile = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   uint64_t graph_launches = 0;  // kernel launches in one replay
+  lbcg::SurrogateState* surrogate = nullptr;  // its device buffers are owned like the rest
 };
+
+namespace {
+void* dev_alloc(lb_handle* h, size_t bytes);
+}
+
+namespace lbcg {
+cudaStream_t handle_stream(lb_handle* h) { return h->stream; }
+void handle_dims(const lb_handle* h, int* nx, int* ny, int* nz, uint32_t* walls) {
+  *nx = h->grid.nx;
+  *ny = h->grid.ny;
+  *nz = h->grid.nz;
+  *walls = h->grid.walls;
+}
+void* handle_alloc(lb_handle* h, size_t bytes) { return dev_alloc(h, bytes); }
+SurrogateState*& handle_surrogate(lb_handle* h) { return h->surrogate; }
+}  // namespace lbcg
+
 
 namespace {
 
@@ -375,6 +393,7 @@ int lb_destroy(lb_handle* h) {
   if (!h) return LB_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
+  if (h->surrogate) destroy_surrogate(h->surrogate);
   while (!h->owned.empty()) dev_free(h, h->owned.back().first);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;

@@ -71,6 +71,11 @@ _SIGS = {
     "lb_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lb_set_nc_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lb_copy_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lb_surrogate_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "lb_surrogate_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lb_surrogate_cycle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_double)]),
     "lb_phi_monitor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_double)]),
     "lb_get_nc_tile": (ctypes.c_int, [ctypes.c_void_p]),
@@ -262,6 +267,23 @@ def lb_phi_monitor(h, phi):
     _check(load_library().lb_phi_monitor(h, ctypes.c_void_p(phi.data_ptr()), ctypes.byref(c), ctypes.byref(v)),
            "lb_phi_monitor")
     return int(c.value), float(v.value)
+
+
+def lb_surrogate_load(h, path: str):
+    _check(load_library().lb_surrogate_load(h, str(path).encode()), "lb_surrogate_load")
+
+
+def lb_surrogate_predict(h, out=None):
+    _check(load_library().lb_surrogate_predict(h, ctypes.c_void_p(out.data_ptr()) if out is not None else None),
+           "lb_surrogate_predict")
+
+
+def lb_surrogate_cycle(h, judge, K: int, vol_tol: float, phi_tol: float):
+    """(accepted, judged phi error or -1)."""
+    a, e = ctypes.c_int32(), ctypes.c_double()
+    _check(load_library().lb_surrogate_cycle(h, judge, int(K), float(vol_tol), float(phi_tol), ctypes.byref(a),
+                                             ctypes.byref(e)), "lb_surrogate_cycle")
+    return bool(a.value), float(e.value)
 
 
 def lb_copy_state(dst, src):

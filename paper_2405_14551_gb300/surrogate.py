@@ -103,6 +103,21 @@ class UNet:
             self.b32[k].copy_(self.torch.as_tensor(np.asarray(b), dtype=self.torch.float32))
             self.wbf[k].copy_(self.w32[k].to(self.torch.bfloat16))
 
+    def save(self, path):
+        """Write the network in the weight-file format lb_surrogate_load reads:
+        magic, version, base, input and head channels, scales, periodic axes,
+        then (ci, co, taps, relu, FP32 weights [co][taps][ci], FP32 bias) per
+        convolution in forward order."""
+        import struct
+        base = self.layers[0][2]
+        with open(path, "wb") as fh:
+            fh.write(struct.pack("<Ii3iffIi", 0x4E4E424C, 1, base, CIN, COUT, S_RHO, S_U, self.periodic,
+                                 len(self.layers)))
+            for name, ci, co, taps, relu in self.layers:
+                fh.write(struct.pack("<4i", ci, co, taps, relu))
+                fh.write(self.w32[name].detach().float().cpu().numpy().astype("<f4").tobytes())
+                fh.write(self.b32[name].detach().float().cpu().numpy().astype("<f4").tobytes())
+
     # ---------------------------------------------------------------- forward
     def _conv(self, name, x, level, shape, out_bf=None, out_f32=None):
         _, ci, co, taps, relu = self.spec[name]
@@ -349,37 +364,39 @@ def train(net, trajs, shape, iters=300, lr=1e-3, seed=0, stream=None, wch=(4.0, 
 class Controller:
     """Alternate K plain LB steps with one surrogate jump of K steps.
 
-    Every candidate is checked by the drift monitors (lb_phi_monitor on the
-    candidate phase field): the droplet count must
-    not change, the dispersed volume sum((1+phi)/2) must stay within vol_tol
-    (relative), and phi is clamped to [-1, 1].  Jumps are also judged by the
-    plain LB: the same K steps run from the exact pre-jump state on a shadow
-    lattice (lb_copy_state), and the surrogate's mean |phi_sur - phi_LB|
-    must not exceed phi_tol.  Every jump is judged until one passes; after
-    that every judge_every-th jump is.  A rejected candidate is replaced by
-    the LB result (the judge's lattice when it ran, else K plain steps); a
-    failed judgement withdraws the trust and suspends the surrogate for
-    backoff cycles.  An accepted jump re-initialises the lattice by
-    regularised reconstruction."""
+    The jump itself is lb_surrogate_cycle (native): candidate from the network
+    loaded on the handle, drift monitors (droplet count unchanged, dispersed
+    volume within vol_tol), optional judgement by the plain LB on a shadow
+    handle from the exact same state (mean |phi_sur - phi_LB| <= phi_tol),
+    acceptance by regularised reconstruction or the LB result.  This class
+    holds the policy: every jump is judged until one passes, then every
+    judge_every-th; a failed judgement withdraws the trust and suspends the
+    surrogate for backoff cycles (2K plain steps per cycle)."""
 
     def __init__(self, sim, net, shape, K=50, vol_tol=0.02, phi_tol=1e-2, judge_every=4, backoff=8,
                  stream=None):
+        import os
+        import tempfile
         import torch
         self.torch = torch
         self.sim, self.net, self.K = sim, net, K
         self.shape = shape
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         nx, ny, nz = shape
-        N = nx * ny * nz
         p = workload_params()
         self.shadow = L.Sim(nx, ny, nz, walls=0b010, stream=self.stream, storage=sim.storage, **p)
-        self.x = torch.empty((N, CIN), dtype=torch.bfloat16, device=net.dev)
-        self.out = torch.empty((5, N), dtype=torch.float32, device=net.dev)
+        fd, path = tempfile.mkstemp(suffix=".lbnn")
+        os.close(fd)
+        try:
+            net.save(path)
+            L.lb_surrogate_load(sim.h, path)
+        finally:
+            os.remove(path)
         self.vol_tol, self.phi_tol = vol_tol, phi_tol
         self.judge_every, self.backoff = judge_every, backoff
         self.accepted = 0
         self.rejected = 0
-        self.judged = []       # (cycle, mean |phi_sur - phi_LB|, max)
+        self.judged = []       # (cycle, mean |phi_sur - phi_LB|)
         self.suspended = 0
         self.cycle = 0
         self.jumps = 0
@@ -387,46 +404,21 @@ class Controller:
 
     def jump(self):
         """One surrogate jump (or its LB replacement); returns (accepted, info)."""
-        # every tensor operation on the library's stream: its allocations and
-        # arithmetic are then ordered with the kernels that fill and read them
-        with self.torch.cuda.stream(self.stream):
-            return self._jump()
-
-    def _jump(self):
-        nx, ny, nz = self.shape
         judge = (not self.trusted) or self.jumps % self.judge_every == 0
         self.jumps += 1
+        ok, err = L.lb_surrogate_cycle(self.sim.h, self.shadow.h if judge else None, self.K, self.vol_tol,
+                                       self.phi_tol)
+        info = {"judged": judge, "phi_err": err}
         if judge:
-            L.lb_copy_state(self.shadow.h, self.sim.h)
-            self.shadow.step(self.K)
-        f0 = self.sim.fields_device(FIELD_MASK).reshape(5, -1)
-        count0, vol0 = L.lb_phi_monitor(self.sim.h, f0[0])
-        pack_input(f0, self.x, self.stream)
-        y = self.net.forward(self.x, (nx, ny, nz, 1))
-        unpack_output(f0, y, self.out, self.stream)
-        count1, vol1 = L.lb_phi_monitor(self.sim.h, self.out[0])
-        ok = count1 == count0 and abs(vol1 - vol0) <= self.vol_tol * max(vol0, 1.0)
-        info = {"count0": count0, "count1": count1, "vol_rel": (vol1 - vol0) / max(vol0, 1.0), "judged": judge}
-        if judge:
-            phi_lb = self.shadow.fields_device(1).reshape(-1)
-            d = (self.out[0] - phi_lb).abs()
-            err, emax = float(d.mean()), float(d.max())
-            self.judged.append((self.cycle, err, emax))
-            info["phi_err"], info["phi_err_max"] = err, emax
-            if err > self.phi_tol:
-                ok = False
+            self.judged.append((self.cycle, err))
+            if ok:
+                self.trusted = True
+            else:
                 self.trusted = False
                 self.suspended = self.backoff
-            else:
-                self.trusted = True
         if ok:
-            self.sim.init_fields(self.out[0], self.out[1], self.out[2:5], regularised=True)
             self.accepted += 1
         else:
-            if judge:
-                L.lb_copy_state(self.sim.h, self.shadow.h)  # the judge's exact LB result
-            else:
-                self.sim.step(self.K)  # fallback: the plain method
             self.rejected += 1
         return ok, info
 
@@ -435,11 +427,9 @@ class Controller:
         surrogate is suspended)."""
         infos = []
         for _ in range(cycles):
-            with self.torch.cuda.stream(self.stream):
-                self.sim.step(self.K)
+            self.sim.step(self.K)
             if self.suspended > 0:
-                with self.torch.cuda.stream(self.stream):
-                    self.sim.step(self.K)
+                self.sim.step(self.K)
                 self.suspended -= 1
                 infos.append((None, {"suspended": True}))
             else:

@@ -179,3 +179,71 @@ def test_training_lowers_the_loss():
     hist = S.train(net, [[f0, f1]], shape, iters=40, lr=2e-3, log_every=39)
     assert hist[-1][1] < 0.75 * hist[0][1], hist
 
+
+
+def test_native_surrogate_matches_python_driver():
+    """The native runtime (lb_surrogate_load / _predict / _cycle) runs the same
+    kernels in the same order as the Python driver: bitwise equal candidate,
+    accepted jumps rebuild the candidate by regularised reconstruction, a
+    rejected judged jump leaves the plain-LB result, and the judged error is
+    the mean |phi_candidate - phi_LB|."""
+    import os
+    import tempfile
+    import torch
+    import paper_2405_14551_gb300.lbcg as L
+    from paper_2405_14551_gb300 import surrogate as S
+    from paper_2405_14551_gb300 import workloads as W
+    n, K = 32, 5
+    p = dict(W.BASE, A_h=0.1, g=(0.0, 0.0, 1e-5), g_mode=1)
+    stream = torch.cuda.current_stream()
+
+    def make():
+        s = L.Sim(n, n, n, walls=0b010, **p)
+        s.init_droplets([[15.3, 14.2, 10.1], [16.2, 17.1, 23.4]], [6.0, 5.5])
+        return s
+
+    sim = make()
+    sim.step(20)
+    net = S.UNet(base=16, seed=4)  # untrained: small increments, the droplet count is kept
+    f0 = sim.fields_device(S.FIELD_MASK).reshape(5, -1)
+    x = torch.empty((n ** 3, S.CIN), dtype=torch.bfloat16, device="cuda")
+    out_py = torch.empty((5, n ** 3), dtype=torch.float32, device="cuda")
+    S.pack_input(f0, x, stream)
+    y = net.forward(x, (n, n, n, 1))
+    S.unpack_output(f0, y, out_py, stream)
+    fd, path = tempfile.mkstemp(suffix=".lbnn")
+    os.close(fd)
+    try:
+        net.save(path)
+        L.lb_surrogate_load(sim.h, path)
+        with pytest.raises(L.LBError):
+            L.lb_surrogate_load(sim.h, path)  # one network per handle
+    finally:
+        os.remove(path)
+    out_c = torch.empty((5, n ** 3), dtype=torch.float32, device="cuda")
+    L.lb_surrogate_predict(sim.h, out_c)
+    torch.cuda.synchronize()
+    assert torch.equal(out_c, out_py)
+    # rejected judged jump: the handle holds the plain-LB state K steps on
+    judge = make()
+    twin = make()
+    L.lb_copy_state(twin.h, sim.h)
+    twin.step(K)
+    ok, err = L.lb_surrogate_cycle(sim.h, judge.h, K, 0.02, 0.0)
+    assert not ok and err > 0
+    phi_lb = twin.fields_device(1).reshape(-1)
+    assert abs(err - float((out_py[0] - phi_lb).double().abs().mean())) < 1e-9
+    ft, fs = twin.fields(), sim.fields()
+    for k in ft:
+        np.testing.assert_array_equal(fs[k], ft[k])
+    # accepted jump (tolerances wide open): regularised reconstruction of the candidate
+    L.lb_surrogate_predict(sim.h, out_c)
+    torch.cuda.synchronize()
+    ok, err = L.lb_surrogate_cycle(sim.h, judge.h, K, 1e9, 1e9)
+    assert ok and err >= 0
+    rec = make()
+    rec.init_fields(out_c[0], out_c[1], out_c[2:5], regularised=True)
+    fr, fs = rec.fields(), sim.fields()
+    for k in fr:
+        np.testing.assert_array_equal(fs[k], fr[k])
+    assert sim.t == 0

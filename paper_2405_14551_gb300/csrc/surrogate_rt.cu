@@ -260,6 +260,7 @@ int lb_surrogate_cycle(lb_handle* h, lb_handle* judge, int32_t K, double vol_tol
                        int32_t* accepted, double* phi_err) {
   if (!h || !accepted || !phi_err) return fail(LB_EINVAL, "null argument");
   if (K < 1) return fail(LB_EINVAL, "K must be >= 1");
+  if (judge == h) return fail(LB_EINVAL, "the judge must be a second handle");
   SurrogateState* S = handle_surrogate(h);
   if (!S) return fail(LB_ESTATE, "no surrogate loaded on this handle");
   int nx, ny, nz;

@@ -87,4 +87,6 @@ def test_null_handle_rejected(lib):
     assert lib.lb_set_nc_tile(None, 0) == L.LB_EINVAL
     assert lib.lb_phi_monitor(None, None, None, None) == L.LB_EINVAL
     assert lib.lb_copy_state(None, None) == L.LB_EINVAL
+    assert lib.lb_surrogate_load(None, b"x") == L.LB_EINVAL
+    assert lib.lb_surrogate_predict(None, None) == L.LB_EINVAL
     assert lib.lb_get_nc_tile(None) == -1

@@ -185,24 +185,45 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ---------------------------------------------------------------------------
-// forward / input gradient, spatially tiled (3x3x3 taps)
+// forward / input gradient, spatially tiled and pipelined (3x3x3 taps)
 // ---------------------------------------------------------------------------
-// A CTA owns an output block of 8 (x) x 16 (y) x TZ (z) voxels and all Cout
-// channels: TZ accumulators of 128 rows x Cout columns in tensor memory.  Per
-// channel chunk of KC channels it stages the input block with a one-voxel halo
-// (10 x 18 x (TZ + 2) voxels) once, in the layout
+// Work item: an output block of 8 (x) x 16 (y) x TZ (z) voxels and CT output
+// channels (CT = Cout, or a slice of it when Cout is large and the grid
+// small).  Persistent CTAs walk the work items; warps have fixed roles:
+//   warps 0-3  epilogue: tensor memory -> bias, ReLU -> BF16 / FP32 stores
+//   warps 4-7  copies (cp.async, zero fill for padded voxels)
+//   warp 8     tensor-memory allocation; lane 0 issues the UMMAs
+// and hand buffers over through mbarriers only.
+//
+// Per chunk of KC input channels the input block with a one-voxel halo
+// (10 x 18 x (TZ + 2) voxels) is staged once, in the layout
 //   piece (cg, zz, yy, xx) of 8 channels at ((cg * SZH + zz) * 18 + yy) * 10 + xx,
-// so that for every tap the 128 output rows of one z plane read 16 core
-// matrices of 8 consecutive x voxels (128 contiguous bytes) 160 bytes apart:
-// the A operand of a tap is the same staged block at a shifted start address,
-// and the input is read once per chunk instead of once per tap.  Weights of
-// one (chunk, tap) step (Cout x KC) stream through a ring of NS buffers.  All
-// 128 threads copy with cp.async (zero fill for padded voxels); one thread
-// issues the UMMAs of a step (TZ planes x KC/16) and commits them to the
-// step's ring barrier, and after the last tap of a chunk to the halo buffer's
-// barrier, before a buffer is refilled.  Every wait is bounded.
-constexpr int TCONV_NS = 5;  // weight ring depth
-constexpr int TCONV_D = 3;   // steps loaded ahead; the slot refilled was read two steps before
+// so that the 128 output rows of a z plane (8 x voxels = one core matrix,
+// 16 y rows 160 bytes apart) read a tap's input as the same staged block at
+// a shifted start address.
+//
+// MERGE (3 CT <= 256): the three z taps of one (dx, dy) share the A operand.
+// The weights of (dx, dy) are staged as one B operand of 3 CT rows, block s
+// holding the tap dz = s - 1, and the accumulator of output plane q sits at
+// column (TZ - 1 - q) CT.  One UMMA with input plane zz and blocks
+// [s_lo, s_hi] then adds W(dz = s - 1) X(zz) to plane q = zz - s for every
+// block at once: 9 steps of TZ + 2 UMMAs of up to 3 CT columns per chunk
+// instead of 27 steps of TZ UMMAs of CT columns.  The first k-step of a work
+// item is issued block by block (block 1 first, without accumulation) so
+// that every plane is initialised before it is accumulated.
+//
+// Without MERGE a step is one tap: TZ UMMAs of CT columns.
+// Accumulators are double buffered (2 TZ CT <= 512 columns), so the epilogue
+// of one work item overlaps the UMMAs of the next.  Every wait is bounded; a
+// wait that gives up sets bit 4 of the status word and the CTA winds down.
+constexpr int PCONV_THREADS = 288;
+constexpr int PCONV_PROD0 = 128;  // first copy thread
+constexpr int PCONV_NPROD = 128;  // copy threads
+constexpr int PCONV_MMA_WARP = 8;
+constexpr int PCONV_MAXWP = 8;    // weight pieces per copy thread and step (3 CT or CT rows x KC / 8 <= 1024)
+constexpr int PCONV_LAG = 5;      // steps a copy thread keeps in flight before it signals them
+constexpr int PCONV_NSW_MAX = 8;  // weight ring slots (at most)
+constexpr uint32_t PCONV_SPIN = 1u << 22;
 
 __device__ __forceinline__ int wrap_or_pad(int c, int n, int periodic) {
   if (c >= 0 && c < n) return c;
@@ -210,34 +231,72 @@ __device__ __forceinline__ int wrap_or_pad(int c, int n, int periodic) {
   return c < 0 ? c + n : c - n;
 }
 
-template <int TZ>
-__global__ void __launch_bounds__(128, 1)
-    k_conv_fwd_tiled(const __nv_bfloat16* __restrict__ X, int Cin, const __nv_bfloat16* __restrict__ W,
-                     const float* __restrict__ bias, __nv_bfloat16* __restrict__ Y, float* __restrict__ Yf, int Cout,
-                     int ldy, int KC, ConvGeo g, int relu, unsigned* __restrict__ status) {
+// Bounded wait that also gives up once another role has given up.
+__device__ __forceinline__ bool pconv_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < PCONV_SPIN; ++it) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
+  }
+  return false;
+}
+
+struct PConvArgs {
+  const __nv_bfloat16* X;
+  const __nv_bfloat16* W;  // [Cout][27][Cin]
+  const float* bias;
+  __nv_bfloat16* Y;
+  float* Yf;
+  int Cin, Cout, ldy, KC, CT, nsw;
+  ConvGeo g;
+  int relu;
+  unsigned* status;
+};
+
+template <int TZ, bool MERGE>
+__global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P) {
   constexpr int SZH = TZ + 2;
   constexpr int HV = 10 * 18 * SZH;  // staged voxels
+  constexpr int NBLK = MERGE ? 3 : 1;
+  constexpr int SPC = MERGE ? 9 : 27;  // steps per chunk
   extern __shared__ __align__(1024) unsigned char smem[];
   const int t = threadIdx.x;
   const int warp = t >> 5;
-  const size_t halo_bytes = (size_t)HV * KC * 2, w_bytes = (size_t)Cout * KC * 2;
-  const int nhalo = Cin > KC ? 2 : 1;  // one chunk needs one input buffer
-  unsigned char* sH[2] = {smem, smem + (nhalo - 1) * halo_bytes};
-  unsigned char* sW = smem + nhalo * halo_bytes;
-  uint64_t* bar_w = reinterpret_cast<uint64_t*>(sW + TCONV_NS * w_bytes);
-  uint64_t* bar_h = bar_w + TCONV_NS;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_h + 2);
+  const int KC = P.KC, CT = P.CT, Cin = P.Cin, nsw = P.nsw;
+  const int NB = NBLK * CT;  // rows of a staged B operand
+  const int cgs = KC / 8;
+  const size_t halo_bytes = (size_t)HV * KC * 2, w_bytes = (size_t)NB * KC * 2;
+  unsigned char* sH = smem;                    // 2 input blocks
+  unsigned char* sW = smem + 2 * halo_bytes;   // nsw weight slots
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sW + (size_t)nsw * w_bytes);
+  uint64_t* w_full = bar;
+  uint64_t* w_empty = bar + PCONV_NSW_MAX;
+  uint64_t* h_full = bar + 2 * PCONV_NSW_MAX;
+  uint64_t* h_empty = h_full + 2;
+  uint64_t* a_full = h_full + 4;
+  uint64_t* a_empty = h_full + 6;
+  uint64_t* fin = h_full + 8;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint32_t ncols = 32;
-  while ((int)ncols < TZ * Cout) ncols <<= 1;
+  while ((int)ncols < 2 * TZ * CT) ncols <<= 1;
 
-  if (warp == 0) {
+  if (warp == PCONV_MMA_WARP) {
     tc::tmem_alloc(tmem_slot, ncols);
     tc::tmem_relinquish();
   }
   if (t == 0) {
-    for (int k = 0; k < TCONV_NS; ++k) tc::mbar_init(&bar_w[k], 1);
-    tc::mbar_init(&bar_h[0], 1);
-    tc::mbar_init(&bar_h[1], 1);
+    for (int k = 0; k < PCONV_NSW_MAX; ++k) {
+      tc::mbar_init(&w_full[k], PCONV_NPROD);
+      tc::mbar_init(&w_empty[k], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      tc::mbar_init(&h_full[k], PCONV_NPROD);
+      tc::mbar_init(&h_empty[k], 1);
+      tc::mbar_init(&a_full[k], 1);
+      tc::mbar_init(&a_empty[k], 128);
+    }
+    tc::mbar_init(fin, 1);
+    *abort_flag = 0;
     tc::fence_mbar_init();
   }
   tc::fence_before_sync();
@@ -245,126 +304,238 @@ __global__ void __launch_bounds__(128, 1)
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
+  const ConvGeo& g = P.g;
   const int bxs = g.nx / 8, bys = g.ny / 16, bzs = g.nz / TZ;
-  int blk = blockIdx.x;
-  const int x0 = (blk % bxs) * 8;
-  blk /= bxs;
-  const int y0 = (blk % bys) * 16;
-  blk /= bys;
-  const int z0 = (blk % bzs) * TZ;
-  const int b = blk / bzs;
-
+  const int nsplit = P.Cout / CT;
+  const int nitems = bxs * bys * bzs * g.nb * nsplit;
   const int nchunks = Cin / KC;
-  const int nks = nchunks * 27;  // (chunk, tap) steps
-  const int cgs = KC / 8;
-  const uint32_t a_lbo = (uint32_t)HV * 16, a_sbo = 160;
-  const uint32_t b_lbo = (uint32_t)Cout * 16, b_sbo = 128;
-  const uint32_t idesc = tc::idesc_bf16(CONV_M, Cout, false, false);
-
-  // issue the copies of step s (weights; the input block too at a chunk's first tap)
-  auto load_step = [&](int s) {
-    const int c = s / 27, tap = s % 27, c0 = c * KC;
-    unsigned char* wdst = sW + (size_t)(s % TCONV_NS) * w_bytes;
-    for (int p = t; p < Cout * cgs; p += 128) {
-      const int co = p % Cout, kg = p / Cout;
-      tc::cp_async16(wdst + ((size_t)kg * Cout + co) * 16, W + ((size_t)co * 27 + tap) * Cin + c0 + kg * 8, true);
-    }
-    if (tap == 0) {
-      unsigned char* hdst = sH[c & 1];
-      for (int p = t; p < HV * cgs; p += 128) {
-        const int xx = p % 10, r = p / 10;
-        const int yy = r % 18, r2 = r / 18;
-        const int zz = r2 % SZH, cg = r2 / SZH;
-        const int gx = wrap_or_pad(x0 - 1 + xx, g.nx, g.px);
-        const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
-        const int gz = wrap_or_pad(z0 - 1 + zz, g.nz, g.pz);
-        const bool ok = gx >= 0 && gy >= 0 && gz >= 0;
-        const long long v = ok ? (((long long)b * g.nz + gz) * g.ny + gy) * g.nx + gx : 0;
-        tc::cp_async16(hdst + (size_t)p * 16, X + v * Cin + c0 + cg * 8, ok);
-      }
-    }
+  const int my_items = blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  auto item_of = [&](int k, int& x0, int& y0, int& z0, int& b, int& n0) {
+    int it = blockIdx.x + k * gridDim.x;
+    n0 = (it % nsplit) * CT;
+    it /= nsplit;
+    x0 = (it % bxs) * 8;
+    it /= bxs;
+    y0 = (it % bys) * 16;
+    it /= bys;
+    z0 = (it % bzs) * TZ;
+    b = it / bzs;
   };
 
-  bool ok = true;
-  for (int s = 0; s < TCONV_D && s < nks; ++s) {
-    load_step(s);
-    tc::cp_async_commit();
-  }
-  for (int s = 0; s < nks; ++s) {
-    // refill: step s + D goes into the ring slot of step s + D - NS = s - 2 (and,
-    // at a chunk's first tap, into the input buffer of chunk c - 2), so the
-    // UMMAs that read it were issued two iterations ago
-    const int pf = s + TCONV_D;
-    bool wok = true;
-    if (pf < nks) {
-      if (pf >= TCONV_NS) wok = tc::mbar_wait(&bar_w[pf % TCONV_NS], (uint32_t)(((pf / TCONV_NS) - 1) & 1), 1u << 22);
-      const int pc = pf / 27;
-      if (wok && pf % 27 == 0 && pc >= 2) wok = tc::mbar_wait(&bar_h[pc & 1], (uint32_t)(((pc / 2) - 1) & 1), 1u << 22);
+  if (t >= PCONV_PROD0 && t < PCONV_PROD0 + PCONV_NPROD) {
+    // ------------------------------------------------------------ copies
+    const int pt = t - PCONV_PROD0;
+    const int nsteps = my_items * nchunks * SPC;
+    // Weight pieces: a copy thread stages the same (k group, row) positions
+    // of every step, so their offsets are set up once; a step only adds its
+    // tap and channel chunk.
+    int woff[PCONV_MAXWP];
+    uint32_t wdo[PCONV_MAXWP];
+#pragma unroll
+    for (int i = 0; i < PCONV_MAXWP; ++i) {
+      const int p = pt + i * PCONV_NPROD;
+      const int kg = p % cgs, n = p / cgs;
+      woff[i] = p < NB * cgs ? ((n % CT) * 27 + 9 * (n / CT)) * Cin + kg * 8 : -1;
+      wdo[i] = (uint32_t)(kg * NB + n) * 16;
     }
-    ok = __syncthreads_and(ok && wok);
-    if (!ok) break;
-    if (pf < nks) load_step(pf);
-    tc::cp_async_commit();
-    tc::cp_async_wait<TCONV_D>();  // step s has landed (this thread's copies)
+    // Input pieces: one staged row (zz, yy) holds 10 x voxels x cgs groups;
+    // a thread keeps its (xx, group) place in the row and walks the rows.
+    const int hl = 10 * cgs, hr = PCONV_NPROD / hl;
+    const bool hact = pt < hr * hl;
+    const int hq = (pt % hl) % cgs, hxx = (pt % hl) / cgs, hr0 = pt / hl;
+    bool ok = true;
+    int gs = 0;
+    for (int k = 0; k < my_items && ok; ++k) {
+      int x0, y0, z0, b, n0;
+      item_of(k, x0, y0, z0, b, n0);
+      const int gx = wrap_or_pad(x0 - 1 + hxx, g.nx, g.px);
+      const __nv_bfloat16* wbase = P.W + (size_t)n0 * 27 * Cin;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int c0 = c * KC;
+        for (int st = 0; st < SPC; ++st, ++gs) {
+          const int slot = gs % nsw;
+          if (gs >= nsw && !pconv_wait(&w_empty[slot], (uint32_t)(((gs / nsw) - 1) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          unsigned char* wdst = sW + (size_t)slot * w_bytes;
+          const __nv_bfloat16* wsrc = wbase + st * Cin + c0;
+#pragma unroll
+          for (int i = 0; i < PCONV_MAXWP; ++i)
+            if (woff[i] >= 0) tc::cp_async16(wdst + wdo[i], wsrc + woff[i], true);
+          if (st == 0) {
+            const int cg = gs / SPC;
+            if (cg >= 2 && !pconv_wait(&h_empty[cg & 1], (uint32_t)(((cg >> 1) - 1) & 1), abort_flag)) {
+              ok = false;
+              break;
+            }
+            if (hact) {
+              unsigned char* hdst = sH + (size_t)(cg & 1) * halo_bytes + ((size_t)hq * SZH * 180 + hxx) * 16;
+              const __nv_bfloat16* hsrc = P.X + c0 + hq * 8;
+              for (int row = hr0; row < SZH * 18; row += hr) {
+                const int zz = row / 18, yy = row - 18 * zz;
+                const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
+                const int gz = wrap_or_pad(z0 - 1 + zz, g.nz, g.pz);
+                const bool in = gx >= 0 && gy >= 0 && gz >= 0;
+                const long long v = in ? (((long long)b * g.nz + gz) * g.ny + gy) * g.nx + gx : 0;
+                tc::cp_async16(hdst + (size_t)row * 160, hsrc + v * Cin, in);
+              }
+            }
+          }
+          tc::cp_async_commit();
+          if (gs >= PCONV_LAG) {  // step gs - LAG has landed: hand it over
+            tc::cp_async_wait<PCONV_LAG>();
+            tc::fence_proxy_async_smem();
+            const int r = gs - PCONV_LAG;
+            tc::mbar_arrive(&w_full[r % nsw]);
+            if (r % SPC == 0) tc::mbar_arrive(&h_full[(r / SPC) & 1]);
+          }
+        }
+      }
+    }
+    tc::cp_async_wait<0>();
     tc::fence_proxy_async_smem();
-    __syncthreads();
-    if (t == 0) {
-      tc::fence_after_sync();
-      const int c = s / 27, tap = s % 27;
-      const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;  // offsets + 1
-      const uint32_t h0 = tc::smem_u32(sH[c & 1]) + (uint32_t)((dz * 18 + dy) * 10 + dx) * 16;
-      const uint32_t w0 = tc::smem_u32(sW + (size_t)(s % TCONV_NS) * w_bytes);
-      for (int z = 0; z < TZ; ++z) {
-        for (int j = 0; j < KC / 16; ++j) {
-          const uint64_t ad = tc::smem_desc(h0 + (uint32_t)z * 180 * 16 + (uint32_t)j * 2 * a_lbo, a_lbo, a_sbo);
-          const uint64_t bd = tc::smem_desc(w0 + (uint32_t)j * 2 * b_lbo, b_lbo, b_sbo);
-          tc::mma_bf16(tmem + (uint32_t)(z * Cout), ad, bd, idesc, (s > 0 || j > 0) ? 1u : 0u);
-        }
+    if (ok) {
+      for (int r = nsteps > PCONV_LAG ? nsteps - PCONV_LAG : 0; r < nsteps; ++r) {
+        tc::mbar_arrive(&w_full[r % nsw]);
+        if (r % SPC == 0) tc::mbar_arrive(&h_full[(r / SPC) & 1]);
       }
-      tc::mma_commit(&bar_w[s % TCONV_NS]);
-      if (tap == 26) tc::mma_commit(&bar_h[c & 1]);
+    } else {
+      *abort_flag = 1;
+      atomicOr(P.status, CONV_TIMEOUT);
     }
-  }
-  tc::cp_async_wait<0>();
-  // the last commit covers every UMMA issued before it
-  const int last = nks - 1;
-  bool done = tc::mbar_wait(&bar_w[last % TCONV_NS], (uint32_t)((last / TCONV_NS) & 1), 1u << 22);
-  if (!done) done = tc::mbar_wait(&bar_w[last % TCONV_NS], (uint32_t)((last / TCONV_NS) & 1), 1u << 22);
-  ok = __syncthreads_and(ok && done);
-  tc::fence_after_sync();
-  if (ok) {
+  } else if (warp == PCONV_MMA_WARP) {
+    // ------------------------------------------------------------ UMMA issue
+    if ((t & 31) == 0) {
+      const uint32_t a_lbo = (uint32_t)HV * 16, a_sbo = 160;
+      const uint32_t b_lbo = (uint32_t)NB * 16, b_sbo = 128;
+      uint32_t idesc[3];
+      for (int k = 0; k < 3; ++k) idesc[k] = tc::idesc_bf16(CONV_M, (k + 1) * CT > 256 ? CT : (k + 1) * CT, false, false);
+      bool ok = true;
+      int gs = 0;
+      for (int k = 0; k < my_items && ok; ++k) {
+        const int ab = k & 1;
+        if (k >= 2 && !pconv_wait(&a_empty[ab], (uint32_t)(((k >> 1) - 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t acc = tmem + (uint32_t)(ab * TZ * CT);
+        for (int c = 0; c < nchunks && ok; ++c) {
+          const int cg = gs / SPC;
+          if (!pconv_wait(&h_full[cg & 1], (uint32_t)((cg >> 1) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t hb = tc::smem_u32(sH + (size_t)(cg & 1) * halo_bytes);
+          for (int st = 0; st < SPC; ++st, ++gs) {
+            const int slot = gs % nsw;
+            if (!pconv_wait(&w_full[slot], (uint32_t)((gs / nsw) & 1), abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t wb = tc::smem_u32(sW + (size_t)slot * w_bytes);
+            if (MERGE) {
+              const int dxp = st % 3, dyp = st / 3;
+              const uint32_t h0 = hb + (uint32_t)(dyp * 10 + dxp) * 16;
+              for (int j = 0; j < KC / 16; ++j) {
+                const uint32_t aj = h0 + (uint32_t)j * 2 * a_lbo, bj = wb + (uint32_t)j * 2 * b_lbo;
+                if (c == 0 && st == 0 && j == 0) {
+                  // block 1 (dz = 0) initialises every plane, then blocks 0 and 2 accumulate
+                  for (int sb = 0; sb < 3; ++sb) {
+                    const int s = sb == 0 ? 1 : (sb == 1 ? 0 : 2);
+                    for (int q = 0; q < TZ; ++q) {
+                      const int zz = q + s;
+                      const uint64_t ad = tc::smem_desc(aj + (uint32_t)zz * 180 * 16, a_lbo, a_sbo);
+                      const uint64_t bd = tc::smem_desc(bj + (uint32_t)(s * CT) * 16, b_lbo, b_sbo);
+                      tc::mma_bf16(acc + (uint32_t)((TZ - 1 - q) * CT), ad, bd, idesc[0], s == 1 ? 0u : 1u);
+                    }
+                  }
+                } else {
+                  for (int zz = 0; zz < SZH; ++zz) {
+                    const int s_lo = zz - (TZ - 1) > 0 ? zz - (TZ - 1) : 0;
+                    const int s_hi = zz < 2 ? zz : 2;
+                    const uint64_t ad = tc::smem_desc(aj + (uint32_t)zz * 180 * 16, a_lbo, a_sbo);
+                    const uint64_t bd = tc::smem_desc(bj + (uint32_t)(s_lo * CT) * 16, b_lbo, b_sbo);
+                    tc::mma_bf16(acc + (uint32_t)((TZ - 1 - zz + s_lo) * CT), ad, bd, idesc[s_hi - s_lo], 1u);
+                  }
+                }
+              }
+            } else {
+              const int dxp = st % 3, dyp = (st / 3) % 3, dzp = st / 9;
+              const uint32_t h0 = hb + (uint32_t)((dzp * 18 + dyp) * 10 + dxp) * 16;
+              for (int j = 0; j < KC / 16; ++j) {
+                const uint64_t bd = tc::smem_desc(wb + (uint32_t)j * 2 * b_lbo, b_lbo, b_sbo);
+                for (int q = 0; q < TZ; ++q) {
+                  const uint64_t ad = tc::smem_desc(h0 + (uint32_t)q * 180 * 16 + (uint32_t)j * 2 * a_lbo, a_lbo, a_sbo);
+                  tc::mma_bf16(acc + (uint32_t)(q * CT), ad, bd, idesc[0], (c > 0 || st > 0 || j > 0) ? 1u : 0u);
+                }
+              }
+            }
+            tc::mma_commit(&w_empty[slot]);
+          }
+          if (ok) tc::mma_commit(&h_empty[cg & 1]);
+        }
+        if (ok) tc::mma_commit(&a_full[ab]);
+      }
+      // every UMMA issued so far has completed before the CTA winds down
+      tc::mma_commit(fin);
+      if (!tc::mbar_wait(fin, 0u, PCONV_SPIN)) ok = false;
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(P.status, CONV_TIMEOUT);
+      }
+    }
+    __syncwarp();
+  } else if (warp < 4) {
+    // ------------------------------------------------------------ epilogue
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    const int x = x0 + (t & 7), y = y0 + (t >> 3);
-    for (int z = 0; z < TZ; ++z) {
-      const long long v = (((long long)b * g.nz + z0 + z) * g.ny + y) * g.nx + x;
-      for (int col = 0; col < Cout; col += 16) {
-        float acc[16];
-        tc::tmem_ld16(lane_base + (uint32_t)(z * Cout + col), acc);
+    const int r = t;  // accumulator row = output voxel (x0 + r % 8, y0 + r / 8)
+    for (int k = 0; k < my_items; ++k) {
+      const int ab = k & 1;
+      // warp-uniform, so that the warp's tensor-memory loads stay converged
+      if (!__all_sync(0xffffffffu, pconv_wait(&a_full[ab], (uint32_t)((k >> 1) & 1), abort_flag))) {
+        *abort_flag = 1;
+        atomicOr(P.status, CONV_TIMEOUT);
+        break;
+      }
+      tc::fence_after_sync();
+      int x0, y0, z0, b, n0;
+      item_of(k, x0, y0, z0, b, n0);
+      const int x = x0 + (r & 7), y = y0 + (r >> 3);
+      for (int q = 0; q < TZ; ++q) {
+        const long long v = (((long long)b * g.nz + z0 + q) * g.ny + y) * g.nx + x;
+        const uint32_t colq = (uint32_t)(ab * TZ * CT + (MERGE ? TZ - 1 - q : q) * CT);
+        for (int col = 0; col < CT; col += 16) {
+          float a[16];
+          tc::tmem_ld16(lane_base + colq + (uint32_t)col, a);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          float vv = acc[k] + (bias ? bias[col + k] : 0.0f);
-          acc[k] = relu ? fmaxf(vv, 0.0f) : vv;
-        }
-        if (Y) {
-          uint4* yp = reinterpret_cast<uint4*>(Y + v * ldy + col);
-          yp[0] = make_uint4(pack_bf16(acc[0], acc[1]), pack_bf16(acc[2], acc[3]), pack_bf16(acc[4], acc[5]),
-                             pack_bf16(acc[6], acc[7]));
-          yp[1] = make_uint4(pack_bf16(acc[8], acc[9]), pack_bf16(acc[10], acc[11]), pack_bf16(acc[12], acc[13]),
-                             pack_bf16(acc[14], acc[15]));
-        }
-        if (Yf) {
-          float4* fp = reinterpret_cast<float4*>(Yf + v * ldy + col);
+          for (int e = 0; e < 16; ++e) {
+            const float vv = a[e] + (P.bias ? __ldg(P.bias + n0 + col + e) : 0.0f);
+            a[e] = P.relu ? fmaxf(vv, 0.0f) : vv;
+          }
+          if (P.Y) {
+            uint4* yp = reinterpret_cast<uint4*>(P.Y + v * P.ldy + n0 + col);
+            yp[0] = make_uint4(pack_bf16(a[0], a[1]), pack_bf16(a[2], a[3]), pack_bf16(a[4], a[5]),
+                               pack_bf16(a[6], a[7]));
+            yp[1] = make_uint4(pack_bf16(a[8], a[9]), pack_bf16(a[10], a[11]), pack_bf16(a[12], a[13]),
+                               pack_bf16(a[14], a[15]));
+          }
+          if (P.Yf) {
+            float4* fp = reinterpret_cast<float4*>(P.Yf + v * P.ldy + n0 + col);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) fp[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+            for (int e = 0; e < 4; ++e) fp[e] = make_float4(a[4 * e], a[4 * e + 1], a[4 * e + 2], a[4 * e + 3]);
+          }
         }
       }
+      tc::fence_before_sync();
+      tc::mbar_arrive(&a_empty[ab]);
     }
-  } else if (t == 0) {
-    atomicOr(status, CONV_TIMEOUT);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+  if (warp == PCONV_MMA_WARP) tc::tmem_dealloc(tmem, ncols);
 }
 
 // ---------------------------------------------------------------------------
@@ -524,17 +695,64 @@ static size_t conv_wgrad_smem(int Cout) {
   return conv_smem(2 * (size_t)CONV_M * 64 * 2 + 2 * (size_t)Cout * 64 * 2 + 64, Cout);
 }
 
-// Shared memory of the tiled forward kernel: two input blocks, the weight
-// ring, barriers and the tensor-memory slot, raised where needed so that the
-// CTAs sharing an SM never ask for more than its 512 tensor-memory columns.
+// Shared memory of the pipelined forward kernel: two input blocks, the
+// weight ring, barriers, the tensor-memory slot and the abort flag.
 constexpr size_t CONV_TILED_SMEM_MAX = 225 * 1024;
-static size_t conv_tiled_smem_need(int tz, int Cin, int Cout, int KC) {
+static size_t pconv_smem_need(int tz, int KC, int CT, bool merge, int nsw) {
   const size_t halo = (size_t)10 * 18 * (tz + 2) * KC * 2;
-  const size_t nhalo = Cin > KC ? 2 : 1;
-  return nhalo * halo + (size_t)TCONV_NS * Cout * KC * 2 + 8 * (TCONV_NS + 2) + 16;
+  return 2 * halo + (size_t)nsw * (merge ? 3 : 1) * CT * KC * 2 + 256;
 }
-static size_t conv_tiled_smem(int tz, int Cin, int Cout, int KC) {
-  return conv_smem(conv_tiled_smem_need(tz, Cin, Cout, KC), Cout * tz);
+
+struct PConvCfg {
+  int tz = 0, kc = 0, ct = 0, nsw = 0;
+  bool merge = false;
+  long long items = 0;
+};
+
+// Choose the work item and staging of the pipelined forward kernel: enough
+// work items for every SM if the grid allows (else the most), then the widest
+// channel slice, the deepest z block (fewer halo voxels per output), the
+// largest channel chunk and the deepest weight ring that fit shared memory.
+static PConvCfg pconv_choose(int cin, int cout, int nx, int ny, int nz, int nb, int nsm) {
+  PConvCfg best;
+  auto better = [&](const PConvCfg& a, const PConvCfg& b) {  // a better than b
+    if (!b.tz) return true;
+    const bool fa = a.items >= nsm, fb = b.items >= nsm;
+    if (fa != fb) return fa;
+    if (!fa && a.items != b.items) return a.items > b.items;
+    if (a.ct != b.ct) return a.ct > b.ct;
+    if (a.tz != b.tz) return a.tz > b.tz;
+    if (a.kc != b.kc) return a.kc > b.kc;
+    return a.nsw > b.nsw;
+  };
+  const int cts[2] = {cout, cout / 2};
+  for (int ci = 0; ci < 2; ++ci) {
+    const int ct = cts[ci];
+    if (ct < 16 || ct % 16 || cout % ct || (ci == 1 && cout < 128)) continue;
+    const bool merge = 3 * ct <= 256;
+    for (int tz = 8; tz >= 1; tz >>= 1) {
+      if (2 * tz * ct > 512 || nz % tz) continue;
+      const int kcs[4] = {64, 48, 32, 16};
+      for (int k = 0; k < 4; ++k) {
+        const int kc = kcs[k];
+        if (kc > cin || cin % kc) continue;
+        for (int nsw = PCONV_NSW_MAX; nsw >= PCONV_LAG + 2; --nsw) {
+          if (pconv_smem_need(tz, kc, ct, merge, nsw) > CONV_TILED_SMEM_MAX) continue;
+          if ((merge ? 3 : 1) * ct * (kc / 8) > PCONV_MAXWP * PCONV_NPROD || 10 * (kc / 8) > PCONV_NPROD) continue;
+          PConvCfg c;
+          c.tz = tz;
+          c.kc = kc;
+          c.ct = ct;
+          c.nsw = nsw;
+          c.merge = merge;
+          c.items = (long long)(nx / 8) * (ny / 16) * (nz / tz) * nb * (cout / ct);
+          if (better(c, best)) best = c;
+          break;
+        }
+      }
+    }
+  }
+  return best;
 }
 
 static int pick_kc(int Cin) {
@@ -566,42 +784,36 @@ int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, con
   ConvGeo g{nx, ny, nz, nb, (int)(periodic & 1u), (int)((periodic >> 1) & 1u), (int)((periodic >> 2) & 1u)};
   cudaStream_t st = (cudaStream_t)stream;
   if (taps == 27 && nx % 8 == 0 && ny % 16 == 0) {
-    // spatially tiled kernel: TZ planes per CTA with TZ x Cout accumulator
-    // columns <= 512 and KC input channels per chunk; every (chunk, tap) step
-    // has a fixed cost, so take the fitting pair with the most work per step
-    // (largest KC x TZ, then the larger TZ)
-    int KCt = 0, tz = 0;
-    {
-      const int cands[7] = {128, 96, 64, 48, 32, 16, 0};
-      int best = 0;
-      for (int k = 0; cands[k]; ++k) {
-        const int kc = cands[k];
-        if (kc > cin || cin % kc) continue;
-        for (int t = 4; t >= 1; t >>= 1) {
-          if (t * cout > 512 || nz % t) continue;
-          if (conv_tiled_smem_need(t, cin, cout, kc) > CONV_TILED_SMEM_MAX) continue;
-          if (kc * t > best) {
-            best = kc * t;
-            KCt = kc;
-            tz = t;
-          }
-        }
-      }
-    }
-    if (!KCt) return report_error(LB_EINVAL, "conv fwd: no tiled configuration fits shared memory");
-    const size_t smem = conv_tiled_smem(tz, cin, cout, KCt);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const PConvCfg c = pconv_choose(cin, cout, nx, ny, nz, nb, nsm);
+    if (!c.tz) return report_error(LB_EINVAL, "conv fwd: no tiled configuration fits shared memory");
+    const size_t smem = conv_smem(pconv_smem_need(c.tz, c.kc, c.ct, c.merge, c.nsw), 2 * c.tz * c.ct);
+    PConvArgs a{(const __nv_bfloat16*)x, (const __nv_bfloat16*)w, bias, (__nv_bfloat16*)y, yf, cin, cout, ldy,
+                c.kc, c.ct, c.nsw, g, relu, status};
     cudaError_t e = cudaSuccess;
     auto launch = [&](auto kern) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return;
-      const unsigned blocks = (unsigned)((nx / 8) * (ny / 16) * (nz / tz) * nb);
-      kern<<<blocks, CONV_M, smem, st>>>((const __nv_bfloat16*)x, cin, (const __nv_bfloat16*)w, bias,
-                                         (__nv_bfloat16*)y, yf, cout, ldy, KCt, g, relu, status);
+      int occ = 1;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PCONV_THREADS, smem);
+      if (e != cudaSuccess) return;
+      const long long cap = (long long)nsm * (occ > 0 ? occ : 1);
+      const unsigned blocks = (unsigned)(c.items < cap ? c.items : cap);
+      kern<<<blocks, PCONV_THREADS, smem, st>>>(a);
       e = cudaGetLastError();
     };
-    if (tz == 4) launch(k_conv_fwd_tiled<4>);
-    else if (tz == 2) launch(k_conv_fwd_tiled<2>);
-    else launch(k_conv_fwd_tiled<1>);
+    if (c.merge) {
+      if (c.tz == 8) launch(k_conv_fwd_pipe<8, true>);
+      else if (c.tz == 4) launch(k_conv_fwd_pipe<4, true>);
+      else if (c.tz == 2) launch(k_conv_fwd_pipe<2, true>);
+      else launch(k_conv_fwd_pipe<1, true>);
+    } else {
+      if (c.tz == 2) launch(k_conv_fwd_pipe<2, false>);
+      else if (c.tz == 1) launch(k_conv_fwd_pipe<1, false>);
+      else e = cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess) return report_error(LB_ECUDA, std::string("conv fwd (tiled): ") + cudaGetErrorString(e));
     count_launches(1);
     return LB_OK;

@@ -59,11 +59,17 @@ def test_conv_forward(dims, cin, cout, taps, per, relu):
     ((8, 16, 4, 1), 16, 32, 7, 0, 0), ((16, 16, 4, 2), 32, 64, 5, 1, 0), ((8, 32, 2, 1), 96, 32, 2, 0, 0),
     ((8, 16, 3, 1), 64, 128, 0, 1, 0), ((8, 16, 4, 1), 384, 128, 5, 1, 0), ((16, 16, 4, 1), 128, 256, 7, 0, 0),
     ((8, 16, 8, 1), 32, 16, 7, 1, 0), ((8, 16, 4, 1), 32, 32, 5, 0, 64), ((8, 16, 2, 1), 128, 64, 7, 1, 0),
-    ((16, 16, 2, 1), 192, 64, 5, 0, 0)])
+    ((16, 16, 2, 1), 192, 64, 5, 0, 0), ((32, 32, 320, 1), 16, 32, 5, 1, 0), ((32, 32, 320, 1), 48, 32, 2, 0, 0),
+    ((32, 32, 160, 1), 64, 64, 7, 1, 0), ((16, 32, 24, 1), 256, 128, 5, 1, 0),
+    ((32, 32, 48, 1), 64, 128, 7, 1, 0)])
 def test_conv_forward_tiled(dims, cin, cout, per, relu, ldy):
-    """Grids with nx % 8 == 0 and ny % 16 == 0 take the spatially tiled kernel
-    (input block staged once per channel chunk, TZ planes per CTA); the same
-    comparison as above, including a strided output (ldy > cout)."""
+    """Grids with nx % 8 == 0 and ny % 16 == 0 take the pipelined tiled kernel
+    (input block staged once per channel chunk, TZ planes per work item, z
+    taps merged into one UMMA when 3 Cout <= 256, Cout split in two slices
+    when the grid is small); the same comparison as above, including a
+    strided output (ldy > cout).  The 32 x 32 x 320 and 32 x 32 x 160 grids
+    have more than twice as many work items as the GPU has SMs, so the
+    persistent CTAs reuse both accumulator and both input buffers."""
     import torch
     import paper_2405_14551_gb300.lbcg as L
     lib = L.load_library()

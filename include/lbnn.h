@@ -32,6 +32,17 @@ int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, con
                     int32_t cout, int32_t ldy, int32_t nx, int32_t ny, int32_t nz, int32_t nb, uint32_t periodic,
                     int32_t relu, unsigned* status, void* stream);
 
+/* The 3x3x3 convolution above of the decoder input concat(skip, up2(low)):
+ * channels [0, cs) are skip[v][cs] at full resolution, channels [cs, cs + cl)
+ * are low[parent(v)][cl] of the half-resolution tensor (nearest x2
+ * upsampling, parent(v) = (x/2, y/2, z/2)), read in place without the
+ * concatenated copy; w is [cout][27][cs + cl].  Same outputs, ldy and
+ * status word as lbnn_conv3d_fwd.  Needs nx % 8 == 0, ny % 16 == 0 and an
+ * even nz (LB_EINVAL otherwise; concatenate with lbnn_up_concat then). */
+int lbnn_conv3d_fwd_upcat(const void* skip, int32_t cs, const void* low, int32_t cl, const void* w, const float* bias,
+                          void* y, float* yf, int32_t cout, int32_t ldy, int32_t nx, int32_t ny, int32_t nz, int32_t nb,
+                          uint32_t periodic, int32_t relu, unsigned* status, void* stream);
+
 /* dw[co][t][ci] += sum_v dy[v][co] x[v + off_t][ci] (FP32, accumulated with
  * atomics; clear dw first).  Voxels are split into slices of vox_per_cta
  * (multiple of 64) per CTA; cout a multiple of 16 up to 256. */

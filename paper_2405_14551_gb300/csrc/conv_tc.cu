@@ -241,7 +241,9 @@ __device__ __forceinline__ bool pconv_wait(uint64_t* bar, uint32_t parity, volat
 }
 
 struct PConvArgs {
-  const __nv_bfloat16* X;
+  const __nv_bfloat16* X;   // input channels [0, cs): X[v][cs]
+  const __nv_bfloat16* X2;  // input channels [cs, Cin), nearest x2 upsampled: X2[parent(v)][Cin - cs] (or null)
+  int cs;
   const __nv_bfloat16* W;  // [Cout][27][Cin]
   const float* bias;
   __nv_bfloat16* Y;
@@ -349,6 +351,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
       int x0, y0, z0, b, n0;
       item_of(k, x0, y0, z0, b, n0);
       const int gx = wrap_or_pad(x0 - 1 + hxx, g.nx, g.px);
+      const int cl = Cin - P.cs;
       const __nv_bfloat16* wbase = P.W + (size_t)n0 * 27 * Cin;
       for (int c = 0; c < nchunks && ok; ++c) {
         const int c0 = c * KC;
@@ -371,14 +374,27 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
             }
             if (hact) {
               unsigned char* hdst = sH + (size_t)(cg & 1) * halo_bytes + ((size_t)hq * SZH * 180 + hxx) * 16;
-              const __nv_bfloat16* hsrc = P.X + c0 + hq * 8;
-              for (int row = hr0; row < SZH * 18; row += hr) {
-                const int zz = row / 18, yy = row - 18 * zz;
-                const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
-                const int gz = wrap_or_pad(z0 - 1 + zz, g.nz, g.pz);
-                const bool in = gx >= 0 && gy >= 0 && gz >= 0;
-                const long long v = in ? (((long long)b * g.nz + gz) * g.ny + gy) * g.nx + gx : 0;
-                tc::cp_async16(hdst + (size_t)row * 160, hsrc + v * Cin, in);
+              if (c0 < P.cs) {  // a chunk lies wholly in one source (KC divides cs)
+                const __nv_bfloat16* hsrc = P.X + c0 + hq * 8;
+                for (int row = hr0; row < SZH * 18; row += hr) {
+                  const int zz = row / 18, yy = row - 18 * zz;
+                  const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
+                  const int gz = wrap_or_pad(z0 - 1 + zz, g.nz, g.pz);
+                  const bool in = gx >= 0 && gy >= 0 && gz >= 0;
+                  const long long v = in ? (((long long)b * g.nz + gz) * g.ny + gy) * g.nx + gx : 0;
+                  tc::cp_async16(hdst + (size_t)row * 160, hsrc + v * P.cs, in);
+                }
+              } else {
+                const __nv_bfloat16* hsrc = P.X2 + (c0 - P.cs) + hq * 8;
+                const int hx = g.nx / 2, hy = g.ny / 2, hz = g.nz / 2;
+                for (int row = hr0; row < SZH * 18; row += hr) {
+                  const int zz = row / 18, yy = row - 18 * zz;
+                  const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
+                  const int gz = wrap_or_pad(z0 - 1 + zz, g.nz, g.pz);
+                  const bool in = gx >= 0 && gy >= 0 && gz >= 0;
+                  const long long v = in ? (((long long)b * hz + (gz >> 1)) * hy + (gy >> 1)) * hx + (gx >> 1) : 0;
+                  tc::cp_async16(hdst + (size_t)row * 160, hsrc + v * cl, in);
+                }
               }
             }
           }
@@ -713,7 +729,7 @@ struct PConvCfg {
 // work items for every SM if the grid allows (else the most), then the widest
 // channel slice, the deepest z block (fewer halo voxels per output), the
 // largest channel chunk and the deepest weight ring that fit shared memory.
-static PConvCfg pconv_choose(int cin, int cout, int nx, int ny, int nz, int nb, int nsm) {
+static PConvCfg pconv_choose(int cin, int cs, int cout, int nx, int ny, int nz, int nb, int nsm) {
   PConvCfg best;
   auto better = [&](const PConvCfg& a, const PConvCfg& b) {  // a better than b
     if (!b.tz) return true;
@@ -735,7 +751,7 @@ static PConvCfg pconv_choose(int cin, int cout, int nx, int ny, int nz, int nb, 
       const int kcs[4] = {64, 48, 32, 16};
       for (int k = 0; k < 4; ++k) {
         const int kc = kcs[k];
-        if (kc > cin || cin % kc) continue;
+        if (kc > cin || cin % kc || cs % kc) continue;
         for (int nsw = PCONV_NSW_MAX; nsw >= PCONV_LAG + 2; --nsw) {
           if (pconv_smem_need(tz, kc, ct, merge, nsw) > CONV_TILED_SMEM_MAX) continue;
           if ((merge ? 3 : 1) * ct * (kc / 8) > PCONV_MAXWP * PCONV_NPROD || 10 * (kc / 8) > PCONV_NPROD) continue;
@@ -753,6 +769,45 @@ static PConvCfg pconv_choose(int cin, int cout, int nx, int ny, int nz, int nb, 
     }
   }
   return best;
+}
+
+// Launch of the pipelined forward kernel; channels [cs, cin) of the input
+// come from x2 upsampled (nearest x2) when x2 is not null.
+static int conv_fwd_pipe(const void* x, int cs, const void* x2, int cin, const void* w, const float* bias, void* y,
+                         float* yf, int cout, int ldy, const ConvGeo& g, int relu, unsigned* status, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const PConvCfg c = pconv_choose(cin, cs, cout, g.nx, g.ny, g.nz, g.nb, nsm);
+  if (!c.tz) return report_error(LB_EINVAL, "conv fwd: no tiled configuration fits shared memory");
+  const size_t smem = conv_smem(pconv_smem_need(c.tz, c.kc, c.ct, c.merge, c.nsw), 2 * c.tz * c.ct);
+  PConvArgs a{(const __nv_bfloat16*)x, (const __nv_bfloat16*)x2, cs, (const __nv_bfloat16*)w, bias,
+              (__nv_bfloat16*)y, yf, cin, cout, ldy, c.kc, c.ct, c.nsw, g, relu, status};
+  cudaError_t e = cudaSuccess;
+  auto launch = [&](auto kern) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return;
+    int occ = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PCONV_THREADS, smem);
+    if (e != cudaSuccess) return;
+    const long long cap = (long long)nsm * (occ > 0 ? occ : 1);
+    const unsigned blocks = (unsigned)(c.items < cap ? c.items : cap);
+    kern<<<blocks, PCONV_THREADS, smem, st>>>(a);
+    e = cudaGetLastError();
+  };
+  if (c.merge) {
+    if (c.tz == 8) launch(k_conv_fwd_pipe<8, true>);
+    else if (c.tz == 4) launch(k_conv_fwd_pipe<4, true>);
+    else if (c.tz == 2) launch(k_conv_fwd_pipe<2, true>);
+    else launch(k_conv_fwd_pipe<1, true>);
+  } else {
+    if (c.tz == 2) launch(k_conv_fwd_pipe<2, false>);
+    else if (c.tz == 1) launch(k_conv_fwd_pipe<1, false>);
+    else e = cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return report_error(LB_ECUDA, std::string("conv fwd (tiled): ") + cudaGetErrorString(e));
+  count_launches(1);
+  return LB_OK;
 }
 
 static int pick_kc(int Cin) {
@@ -783,41 +838,8 @@ int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, con
     return report_error(LB_EINVAL, "tensors must be 16-byte aligned");
   ConvGeo g{nx, ny, nz, nb, (int)(periodic & 1u), (int)((periodic >> 1) & 1u), (int)((periodic >> 2) & 1u)};
   cudaStream_t st = (cudaStream_t)stream;
-  if (taps == 27 && nx % 8 == 0 && ny % 16 == 0) {
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const PConvCfg c = pconv_choose(cin, cout, nx, ny, nz, nb, nsm);
-    if (!c.tz) return report_error(LB_EINVAL, "conv fwd: no tiled configuration fits shared memory");
-    const size_t smem = conv_smem(pconv_smem_need(c.tz, c.kc, c.ct, c.merge, c.nsw), 2 * c.tz * c.ct);
-    PConvArgs a{(const __nv_bfloat16*)x, (const __nv_bfloat16*)w, bias, (__nv_bfloat16*)y, yf, cin, cout, ldy,
-                c.kc, c.ct, c.nsw, g, relu, status};
-    cudaError_t e = cudaSuccess;
-    auto launch = [&](auto kern) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return;
-      int occ = 1;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PCONV_THREADS, smem);
-      if (e != cudaSuccess) return;
-      const long long cap = (long long)nsm * (occ > 0 ? occ : 1);
-      const unsigned blocks = (unsigned)(c.items < cap ? c.items : cap);
-      kern<<<blocks, PCONV_THREADS, smem, st>>>(a);
-      e = cudaGetLastError();
-    };
-    if (c.merge) {
-      if (c.tz == 8) launch(k_conv_fwd_pipe<8, true>);
-      else if (c.tz == 4) launch(k_conv_fwd_pipe<4, true>);
-      else if (c.tz == 2) launch(k_conv_fwd_pipe<2, true>);
-      else launch(k_conv_fwd_pipe<1, true>);
-    } else {
-      if (c.tz == 2) launch(k_conv_fwd_pipe<2, false>);
-      else if (c.tz == 1) launch(k_conv_fwd_pipe<1, false>);
-      else e = cudaErrorInvalidValue;
-    }
-    if (e != cudaSuccess) return report_error(LB_ECUDA, std::string("conv fwd (tiled): ") + cudaGetErrorString(e));
-    count_launches(1);
-    return LB_OK;
-  }
+  if (taps == 27 && nx % 8 == 0 && ny % 16 == 0)
+    return conv_fwd_pipe(x, cin, nullptr, cin, w, bias, y, yf, cout, ldy, g, relu, status, st);
   const int KC = pick_kc(cin);
   const size_t smem = conv_fwd_smem(cout, KC);
   const unsigned blocks = (unsigned)((nvox + CONV_M - 1) / CONV_M);
@@ -837,6 +859,25 @@ int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, con
   if (e != cudaSuccess) return report_error(LB_ECUDA, std::string("conv fwd: ") + cudaGetErrorString(e));
   count_launches(1);
   return LB_OK;
+}
+
+int lbnn_conv3d_fwd_upcat(const void* skip, int32_t cs, const void* low, int32_t cl, const void* w, const float* bias,
+                          void* y, float* yf, int32_t cout, int32_t ldy, int32_t nx, int32_t ny, int32_t nz, int32_t nb,
+                          uint32_t periodic, int32_t relu, unsigned* status, void* stream) {
+  if (!skip || !low || !w || (!y && !yf) || !status) return report_error(LB_EINVAL, "null pointer");
+  if (cs < 16 || cs % 16 || cl < 16 || cl % 16 || cs + cl > 1024)
+    return report_error(LB_EINVAL, "cs, cl must be multiples of 16 with cs + cl <= 1024");
+  if (cout < 16 || cout % 16 || cout > 256) return report_error(LB_EINVAL, "cout must be a multiple of 16 in [16, 256]");
+  if (nx < 8 || nx % 8 || ny < 16 || ny % 16 || nz < 2 || nz % 2 || nb < 1)
+    return report_error(LB_EINVAL, "needs nx % 8 == 0, ny % 16 == 0 and an even nz");
+  if (ldy == 0) ldy = cout;
+  if (ldy < cout || ldy % 8) return report_error(LB_EINVAL, "ldy must be >= cout and a multiple of 8");
+  const long long nvox = (long long)nx * ny * nz * nb;
+  if (nvox > (1ll << 31)) return report_error(LB_EINVAL, "too many voxels");
+  if (((uintptr_t)skip | (uintptr_t)low | (uintptr_t)w | (uintptr_t)y | (uintptr_t)yf) & 15)
+    return report_error(LB_EINVAL, "tensors must be 16-byte aligned");
+  ConvGeo g{nx, ny, nz, nb, (int)(periodic & 1u), (int)((periodic >> 1) & 1u), (int)((periodic >> 2) & 1u)};
+  return conv_fwd_pipe(skip, cs, low, cs + cl, w, bias, y, yf, cout, ldy, g, relu, status, (cudaStream_t)stream);
 }
 
 int lbnn_conv3d_wgrad(const void* dy, int32_t cout, const void* x, int32_t cin, int32_t taps, float* dw, int32_t nx,

@@ -104,6 +104,21 @@ int conv(SurrogateState* S, int li, const void* in, void* out_bf, float* out_f, 
                          S->status, st);
 }
 
+// Grids on which lbnn_conv3d_fwd_upcat reads the skip tensor and the
+// upsampled coarse tensor directly (no concatenated copy).
+bool upcat_fused(int nx, int ny, int nz) { return nx % 8 == 0 && ny % 16 == 0 && nz % 2 == 0; }
+
+// conv(li) of concat(skip, up2(low)) at extents (nx, ny, nz)
+int conv_cat(SurrogateState* S, int li, const void* skip, int cs, const void* low, int cl, void* ubuf, void* out,
+             int nx, int ny, int nz, cudaStream_t st) {
+  const UnetLayer& L = S->layers[li];
+  if (upcat_fused(nx, ny, nz))
+    return lbnn_conv3d_fwd_upcat(skip, cs, low, cl, L.w, L.b, out, nullptr, L.co, 0, nx, ny, nz, 1, S->periodic, L.relu,
+                                 S->status, st);
+  const int rc = lbnn_up_concat(skip, cs, low, cl, nx, ny, nz, 1, ubuf, st);
+  return rc ? rc : conv(S, li, ubuf, out, nullptr, nx, ny, nz, st);
+}
+
 // U-Net forward on x (the handle's grid) into S->head
 int forward(SurrogateState* S, int nx, int ny, int nz, cudaStream_t st) {
   const int c1 = S->base, c2 = 2 * c1, c3 = 4 * c1, c4 = 8 * c1;
@@ -122,14 +137,11 @@ int forward(SurrogateState* S, int nx, int ny, int nz, cudaStream_t st) {
   LBNN_TRY(lbnn_avgpool2(a[5], c3, nx / 4, ny / 4, nz / 4, 1, S->p3, st));
   LBNN_TRY(conv(S, 6, S->p3, a[6], nullptr, nx / 8, ny / 8, nz / 8, st));
   LBNN_TRY(conv(S, 7, a[6], a[7], nullptr, nx / 8, ny / 8, nz / 8, st));  // b4
-  LBNN_TRY(lbnn_up_concat(a[5], c3, a[7], c4, nx / 4, ny / 4, nz / 4, 1, S->u3, st));
-  LBNN_TRY(conv(S, 8, S->u3, a[8], nullptr, nx / 4, ny / 4, nz / 4, st));
+  LBNN_TRY(conv_cat(S, 8, a[5], c3, a[7], c4, S->u3, a[8], nx / 4, ny / 4, nz / 4, st));
   LBNN_TRY(conv(S, 9, a[8], a[9], nullptr, nx / 4, ny / 4, nz / 4, st));  // d3
-  LBNN_TRY(lbnn_up_concat(a[3], c2, a[9], c3, nx / 2, ny / 2, nz / 2, 1, S->u2, st));
-  LBNN_TRY(conv(S, 10, S->u2, a[10], nullptr, nx / 2, ny / 2, nz / 2, st));
+  LBNN_TRY(conv_cat(S, 10, a[3], c2, a[9], c3, S->u2, a[10], nx / 2, ny / 2, nz / 2, st));
   LBNN_TRY(conv(S, 11, a[10], a[11], nullptr, nx / 2, ny / 2, nz / 2, st));  // d2
-  LBNN_TRY(lbnn_up_concat(a[1], c1, a[11], c2, nx, ny, nz, 1, S->u1, st));
-  LBNN_TRY(conv(S, 12, S->u1, a[12], nullptr, nx, ny, nz, st));
+  LBNN_TRY(conv_cat(S, 12, a[1], c1, a[11], c2, S->u1, a[12], nx, ny, nz, st));
   LBNN_TRY(conv(S, 13, a[12], a[13], nullptr, nx, ny, nz, st));  // d1
   LBNN_TRY(conv(S, 14, a[13], nullptr, S->head, nx, ny, nz, st));
 #undef LBNN_TRY
@@ -214,11 +226,14 @@ int lb_surrogate_load(lb_handle* h, const char* path) {
   S->p1 = (__nv_bfloat16*)dalloc(lv[1] * c1 * 2);
   S->p2 = (__nv_bfloat16*)dalloc(lv[2] * c2 * 2);
   S->p3 = (__nv_bfloat16*)dalloc(lv[3] * c3 * 2);
-  S->u3 = (__nv_bfloat16*)dalloc(lv[2] * (c3 + c4) * 2);
-  S->u2 = (__nv_bfloat16*)dalloc(lv[1] * (c2 + c3) * 2);
-  S->u1 = (__nv_bfloat16*)dalloc(lv[0] * (c1 + c2) * 2);
+  // concatenated decoder inputs, only for levels the fused up-concat convolution cannot take
+  const bool f3 = upcat_fused(nx / 4, ny / 4, nz / 4), f2 = upcat_fused(nx / 2, ny / 2, nz / 2),
+             f1 = upcat_fused(nx, ny, nz);
+  S->u3 = f3 ? nullptr : (__nv_bfloat16*)dalloc(lv[2] * (c3 + c4) * 2);
+  S->u2 = f2 ? nullptr : (__nv_bfloat16*)dalloc(lv[1] * (c2 + c3) * 2);
+  S->u1 = f1 ? nullptr : (__nv_bfloat16*)dalloc(lv[0] * (c1 + c2) * 2);
   bool all = S->fields && S->cand && S->judge_phi && S->x && S->head && S->status && S->partials && S->p1 && S->p2 &&
-             S->p3 && S->u1 && S->u2 && S->u3;
+             S->p3 && (f1 || S->u1) && (f2 || S->u2) && (f3 || S->u3);
   for (auto* p : S->act) all = all && p;
   if (!all) {
     delete S;

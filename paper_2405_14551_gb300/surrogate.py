@@ -145,6 +145,22 @@ class UNet:
         self._check(self.lib.lbnn_up_concat(_p(skip), cs, _p(low), cl, nx, ny, nz, nb, _p(y), self.sp), "up_concat")
         return y
 
+    def _conv_cat(self, name, key, skip, cs, low, cl, level, shape):
+        """Decoder convolution of concat(skip, up2(low)).  Where the grid allows
+        it, the kernel reads both sources in place; the concatenated copy the
+        weight gradient needs is then built in backward()."""
+        nx, ny, nz, nb = self._dims(level, shape)
+        if nx % 8 or ny % 16 or nz % 2:
+            return self._conv(name, self._upcat(key, skip, cs, low, cl, level, shape), level, shape)
+        _, ci, co, taps, relu = self.spec[name]
+        out = self._buf(("act", name), (nx * ny * nz * nb, co), self.torch.bfloat16)
+        rc = self.lib.lbnn_conv3d_fwd_upcat(_p(skip), cs, _p(low), cl, _p(self.wbf[name]), _p(self.b32[name]),
+                                            _p(out), None, co, 0, nx, ny, nz, nb, self.periodic, relu,
+                                            _p(self.status), self.sp)
+        self._check(rc, f"conv {name}")
+        self.acts[("in", name)] = (key, skip, cs, low, cl, level)
+        return out
+
     def forward(self, x, shape):
         """x: BF16 [nvox][CIN] on the device; shape = (nx, ny, nz, nb).
         Returns the FP32 head output [nvox][COUT]."""
@@ -161,11 +177,11 @@ class UNet:
         s3 = self._conv("c3b", a, 2, shape)
         a = self._conv("c4a", self._pool("p3", s3, sp["c3b"][2], 2, shape), 3, shape)
         b4 = self._conv("c4b", a, 3, shape)
-        a = self._conv("c5a", self._upcat("u3", s3, sp["c3b"][2], b4, sp["c4b"][2], 2, shape), 2, shape)
+        a = self._conv_cat("c5a", "u3", s3, sp["c3b"][2], b4, sp["c4b"][2], 2, shape)
         d3 = self._conv("c5b", a, 2, shape)
-        a = self._conv("c6a", self._upcat("u2", s2, sp["c2b"][2], d3, sp["c5b"][2], 1, shape), 1, shape)
+        a = self._conv_cat("c6a", "u2", s2, sp["c2b"][2], d3, sp["c5b"][2], 1, shape)
         d2 = self._conv("c6b", a, 1, shape)
-        a = self._conv("c7a", self._upcat("u1", s1, sp["c1b"][2], d2, sp["c6b"][2], 0, shape), 0, shape)
+        a = self._conv_cat("c7a", "u1", s1, sp["c1b"][2], d2, sp["c6b"][2], 0, shape)
         d1 = self._conv("c7b", a, 0, shape)
         nx, ny, nz, nb = shape
         y = self._buf(("act", "head32"), (nx * ny * nz * nb, COUT), self.torch.float32)
@@ -187,6 +203,9 @@ class UNet:
                                            _p(gpre_b), _p(gpre_f), self.sp), "relu_bwd")
         self._check(self.lib.lbnn_bias_grad(_p(gpre_f), nv, co, _p(self.gb[name]), self.sp), "bias_grad")
         x = self.acts[("in", name)]
+        if isinstance(x, tuple):  # fused up-concat in forward: build the concatenated input now
+            key, skip, cs, low, cl, lev = x
+            x = self._upcat(key, skip, cs, low, cl, lev, self.shape)
         vpc = max(64, min(8192, (nv // 256 + 63) // 64 * 64))
         self._check(self.lib.lbnn_conv3d_wgrad(_p(gpre_b), co, _p(x), ci, taps, _p(self.gw[name]), nx, ny, nz, nb,
                                                self.periodic, vpc, _p(self.status), self.sp),

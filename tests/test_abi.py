@@ -90,3 +90,21 @@ def test_null_handle_rejected(lib):
     assert lib.lb_surrogate_load(None, b"x") == L.LB_EINVAL
     assert lib.lb_surrogate_predict(None, None) == L.LB_EINVAL
     assert lib.lb_get_nc_tile(None) == -1
+
+
+def test_conv_argument_checks_without_gpu(lib):
+    """The convolution entry points validate their arguments on the host
+    before any launch (null tensors, channel counts, extents)."""
+    import paper_2405_14551_gb300.lbcg as L
+    st = ctypes.c_void_p(16)
+    assert lib.lbnn_conv3d_fwd(None, 16, None, 27, None, None, None, 16, 0, 8, 16, 4, 1, 0, 0, st, None) == L.LB_EINVAL
+    buf = ctypes.c_void_p(256)  # never dereferenced: every call below is rejected first
+    assert lib.lbnn_conv3d_fwd(buf, 24, buf, 27, None, buf, None, 16, 0, 8, 16, 4, 1, 0, 0, st, None) == L.LB_EINVAL
+    assert lib.lbnn_conv3d_fwd_upcat(None, 32, buf, 64, buf, None, buf, None, 32, 0, 16, 16, 4, 1, 0, 1, st,
+                                     None) == L.LB_EINVAL
+    assert lib.lbnn_conv3d_fwd_upcat(buf, 24, buf, 64, buf, None, buf, None, 32, 0, 16, 16, 4, 1, 0, 1, st,
+                                     None) == L.LB_EINVAL
+    assert lib.lbnn_conv3d_fwd_upcat(buf, 32, buf, 64, buf, None, buf, None, 32, 0, 16, 8, 4, 1, 0, 1, st,
+                                     None) == L.LB_EINVAL  # ny % 16
+    assert lib.lbnn_conv3d_fwd_upcat(buf, 32, buf, 64, buf, None, buf, None, 32, 0, 16, 16, 3, 1, 0, 1, st,
+                                     None) == L.LB_EINVAL  # odd nz

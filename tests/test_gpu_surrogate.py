@@ -102,6 +102,39 @@ def test_conv_forward_tiled(dims, cin, cout, per, relu, ldy):
     assert np.abs(gb - ref).max() <= 1e-2 * max(1.0, np.abs(ref).max())  # BF16 copy of the same values
 
 
+@pytest.mark.parametrize("dims,cs,cl,cout,per", [
+    ((16, 16, 4, 1), 32, 64, 32, 5), ((16, 32, 8, 1), 64, 128, 64, 7), ((8, 16, 4, 1), 128, 256, 128, 5),
+    ((32, 32, 48, 2), 32, 64, 32, 2)])
+def test_conv_forward_upcat(dims, cs, cl, cout, per):
+    """The decoder convolution reading the skip tensor and the half-resolution
+    tensor in place equals the convolution of their concatenation (nearest x2
+    upsampling), against the FP64 reference."""
+    import torch
+    import paper_2405_14551_gb300.lbcg as L
+    lib = L.load_library()
+    rng = np.random.default_rng(cs + cl + cout + dims[2])
+    nx, ny, nz, nb = dims
+    skip = _bf(rng.standard_normal((nb, nz, ny, nx, cs)))
+    low = _bf(rng.standard_normal((nb, nz // 2, ny // 2, nx // 2, cl)))
+    up = low.repeat(2, axis=1).repeat(2, axis=2).repeat(2, axis=3)
+    X = np.concatenate([skip, up], axis=-1)
+    W = _bf(rng.standard_normal((cout, 27, cs + cl)) / np.sqrt(27 * (cs + cl)))
+    b = rng.standard_normal(cout).astype(np.float32)
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(dev)
+    Sd, Ld, Wd = t(skip), t(low), t(W)
+    bd = torch.from_numpy(b).to(dev)
+    Yf = torch.zeros((nb, nz, ny, nx, cout), dtype=torch.float32, device=dev)
+    st = torch.zeros(4, dtype=torch.int32, device=dev)
+    rc = lib.lbnn_conv3d_fwd_upcat(Sd.data_ptr(), cs, Ld.data_ptr(), cl, Wd.data_ptr(), bd.data_ptr(), None,
+                                   Yf.data_ptr(), cout, 0, nx, ny, nz, nb, per, 1, st.data_ptr(), None)
+    assert rc == 0, lib.lb_last_error()
+    torch.cuda.synchronize()
+    ref = np.maximum(U.conv3d(X, W, b.astype(np.float64), (per & 1, (per >> 1) & 1, (per >> 2) & 1), 27), 0)
+    assert int(st[0].item()) == 0
+    assert np.abs(Yf.cpu().numpy() - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
 @pytest.mark.parametrize("dims,cin,cout,taps,per,vpc", [
     ((8, 4, 4, 1), 16, 16, 1, 7, 64), ((8, 4, 4, 1), 16, 32, 27, 7, 64), ((8, 8, 8, 1), 32, 64, 27, 5, 128),
     ((8, 4, 8, 2), 96, 32, 27, 2, 64), ((8, 4, 4, 1), 128, 256, 27, 5, 64)])

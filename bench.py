@@ -387,8 +387,7 @@ def surrogate_extra(L, stream, ntraj=16, iters=2000, cycles=20, spinup=2000):
         L.lb_copy_state(b.h, a.h)
         b.step(100)
         L.lb_copy_state(b.h, a.h)
-        ctl.jumps, ctl.suspended, ctl.accepted, ctl.rejected, ctl.judged = 0, 0, 0, 0, []
-        ctl.cycle, ctl.trusted = 0, False
+        ctl.reset()
         torch.cuda.synchronize()
         t2 = time.time()
         ctl.run(cycles)

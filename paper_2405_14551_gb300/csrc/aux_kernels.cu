@@ -224,11 +224,21 @@ __global__ void k_cc_init(Geo g, const R* __restrict__ phi, int* __restrict__ L)
     L[i] = (!node_solid(g, i) && phi[i] > R(0)) ? (int)i : -1;
 }
 
+// Root of i.  Every parent label is smaller than its child's (init: L[i] = i;
+// a root is only ever hooked under a smaller root), so each node met on the
+// way may be pointed at its grandparent (path halving, as in intermediate
+// pointer jumping): the writes only shorten paths and keep the forest valid
+// under concurrent unions.  -1 if the walk exceeded its limit.
 __device__ __forceinline__ int cc_find(volatile int* L, int i, long long limit) {
+  int curr = L[i];
+  if (curr == i) return i;
+  int prev = i;
   for (long long it = 0; it < limit; ++it) {
-    const int p = L[i];
-    if (p == i) return i;
-    i = p;
+    const int next = L[curr];
+    if (next >= curr) return curr;  // a root (next == curr)
+    L[prev] = next;
+    prev = curr;
+    curr = next;
   }
   return -1;
 }

@@ -389,11 +389,14 @@ class Controller:
     handle from the exact same state (mean |phi_sur - phi_LB| <= phi_tol),
     acceptance by regularised reconstruction or the LB result.  This class
     holds the policy: every jump is judged until one passes, then every
-    judge_every-th; a failed judgement withdraws the trust and suspends the
-    surrogate for backoff cycles (2K plain steps per cycle)."""
+    judge_every-th; a judgement that passes with a margin (error <= margin x
+    phi_tol) doubles the interval up to judge_max, one that passes without it
+    keeps the interval, and a failed judgement withdraws the trust, resets
+    the interval and suspends the surrogate for backoff cycles (2K plain
+    steps per cycle)."""
 
     def __init__(self, sim, net, shape, K=50, vol_tol=0.02, phi_tol=1e-2, judge_every=4, backoff=8,
-                 stream=None):
+                 judge_max=16, margin=0.75, stream=None):
         import os
         import tempfile
         import torch
@@ -413,6 +416,9 @@ class Controller:
             os.remove(path)
         self.vol_tol, self.phi_tol = vol_tol, phi_tol
         self.judge_every, self.backoff = judge_every, backoff
+        self.judge_max, self.margin = judge_max, margin
+        self.interval = judge_every
+        self.since = 0         # jumps since the last judgement
         self.accepted = 0
         self.rejected = 0
         self.judged = []       # (cycle, mean |phi_sur - phi_LB|)
@@ -421,9 +427,19 @@ class Controller:
         self.jumps = 0
         self.trusted = False   # set by a passing judgement
 
+    def reset(self):
+        """Forget the counters and the trust (the network and lattices stay)."""
+        self.accepted = self.rejected = self.suspended = self.cycle = self.jumps = self.since = 0
+        self.judged = []
+        self.trusted = False
+        self.interval = self.judge_every
+
     def jump(self):
         """One surrogate jump (or its LB replacement); returns (accepted, info)."""
-        judge = (not self.trusted) or self.jumps % self.judge_every == 0
+        self.since += 1
+        judge = (not self.trusted) or self.since >= self.interval
+        if judge:
+            self.since = 0
         self.jumps += 1
         ok, err = L.lb_surrogate_cycle(self.sim.h, self.shadow.h if judge else None, self.K, self.vol_tol,
                                        self.phi_tol)
@@ -431,9 +447,12 @@ class Controller:
         if judge:
             self.judged.append((self.cycle, err))
             if ok:
+                if self.trusted and err <= self.margin * self.phi_tol:
+                    self.interval = min(2 * self.interval, self.judge_max)
                 self.trusted = True
             else:
                 self.trusted = False
+                self.interval = self.judge_every
                 self.suspended = self.backoff
         if ok:
             self.accepted += 1

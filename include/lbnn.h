@@ -44,8 +44,10 @@ int lbnn_conv3d_fwd_upcat(const void* skip, int32_t cs, const void* low, int32_t
                           uint32_t periodic, int32_t relu, unsigned* status, void* stream);
 
 /* dw[co][t][ci] += sum_v dy[v][co] x[v + off_t][ci] (FP32, accumulated with
- * atomics; clear dw first).  Voxels are split into slices of vox_per_cta
- * (multiple of 64) per CTA; cout a multiple of 16 up to 256. */
+ * atomics; clear dw first); cout a multiple of 16 up to 256.  With taps = 27,
+ * nx % 8 == 0 and ny % 16 == 0 the sum runs over 8 x 16 plane blocks, each
+ * CTA adding its partial sums once; otherwise voxels are split into slices
+ * of vox_per_cta per CTA.  vox_per_cta: a multiple of 64 in either case. */
 int lbnn_conv3d_wgrad(const void* dy, int32_t cout, const void* x, int32_t cin, int32_t taps, float* dw, int32_t nx,
                       int32_t ny, int32_t nz, int32_t nb, uint32_t periodic, int32_t vox_per_cta, unsigned* status,
                       void* stream);

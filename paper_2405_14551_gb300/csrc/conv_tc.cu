@@ -555,6 +555,208 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
 }
 
 // ---------------------------------------------------------------------------
+// weight gradient, spatially tiled and pipelined (3x3x3 taps)
+// ---------------------------------------------------------------------------
+// dW[co][t][ci] = sum_v dY[v][co] X[v + off_t][ci], summed over plane blocks
+// of 8 (x) x 16 (y) voxels.  One operand, H (CH channels), is staged with a
+// one-voxel halo, its planes ordered (channel group, z):
+//   piece (plane lp = 3 hg + zz - 16 j, yy, xx) of 8 channels at (lp * 18 + yy) * 10 + xx,
+// the other, P (CP channels), for the block alone:
+//   piece (pg, y, x) at (pg * 16 + y) * 8 + x.
+// Both are MN-major operands (8 channels contiguous, 8 x voxels 16 bytes
+// apart).  One UMMA D[M = 128][N = CN] += H(dx, dy) P over K = 16 voxels
+// (two y rows) then adds, for one (dx, dy), the three z taps of 16 / 3
+// channel groups at once: M row (lp, e) is channel 8 hg + e at dz = zz - 1.
+// O1: H = X, P = dY: D row (ci, dz), column co, tap offset +(dx, dy, dz).
+// O2: H = dY, P = X: D row (co, dz), column ci, tap offset -(dx, dy, dz)
+//     (sum_v dY[v] X[v + off] = sum_u dY[u - off] X[u]).
+// A pass is (M block j, group of (dx, dy) taps, slice of P channels); every
+// CTA accumulates its pass over its run of blocks in tensor memory and adds
+// the result to dW with FP32 atomics once.  Warp roles and bounded waits as
+// in the forward kernel.
+constexpr int WCONV_HPLANE = 180 * 16;           // bytes of one staged halo plane
+constexpr int WCONV_HBYTES = 16 * WCONV_HPLANE;  // the 16 planes of an M block
+
+struct WConvArgs {
+  const __nv_bfloat16* H;  // [v][CH]
+  const __nv_bfloat16* P;  // [v][CP]
+  float* dW;               // [Cout][27][Cin]
+  int CH, CP, Cin, o2;
+  int CN, TG, ngroups, nchunks, blocks_per_cta;
+  ConvGeo g;
+  unsigned* status;
+};
+
+__global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs P) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  const int CN = P.CN;
+  const size_t p_bytes = (size_t)128 * CN * 2, stage_bytes = WCONV_HBYTES + p_bytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
+  uint64_t* full = bar;
+  uint64_t* empty = bar + 2;
+  uint64_t* done = bar + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // this CTA's pass and run of blocks
+  int pass = blockIdx.y;
+  const int nc = pass % P.nchunks;
+  pass /= P.nchunks;
+  const int grp = pass % P.ngroups;
+  const int mj = pass / P.ngroups;
+  const int n0 = nc * CN;
+  const int ntap = min(P.TG, 9 - grp * P.TG), tap0 = grp * P.TG;
+  const ConvGeo& g = P.g;
+  const int bxs = g.nx / 8, bys = g.ny / 16;
+  const long long nblocks = (long long)bxs * bys * g.nz * g.nb;
+  const long long b_begin = (long long)blockIdx.x * P.blocks_per_cta;
+  const long long b_end = b_begin + P.blocks_per_cta < nblocks ? b_begin + P.blocks_per_cta : nblocks;
+  const int nmine = b_end > b_begin ? (int)(b_end - b_begin) : 0;
+  const int nplanes = 3 * (P.CH / 8);  // valid (hg, zz) planes over all M blocks
+  uint32_t ncols = 32;
+  while ((int)ncols < ntap * CN) ncols <<= 1;
+
+  if (warp == PCONV_MMA_WARP) {
+    tc::tmem_alloc(tmem_slot, ncols);
+    tc::tmem_relinquish();
+  }
+  if (t == 0) {
+    for (int k = 0; k < 2; ++k) {
+      tc::mbar_init(&full[k], PCONV_NPROD);
+      tc::mbar_init(&empty[k], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  auto block_of = [&](long long bi, int& x0, int& y0, int& z, int& b) {
+    x0 = (int)(bi % bxs) * 8;
+    bi /= bxs;
+    y0 = (int)(bi % bys) * 16;
+    bi /= bys;
+    z = (int)(bi % g.nz);
+    b = (int)(bi / g.nz);
+  };
+
+  if (t >= PCONV_PROD0 && t < PCONV_PROD0 + PCONV_NPROD) {
+    // ------------------------------------------------------------ copies
+    const int pt = t - PCONV_PROD0;
+    const int hrow0 = pt / 10, hxx = pt % 10;  // 12 halo rows per pass (120 threads)
+    const bool hact = pt < 120;
+    bool ok = true;
+    for (int i = 0; i < nmine && ok; ++i) {
+      const int s = i & 1;
+      if (i >= 2 && !pconv_wait(&empty[s], (uint32_t)(((i >> 1) - 1) & 1), abort_flag)) {
+        ok = false;
+        break;
+      }
+      int x0, y0, z, b;
+      block_of(b_begin + i, x0, y0, z, b);
+      unsigned char* sH = smem + (size_t)s * stage_bytes;
+      unsigned char* sP = sH + WCONV_HBYTES;
+      if (hact) {
+        const int gx = wrap_or_pad(x0 - 1 + hxx, g.nx, g.px);
+        for (int row = hrow0; row < 16 * 18; row += 12) {
+          const int lp = row / 18, yy = row - 18 * lp;
+          const int p = 16 * mj + lp;
+          const int hg = p / 3, zz = p - 3 * hg;
+          const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
+          const int gz = wrap_or_pad(z - 1 + zz, g.nz, g.pz);
+          const bool in = p < nplanes && gx >= 0 && gy >= 0 && gz >= 0;
+          const long long v = in ? (((long long)b * g.nz + gz) * g.ny + gy) * g.nx + gx : 0;
+          tc::cp_async16(sH + (size_t)(row * 10 + hxx) * 16, P.H + v * P.CH + hg * 8, in);
+        }
+      }
+      const long long vrow = (((long long)b * g.nz + z) * g.ny + y0) * g.nx + x0;
+      for (int q = pt; q < 128 * (CN / 8); q += PCONV_NPROD) {
+        const int x = q & 7, y = (q >> 3) & 15, pg = q >> 7;
+        tc::cp_async16(sP + (size_t)q * 16, P.P + (vrow + (long long)y * g.nx + x) * P.CP + n0 + pg * 8, true);
+      }
+      tc::cp_async_commit();
+      tc::cp_async_wait<0>();
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&full[s]);
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      atomicOr(P.status, CONV_TIMEOUT);
+    }
+  } else if (warp == PCONV_MMA_WARP) {
+    // ------------------------------------------------------------ UMMA issue
+    if ((t & 31) == 0) {
+      const uint32_t idesc = tc::idesc_bf16(CONV_M, CN, true, true);
+      bool ok = true;
+      for (int i = 0; i < nmine; ++i) {
+        const int s = i & 1;
+        if (!pconv_wait(&full[s], (uint32_t)((i >> 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t h0 = tc::smem_u32(smem + (size_t)s * stage_bytes);
+        const uint32_t p0 = h0 + WCONV_HBYTES;
+        for (int tt = 0; tt < ntap; ++tt) {
+          const int dxy = tap0 + tt, dxp = dxy % 3, dyp = dxy / 3;
+          const uint32_t a0 = h0 + (uint32_t)(dyp * 10 + dxp) * 16;
+          for (int k = 0; k < 8; ++k) {
+            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)k * 320, 160, WCONV_HPLANE);
+            const uint64_t bd = tc::smem_desc(p0 + (uint32_t)k * 256, 128, 2048);
+            tc::mma_bf16(tmem + (uint32_t)(tt * CN), ad, bd, idesc, (i > 0 || k > 0) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&empty[s]);
+      }
+      tc::mma_commit(done);  // every UMMA of this CTA, or none
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(P.status, CONV_TIMEOUT);
+      }
+    }
+    __syncwarp();
+  } else if (warp < 4) {
+    // ------------------------------------------------------------ epilogue
+    bool ok = __all_sync(0xffffffffu, pconv_wait(done, 0u, abort_flag));
+    ok = __all_sync(0xffffffffu, ok && *abort_flag == 0);  // no partial sums after a give-up
+    tc::fence_after_sync();
+    const int m = t;
+    const int lp = m >> 3, e = m & 7;
+    const int p = 16 * mj + lp;
+    const bool valid = ok && nmine > 0 && p < nplanes;
+    const int hg = p / 3, zz = p - 3 * hg, hch = hg * 8 + e;
+    if (ok && nmine > 0) {
+      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      for (int tt = 0; tt < ntap; ++tt) {
+        const int dxy = tap0 + tt, dxp = dxy % 3, dyp = dxy / 3;
+        const int tap = P.o2 ? (2 - dxp) + 3 * (2 - dyp) + 9 * (2 - zz) : dxp + 3 * dyp + 9 * zz;
+        for (int col = 0; col < CN; col += 16) {
+          float a[16];
+          tc::tmem_ld16(lane_base + (uint32_t)(tt * CN + col), a);
+          if (valid) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int pch = n0 + col + k;
+              const int co = P.o2 ? hch : pch, ci = P.o2 ? pch : hch;
+              atomicAdd(P.dW + ((size_t)co * 27 + tap) * P.Cin + ci, a[k]);
+            }
+          }
+        }
+      }
+    } else if (!ok && t == 0) {
+      *abort_flag = 1;
+      atomicOr(P.status, CONV_TIMEOUT);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == PCONV_MMA_WARP) tc::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
 // weight gradient
 // ---------------------------------------------------------------------------
 // dW[co][(t,ci)] = sum_v X[v + off_t][ci] dY[v][co] as D[M = 128 (t,ci)
@@ -810,6 +1012,55 @@ static int conv_fwd_pipe(const void* x, int cs, const void* x2, int cin, const v
   return LB_OK;
 }
 
+// Launch of the pipelined weight-gradient kernel: the orientation with fewer
+// UMMAs (H = x or H = dy), the P channel slices and the tap groups that fit
+// tensor memory, and enough voxel runs for every SM.
+static int conv_wgrad_pipe(const void* dy, int cout, const void* x, int cin, float* dw, const ConvGeo& g,
+                           unsigned* status, cudaStream_t st) {
+  struct Or {
+    int o2, CH, CP, mblocks, nchunks, CN, ngroups, TG;
+    long long cost;
+  };
+  auto plan = [](int o2, int CH, int CP) {
+    Or o{o2, CH, CP, (3 * (CH / 8) + 15) / 16, 1, CP, 0, 0, 0};
+    while (o.CN > 256 || o.CP % o.nchunks || (o.CP / o.nchunks) % 16) {
+      ++o.nchunks;
+      o.CN = o.CP / o.nchunks;
+    }
+    o.CN = o.CP / o.nchunks;
+    const int fit = 512 / o.CN;  // taps whose accumulators fit tensor memory together
+    o.ngroups = (9 + fit - 1) / fit;
+    o.TG = (9 + o.ngroups - 1) / o.ngroups;
+    o.cost = (long long)o.mblocks * o.nchunks;
+    return o;
+  };
+  const Or a = plan(0, cin, cout), b = plan(1, cout, cin);
+  const Or o = b.cost < a.cost ? b : a;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long nblocks = (long long)(g.nx / 8) * (g.ny / 16) * g.nz * g.nb;
+  const int npass = o.mblocks * o.ngroups * o.nchunks;
+  long long slices = (nsm + npass - 1) / npass;
+  if (slices > nblocks) slices = nblocks;
+  if (slices < 1) slices = 1;
+  const long long per = (nblocks + slices - 1) / slices;
+  slices = (nblocks + per - 1) / per;
+  if (npass > 65535) return report_error(LB_EINVAL, "conv wgrad: too many passes");
+  const size_t need = 2 * ((size_t)WCONV_HBYTES + (size_t)128 * o.CN * 2) + 64;
+  const size_t smem = conv_smem(need, o.TG * o.CN);
+  WConvArgs args{(const __nv_bfloat16*)(o.o2 ? dy : x), (const __nv_bfloat16*)(o.o2 ? x : dy), dw, o.CH, o.CP, cin,
+                 o.o2, o.CN, o.TG, o.ngroups, o.nchunks, (int)per, g, status};
+  cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    k_conv_wgrad_pipe<<<dim3((unsigned)slices, (unsigned)npass), PCONV_THREADS, smem, st>>>(args);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return report_error(LB_ECUDA, std::string("conv wgrad (tiled): ") + cudaGetErrorString(e));
+  count_launches(1);
+  return LB_OK;
+}
+
 static int pick_kc(int Cin) {
   if (Cin % 64 == 0) return 64;
   if (Cin % 32 == 0) return 32;
@@ -893,6 +1144,7 @@ int lbnn_conv3d_wgrad(const void* dy, int32_t cout, const void* x, int32_t cin, 
   if (nvox > (1ll << 31)) return report_error(LB_EINVAL, "too many voxels");
   if (((uintptr_t)x | (uintptr_t)dy) & 15) return report_error(LB_EINVAL, "tensors must be 16-byte aligned");
   ConvGeo g{nx, ny, nz, nb, (int)(periodic & 1u), (int)((periodic >> 1) & 1u), (int)((periodic >> 2) & 1u)};
+  if (taps == 27 && nx % 8 == 0 && ny % 16 == 0) return conv_wgrad_pipe(dy, cout, x, cin, dw, g, status, (cudaStream_t)stream);
   const size_t smem = conv_wgrad_smem(cout);
   dim3 grid((unsigned)((nvox + vox_per_cta - 1) / vox_per_cta), (unsigned)((taps * cin + CONV_M - 1) / CONV_M));
   cudaStream_t st = (cudaStream_t)stream;

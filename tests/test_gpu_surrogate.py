@@ -137,7 +137,11 @@ def test_conv_forward_upcat(dims, cs, cl, cout, per):
 
 @pytest.mark.parametrize("dims,cin,cout,taps,per,vpc", [
     ((8, 4, 4, 1), 16, 16, 1, 7, 64), ((8, 4, 4, 1), 16, 32, 27, 7, 64), ((8, 8, 8, 1), 32, 64, 27, 5, 128),
-    ((8, 4, 8, 2), 96, 32, 27, 2, 64), ((8, 4, 4, 1), 128, 256, 27, 5, 64)])
+    ((8, 4, 8, 2), 96, 32, 27, 2, 64), ((8, 4, 4, 1), 128, 256, 27, 5, 64),
+    # nx % 8 == 0 and ny % 16 == 0: the pipelined kernel (x or dy as the halo operand,
+    # channel slices and tap groups), including runs of many blocks per CTA
+    ((16, 16, 4, 1), 32, 64, 27, 7, 64), ((8, 16, 6, 2), 96, 32, 27, 5, 64), ((8, 16, 4, 1), 384, 128, 27, 5, 64),
+    ((16, 16, 2, 1), 128, 256, 27, 2, 64), ((8, 16, 4, 1), 16, 32, 27, 0, 64), ((32, 32, 64, 1), 32, 32, 27, 5, 64)])
 def test_conv_weight_gradient(dims, cin, cout, taps, per, vpc):
     import torch
     import paper_2405_14551_gb300.lbcg as L

@@ -330,7 +330,7 @@ def batch_extra(args, L, W, stream):
             "speedup": round(ms_seq / mb, 3)}
 
 
-def surrogate_extra(L, stream, ntraj=16, iters=2000, cycles=20, spinup=2000):
+def surrogate_extra(L, stream, ntraj=24, iters=4000, cycles=20, spinup=2000):
     """The learned surrogate on the 128x128x256 dense emulsion: trajectories
     from the LB itself (seeded emulsions, 2000 spin-up steps, snapshots 50
     steps apart: the slow, late-time regime of a long run), a training run of

@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(128, 1)
 // Accumulators are double buffered (2 TZ CT <= 512 columns), so the epilogue
 // of one work item overlaps the UMMAs of the next.  Every wait is bounded; a
 // wait that gives up sets bit 4 of the status word and the CTA winds down.
+constexpr int PCONV_EPI = 128;     // epilogue threads (warps 0-3, one per tensor-memory lane quarter)
 constexpr int PCONV_THREADS = 288;
 constexpr int PCONV_PROD0 = 128;  // first copy thread
 constexpr int PCONV_NPROD = 128;  // copy threads
@@ -232,10 +233,13 @@ __device__ __forceinline__ int wrap_or_pad(int c, int n, int periodic) {
 }
 
 // Bounded wait that also gives up once another role has given up.
+// After a few polls the waiting warp backs off briefly, so that idle roles do
+// not crowd the shared-memory pipe that the copies and the UMMAs use.
 __device__ __forceinline__ bool pconv_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   for (uint32_t it = 0; it < PCONV_SPIN; ++it) {
     if (tc::mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u && *abort_flag) return false;
+    if (it >= 16) __nanosleep(32);
   }
   return false;
 }
@@ -279,8 +283,10 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
   uint64_t* fin = h_full + 8;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* sbias = reinterpret_cast<float*>(tmem_slot + 4);  // Cout values (0 without bias)
   uint32_t ncols = 32;
   while ((int)ncols < 2 * TZ * CT) ncols <<= 1;
+  for (int c = t; c < P.Cout; c += PCONV_THREADS) sbias[c] = P.bias ? P.bias[c] : 0.0f;
 
   if (warp == PCONV_MMA_WARP) {
     tc::tmem_alloc(tmem_slot, ncols);
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
       tc::mbar_init(&h_full[k], PCONV_NPROD);
       tc::mbar_init(&h_empty[k], 1);
       tc::mbar_init(&a_full[k], 1);
-      tc::mbar_init(&a_empty[k], 128);
+      tc::mbar_init(&a_empty[k], PCONV_EPI);
     }
     tc::mbar_init(fin, 1);
     *abort_flag = 0;
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
     // a thread keeps its (xx, group) place in the row and walks the rows.
     const int hl = 10 * cgs, hr = PCONV_NPROD / hl;
     const bool hact = pt < hr * hl;
-    const int hq = (pt % hl) % cgs, hxx = (pt % hl) / cgs, hr0 = pt / hl;
+    const int hq = (pt % hl) % cgs, hxx = (pt % hl) / cgs, hy0 = pt / hl;
     bool ok = true;
     int gs = 0;
     for (int k = 0; k < my_items && ok; ++k) {
@@ -374,27 +380,18 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
             }
             if (hact) {
               unsigned char* hdst = sH + (size_t)(cg & 1) * halo_bytes + ((size_t)hq * SZH * 180 + hxx) * 16;
-              if (c0 < P.cs) {  // a chunk lies wholly in one source (KC divides cs)
-                const __nv_bfloat16* hsrc = P.X + c0 + hq * 8;
-                for (int row = hr0; row < SZH * 18; row += hr) {
-                  const int zz = row / 18, yy = row - 18 * zz;
-                  const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
-                  const int gz = wrap_or_pad(z0 - 1 + zz, g.nz, g.pz);
-                  const bool in = gx >= 0 && gy >= 0 && gz >= 0;
-                  const long long v = in ? (((long long)b * g.nz + gz) * g.ny + gy) * g.nx + gx : 0;
-                  tc::cp_async16(hdst + (size_t)row * 160, hsrc + v * P.cs, in);
-                }
-              } else {
-                const __nv_bfloat16* hsrc = P.X2 + (c0 - P.cs) + hq * 8;
-                const int hx = g.nx / 2, hy = g.ny / 2, hz = g.nz / 2;
-                for (int row = hr0; row < SZH * 18; row += hr) {
-                  const int zz = row / 18, yy = row - 18 * zz;
-                  const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
-                  const int gz = wrap_or_pad(z0 - 1 + zz, g.nz, g.pz);
-                  const bool in = gx >= 0 && gy >= 0 && gz >= 0;
-                  const long long v = in ? (((long long)b * hz + (gz >> 1)) * hy + (gy >> 1)) * hx + (gx >> 1) : 0;
-                  tc::cp_async16(hdst + (size_t)row * 160, hsrc + v * cl, in);
-                }
+              // a chunk lies wholly in one source (KC divides cs); the second is read at the parent voxel
+              const bool up = c0 >= P.cs;
+              const __nv_bfloat16* hsrc = up ? P.X2 + (c0 - P.cs) + hq * 8 : P.X + c0 + hq * 8;
+              const int sh = up ? 1 : 0, ld = up ? cl : P.cs;
+              const int nyv = g.ny >> sh, nxv = g.nx >> sh, nzv = g.nz >> sh, gxv = gx >> sh;
+              for (int row = hy0; row < SZH * 18; row += hr) {
+                const int zz = row / 18, yy = row - 18 * zz;
+                const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
+                const int gz = wrap_or_pad(z0 - 1 + zz, g.nz, g.pz);
+                const bool in = gx >= 0 && gy >= 0 && gz >= 0;
+                const int v = in ? ((b * nzv + (gz >> sh)) * nyv + (gy >> sh)) * nxv + gxv : 0;
+                tc::cp_async16(hdst + (size_t)row * 160, hsrc + (long long)v * ld, in);
               }
             }
           }
@@ -423,12 +420,17 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
   } else if (warp == PCONV_MMA_WARP) {
     // ------------------------------------------------------------ UMMA issue
     if ((t & 31) == 0) {
-      const uint32_t a_lbo = (uint32_t)HV * 16, a_sbo = 160;
-      const uint32_t b_lbo = (uint32_t)NB * 16, b_sbo = 128;
-      uint32_t idesc[3];
-      for (int k = 0; k < 3; ++k) idesc[k] = tc::idesc_bf16(CONV_M, (k + 1) * CT > 256 ? CT : (k + 1) * CT, false, false);
+      // descriptors: constant part + (shared address >> 4); every offset below is in 16-byte units
+      const uint32_t a_lbo = (uint32_t)HV * 16, b_lbo = (uint32_t)NB * 16;
+      const uint64_t adb = tc::smem_desc_base(a_lbo, 160), bdb = tc::smem_desc_base(b_lbo, 128);
+      const uint32_t a_j = 2 * a_lbo >> 4, b_j = 2 * b_lbo >> 4;  // one k-step of 16 channels
+      const uint32_t id1 = tc::idesc_bf16(CONV_M, CT, false, false);
+      const uint32_t id2 = MERGE ? tc::idesc_bf16(CONV_M, 2 * CT, false, false) : id1;
+      const uint32_t id3 = MERGE ? tc::idesc_bf16(CONV_M, 3 * CT, false, false) : id1;
+      const int njs = KC / 16;
       bool ok = true;
-      int gs = 0;
+      int gs = 0, slot = 0;
+      uint32_t wphase = 0;
       for (int k = 0; k < my_items && ok; ++k) {
         const int ab = k & 1;
         if (k >= 2 && !pconv_wait(&a_empty[ab], (uint32_t)(((k >> 1) - 1) & 1), abort_flag)) {
@@ -445,51 +447,54 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
           }
           const uint32_t hb = tc::smem_u32(sH + (size_t)(cg & 1) * halo_bytes);
           for (int st = 0; st < SPC; ++st, ++gs) {
-            const int slot = gs % nsw;
-            if (!pconv_wait(&w_full[slot], (uint32_t)((gs / nsw) & 1), abort_flag)) {
+            if (!pconv_wait(&w_full[slot], wphase, abort_flag)) {
               ok = false;
               break;
             }
             tc::fence_after_sync();
-            const uint32_t wb = tc::smem_u32(sW + (size_t)slot * w_bytes);
+            const uint64_t b0 = bdb + (tc::smem_u32(sW + (size_t)slot * w_bytes) >> 4);
             if (MERGE) {
               const int dxp = st % 3, dyp = st / 3;
-              const uint32_t h0 = hb + (uint32_t)(dyp * 10 + dxp) * 16;
-              for (int j = 0; j < KC / 16; ++j) {
-                const uint32_t aj = h0 + (uint32_t)j * 2 * a_lbo, bj = wb + (uint32_t)j * 2 * b_lbo;
+              const uint64_t a0 = adb + ((hb + (uint32_t)(dyp * 10 + dxp) * 16) >> 4);
+              for (int j = 0; j < njs; ++j) {
+                const uint64_t aj = a0 + (uint64_t)j * a_j, bj = b0 + (uint64_t)j * b_j;
                 if (c == 0 && st == 0 && j == 0) {
                   // block 1 (dz = 0) initialises every plane, then blocks 0 and 2 accumulate
+#pragma unroll
                   for (int sb = 0; sb < 3; ++sb) {
                     const int s = sb == 0 ? 1 : (sb == 1 ? 0 : 2);
-                    for (int q = 0; q < TZ; ++q) {
-                      const int zz = q + s;
-                      const uint64_t ad = tc::smem_desc(aj + (uint32_t)zz * 180 * 16, a_lbo, a_sbo);
-                      const uint64_t bd = tc::smem_desc(bj + (uint32_t)(s * CT) * 16, b_lbo, b_sbo);
-                      tc::mma_bf16(acc + (uint32_t)((TZ - 1 - q) * CT), ad, bd, idesc[0], s == 1 ? 0u : 1u);
-                    }
+#pragma unroll
+                    for (int q = 0; q < TZ; ++q)
+                      tc::mma_bf16(acc + (uint32_t)((TZ - 1 - q) * CT), aj + (uint64_t)((q + s) * 180),
+                                   bj + (uint64_t)(s * CT), id1, s == 1 ? 0u : 1u);
                   }
                 } else {
+#pragma unroll
                   for (int zz = 0; zz < SZH; ++zz) {
                     const int s_lo = zz - (TZ - 1) > 0 ? zz - (TZ - 1) : 0;
                     const int s_hi = zz < 2 ? zz : 2;
-                    const uint64_t ad = tc::smem_desc(aj + (uint32_t)zz * 180 * 16, a_lbo, a_sbo);
-                    const uint64_t bd = tc::smem_desc(bj + (uint32_t)(s_lo * CT) * 16, b_lbo, b_sbo);
-                    tc::mma_bf16(acc + (uint32_t)((TZ - 1 - zz + s_lo) * CT), ad, bd, idesc[s_hi - s_lo], 1u);
+                    const uint32_t id = s_hi - s_lo == 0 ? id1 : (s_hi - s_lo == 1 ? id2 : id3);
+                    tc::mma_bf16(acc + (uint32_t)((TZ - 1 - zz + s_lo) * CT), aj + (uint64_t)(zz * 180),
+                                 bj + (uint64_t)(s_lo * CT), id, 1u);
                   }
                 }
               }
             } else {
               const int dxp = st % 3, dyp = (st / 3) % 3, dzp = st / 9;
-              const uint32_t h0 = hb + (uint32_t)((dzp * 18 + dyp) * 10 + dxp) * 16;
-              for (int j = 0; j < KC / 16; ++j) {
-                const uint64_t bd = tc::smem_desc(wb + (uint32_t)j * 2 * b_lbo, b_lbo, b_sbo);
-                for (int q = 0; q < TZ; ++q) {
-                  const uint64_t ad = tc::smem_desc(h0 + (uint32_t)q * 180 * 16 + (uint32_t)j * 2 * a_lbo, a_lbo, a_sbo);
-                  tc::mma_bf16(acc + (uint32_t)(q * CT), ad, bd, idesc[0], (c > 0 || st > 0 || j > 0) ? 1u : 0u);
-                }
+              const uint64_t a0 = adb + ((hb + (uint32_t)((dzp * 18 + dyp) * 10 + dxp) * 16) >> 4);
+              for (int j = 0; j < njs; ++j) {
+                const uint64_t aj = a0 + (uint64_t)j * a_j, bj = b0 + (uint64_t)j * b_j;
+                const uint32_t accf = (c > 0 || st > 0 || j > 0) ? 1u : 0u;
+#pragma unroll
+                for (int q = 0; q < TZ; ++q)
+                  tc::mma_bf16(acc + (uint32_t)(q * CT), aj + (uint64_t)(q * 180), bj, id1, accf);
               }
             }
             tc::mma_commit(&w_empty[slot]);
+            if (++slot == nsw) {
+              slot = 0;
+              wphase ^= 1u;
+            }
           }
           if (ok) tc::mma_commit(&h_empty[cg & 1]);
         }
@@ -504,7 +509,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
       }
     }
     __syncwarp();
-  } else if (warp < 4) {
+  } else if (warp < PCONV_EPI / 32) {
     // ------------------------------------------------------------ epilogue
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     const int r = t;  // accumulator row = output voxel (x0 + r % 8, y0 + r / 8)
@@ -523,25 +528,33 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
       for (int q = 0; q < TZ; ++q) {
         const long long v = (((long long)b * g.nz + z0 + q) * g.ny + y) * g.nx + x;
         const uint32_t colq = (uint32_t)(ab * TZ * CT + (MERGE ? TZ - 1 - q : q) * CT);
-        for (int col = 0; col < CT; col += 16) {
-          float a[16];
-          tc::tmem_ld16(lane_base + colq + (uint32_t)col, a);
+        for (int col = 0; col < CT; col += 32) {
+          const bool two = col + 16 < CT;
+          uint32_t u[32];
+          tc::tmem_ld16_nowait(lane_base + colq + (uint32_t)col, u);
+          if (two) tc::tmem_ld16_nowait(lane_base + colq + (uint32_t)col + 16, u + 16);
+          tc::tmem_wait_ld();
+          const int ng = two ? 2 : 1;
+          for (int h = 0; h < ng; ++h) {
+            float a[16];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const float vv = a[e] + (P.bias ? __ldg(P.bias + n0 + col + e) : 0.0f);
-            a[e] = P.relu ? fmaxf(vv, 0.0f) : vv;
-          }
-          if (P.Y) {
-            uint4* yp = reinterpret_cast<uint4*>(P.Y + v * P.ldy + n0 + col);
-            yp[0] = make_uint4(pack_bf16(a[0], a[1]), pack_bf16(a[2], a[3]), pack_bf16(a[4], a[5]),
-                               pack_bf16(a[6], a[7]));
-            yp[1] = make_uint4(pack_bf16(a[8], a[9]), pack_bf16(a[10], a[11]), pack_bf16(a[12], a[13]),
-                               pack_bf16(a[14], a[15]));
-          }
-          if (P.Yf) {
-            float4* fp = reinterpret_cast<float4*>(P.Yf + v * P.ldy + n0 + col);
+            for (int e = 0; e < 16; ++e) {
+              const float vv = __uint_as_float(u[16 * h + e]) + sbias[n0 + col + 16 * h + e];
+              a[e] = P.relu ? fmaxf(vv, 0.0f) : vv;
+            }
+            const int c0 = n0 + col + 16 * h;
+            if (P.Y) {
+              uint4* yp = reinterpret_cast<uint4*>(P.Y + v * P.ldy + c0);
+              yp[0] = make_uint4(pack_bf16(a[0], a[1]), pack_bf16(a[2], a[3]), pack_bf16(a[4], a[5]),
+                                 pack_bf16(a[6], a[7]));
+              yp[1] = make_uint4(pack_bf16(a[8], a[9]), pack_bf16(a[10], a[11]), pack_bf16(a[12], a[13]),
+                                 pack_bf16(a[14], a[15]));
+            }
+            if (P.Yf) {
+              float4* fp = reinterpret_cast<float4*>(P.Yf + v * P.ldy + c0);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) fp[e] = make_float4(a[4 * e], a[4 * e + 1], a[4 * e + 2], a[4 * e + 3]);
+              for (int e = 0; e < 4; ++e) fp[e] = make_float4(a[4 * e], a[4 * e + 1], a[4 * e + 2], a[4 * e + 3]);
+            }
           }
         }
       }
@@ -582,7 +595,7 @@ struct WConvArgs {
   const __nv_bfloat16* P;  // [v][CP]
   float* dW;               // [Cout][27][Cin]
   int CH, CP, Cin, o2;
-  int CN, TG, ngroups, nchunks, blocks_per_cta;
+  int CN, TG, ngroups, nchunks, blocks_per_cta, nst;  // nst: staged blocks in flight (2..4)
   ConvGeo g;
   unsigned* status;
 };
@@ -593,11 +606,12 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
   const int warp = t >> 5;
   const int CN = P.CN;
   const size_t p_bytes = (size_t)128 * CN * 2, stage_bytes = WCONV_HBYTES + p_bytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
+  const int nst = P.nst;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)nst * stage_bytes);
   uint64_t* full = bar;
-  uint64_t* empty = bar + 2;
-  uint64_t* done = bar + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 5);
+  uint64_t* empty = bar + 4;
+  uint64_t* done = bar + 8;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 9);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   // this CTA's pass and run of blocks
   int pass = blockIdx.y;
@@ -622,7 +636,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
     tc::tmem_relinquish();
   }
   if (t == 0) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {
       tc::mbar_init(&full[k], PCONV_NPROD);
       tc::mbar_init(&empty[k], 1);
     }
@@ -648,10 +662,13 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
     const int pt = t - PCONV_PROD0;
     const int hrow0 = pt / 10, hxx = pt % 10;  // 12 halo rows per pass (120 threads)
     const bool hact = pt < 120;
+    // blocks a copy thread keeps in flight before it signals them; the slot it
+    // refills next must belong to a block whose UMMAs were already issued
+    const int lag = nst >= 3 ? nst - 2 : 0;
     bool ok = true;
     for (int i = 0; i < nmine && ok; ++i) {
-      const int s = i & 1;
-      if (i >= 2 && !pconv_wait(&empty[s], (uint32_t)(((i >> 1) - 1) & 1), abort_flag)) {
+      const int s = i % nst;
+      if (i >= nst && !pconv_wait(&empty[s], (uint32_t)(((i / nst) - 1) & 1), abort_flag)) {
         ok = false;
         break;
       }
@@ -664,10 +681,11 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
         for (int row = hrow0; row < 16 * 18; row += 12) {
           const int lp = row / 18, yy = row - 18 * lp;
           const int p = 16 * mj + lp;
+          if (p >= nplanes) break;  // rows of planes past the channels feed D rows nobody reads
           const int hg = p / 3, zz = p - 3 * hg;
           const int gy = wrap_or_pad(y0 - 1 + yy, g.ny, g.py);
           const int gz = wrap_or_pad(z - 1 + zz, g.nz, g.pz);
-          const bool in = p < nplanes && gx >= 0 && gy >= 0 && gz >= 0;
+          const bool in = gx >= 0 && gy >= 0 && gz >= 0;
           const long long v = in ? (((long long)b * g.nz + gz) * g.ny + gy) * g.nx + gx : 0;
           tc::cp_async16(sH + (size_t)(row * 10 + hxx) * 16, P.H + v * P.CH + hg * 8, in);
         }
@@ -678,10 +696,18 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
         tc::cp_async16(sP + (size_t)q * 16, P.P + (vrow + (long long)y * g.nx + x) * P.CP + n0 + pg * 8, true);
       }
       tc::cp_async_commit();
-      tc::cp_async_wait<0>();
-      tc::fence_proxy_async_smem();
-      tc::mbar_arrive(&full[s]);
+      if (i >= lag) {
+        if (lag == 2) tc::cp_async_wait<2>();
+        else if (lag == 1) tc::cp_async_wait<1>();
+        else tc::cp_async_wait<0>();
+        tc::fence_proxy_async_smem();
+        tc::mbar_arrive(&full[(i - lag) % nst]);
+      }
     }
+    tc::cp_async_wait<0>();
+    tc::fence_proxy_async_smem();
+    if (ok)
+      for (int r = nmine > lag ? nmine - lag : 0; r < nmine; ++r) tc::mbar_arrive(&full[r % nst]);
     if (!ok) {
       *abort_flag = 1;
       atomicOr(P.status, CONV_TIMEOUT);
@@ -692,22 +718,22 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
       const uint32_t idesc = tc::idesc_bf16(CONV_M, CN, true, true);
       bool ok = true;
       for (int i = 0; i < nmine; ++i) {
-        const int s = i & 1;
-        if (!pconv_wait(&full[s], (uint32_t)((i >> 1) & 1), abort_flag)) {
+        const int s = i % nst;
+        if (!pconv_wait(&full[s], (uint32_t)((i / nst) & 1), abort_flag)) {
           ok = false;
           break;
         }
         tc::fence_after_sync();
         const uint32_t h0 = tc::smem_u32(smem + (size_t)s * stage_bytes);
-        const uint32_t p0 = h0 + WCONV_HBYTES;
+        const uint64_t bd0 = tc::smem_desc_base(128, 2048) + ((h0 + WCONV_HBYTES) >> 4);
+        const uint64_t ad0 = tc::smem_desc_base(160, WCONV_HPLANE) + (h0 >> 4);
         for (int tt = 0; tt < ntap; ++tt) {
           const int dxy = tap0 + tt, dxp = dxy % 3, dyp = dxy / 3;
-          const uint32_t a0 = h0 + (uint32_t)(dyp * 10 + dxp) * 16;
-          for (int k = 0; k < 8; ++k) {
-            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)k * 320, 160, WCONV_HPLANE);
-            const uint64_t bd = tc::smem_desc(p0 + (uint32_t)k * 256, 128, 2048);
-            tc::mma_bf16(tmem + (uint32_t)(tt * CN), ad, bd, idesc, (i > 0 || k > 0) ? 1u : 0u);
-          }
+          const uint64_t a0 = ad0 + (uint64_t)(dyp * 10 + dxp);
+          const uint32_t d = tmem + (uint32_t)(tt * CN);
+#pragma unroll
+          for (int k = 0; k < 8; ++k)  // k-step: two rows of 8 voxels (320 and 256 bytes on)
+            tc::mma_bf16(d, a0 + (uint64_t)(k * 20), bd0 + (uint64_t)(k * 16), idesc, (i > 0 || k > 0) ? 1u : 0u);
         }
         tc::mma_commit(&empty[s]);
       }
@@ -718,7 +744,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
       }
     }
     __syncwarp();
-  } else if (warp < 4) {
+  } else if (warp < PCONV_EPI / 32) {
     // ------------------------------------------------------------ epilogue
     bool ok = __all_sync(0xffffffffu, pconv_wait(done, 0u, abort_flag));
     ok = __all_sync(0xffffffffu, ok && *abort_flag == 0);  // no partial sums after a give-up
@@ -918,7 +944,7 @@ static size_t conv_wgrad_smem(int Cout) {
 constexpr size_t CONV_TILED_SMEM_MAX = 225 * 1024;
 static size_t pconv_smem_need(int tz, int KC, int CT, bool merge, int nsw) {
   const size_t halo = (size_t)10 * 18 * (tz + 2) * KC * 2;
-  return 2 * halo + (size_t)nsw * (merge ? 3 : 1) * CT * KC * 2 + 256;
+  return 2 * halo + (size_t)nsw * (merge ? 3 : 1) * CT * KC * 2 + 256 + 1024;  // + barriers, flags, bias
 }
 
 struct PConvCfg {
@@ -1047,10 +1073,13 @@ static int conv_wgrad_pipe(const void* dy, int cout, const void* x, int cin, flo
   const long long per = (nblocks + slices - 1) / slices;
   slices = (nblocks + per - 1) / per;
   if (npass > 65535) return report_error(LB_EINVAL, "conv wgrad: too many passes");
-  const size_t need = 2 * ((size_t)WCONV_HBYTES + (size_t)128 * o.CN * 2) + 64;
-  const size_t smem = conv_smem(need, o.TG * o.CN);
+  const size_t stage = (size_t)WCONV_HBYTES + (size_t)128 * o.CN * 2;
+  int nst = (int)((CONV_TILED_SMEM_MAX - 128) / stage);
+  nst = nst > 4 ? 4 : nst;
+  if (nst < 2) return report_error(LB_EINVAL, "conv wgrad: staging does not fit shared memory");
+  const size_t smem = conv_smem((size_t)nst * stage + 128, o.TG * o.CN);
   WConvArgs args{(const __nv_bfloat16*)(o.o2 ? dy : x), (const __nv_bfloat16*)(o.o2 ? x : dy), dw, o.CH, o.CP, cin,
-                 o.o2, o.CN, o.TG, o.ngroups, o.nchunks, (int)per, g, status};
+                 o.o2, o.CN, o.TG, o.ngroups, o.nchunks, (int)per, nst, g, status};
   cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     k_conv_wgrad_pipe<<<dim3((unsigned)slices, (unsigned)npass), PCONV_THREADS, smem, st>>>(args);

@@ -254,11 +254,12 @@ def end_to_end(args, L, sim, wl, nodes, world, barrier, maxall):
 
 
 def other_storages(args, L, make, stream, tile, nc_tile, world, nodes, maxall, peak):
-    """The reduced FP32 and FP16-deviation formats on the same workload, and the
-    regularised collision in the bench's own storage."""
+    """The reduced FP32 and FP16-deviation formats on the same workload, the
+    regularised collision in the bench's own storage, and the moment storage
+    of the regularised collision (ten coefficients + colour scalars per node)."""
     import torch
     extra = {}
-    for other, coll in (("reduced_f32", 0), ("reduced_f16", 0), (args.storage, 1)):
+    for other, coll in (("reduced_f32", 0), ("reduced_f16", 0), (args.storage, 1), ("moment_f32", 1)):
         if other == args.storage and coll == 0:
             continue
         s2 = make(other, collision=coll)

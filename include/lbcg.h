@@ -53,6 +53,14 @@ extern "C" {
 #define LB_STORAGE_REDUCED_F16 2
 /* Two population sets in FP64, FP64 arithmetic (parity instantiation). */
 #define LB_STORAGE_TWOSET_F64 3
+/* Moment storage (population-free, Sec. IV.C, Eqs. distnoneq, LBpostmom,
+ * eq:llb-pull): with the regularised collision every post-collision total
+ * population is w_i times a quadratic form in c_i, so a node stores the ten
+ * coefficients (alpha, beta, Gamma) of f*_i = w_i (alpha + beta.c_i +
+ * c_i.Gamma.c_i) plus the colour scalars (s, v) of REDUCED_F32; the pulling
+ * node evaluates them.  FP32, 56 B per node per lattice (112 B per node
+ * update).  Requires collision = 1 (LB_EINVAL otherwise). */
+#define LB_STORAGE_MOMENT_F32 4
 
 /* ---- field selection for lb_fields: bit k selects field k --------------- */
 #define LB_F_PHI (1u << 0)  /* order parameter (rhoA-rhoB)/(rhoA+rhoB), Eq. order_param */

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbcg.so")
-SOURCES = ["step_twoset_f32.cu", "step_reduced_f32.cu", "step_reduced_f16.cu", "step_twoset_f64.cu",
+SOURCES = ["step_twoset_f32.cu", "step_reduced_f32.cu", "step_reduced_f16.cu", "step_twoset_f64.cu", "step_moment_f32.cu",
            "step_kernels.cu", "aux_kernels.cu", "runtime.cu", "noalloc.cu",
            "conv_tc.cu", "nn_kernels.cu", "surrogate_rt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

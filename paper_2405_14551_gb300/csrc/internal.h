@@ -72,6 +72,9 @@ constexpr int NUM_TILES = 5;
 extern const Tile kTiles[NUM_TILES];
 
 size_t elem_bytes(int storage);
+// population-like arrays of a state: 2 x 27 (two sets), 27 (single set) or
+// the 10 quadratic-form coefficients of the moment storage
+int state_arrays(int storage);
 bool storage_is_twoset(int storage);
 bool storage_is_f64(int storage);
 

@@ -13,6 +13,7 @@
 namespace lbcg {
 
 constexpr int Q = 27;
+constexpr int MOMENT_COEFS = 10;  // alpha, beta (3), Gamma (6) of the moment storage
 constexpr int REST = 13;
 
 __host__ __device__ constexpr int cx(int i) { return i % 3 - 1; }

@@ -156,18 +156,20 @@ size_t real_bytes(int storage) { return storage_is_f64(storage) ? 8 : 4; }
 
 size_t state_bytes(const lb_handle* h) {
   const size_t N = (size_t)h->g.N;
-  if (storage_is_twoset(h->storage)) return 2 * (size_t)Q * N * elem_bytes(h->storage);
-  return (size_t)Q * N * elem_bytes(h->storage) + 4 * N * sizeof(float);
+  const size_t fbytes = (size_t)state_arrays(h->storage) * N * elem_bytes(h->storage);
+  if (storage_is_twoset(h->storage)) return fbytes;
+  return fbytes + 4 * N * sizeof(float);
 }
 
 bool alloc_state(lb_handle* h, StateBuf& s) {
   const size_t N = (size_t)h->g.N;
   if (storage_is_twoset(h->storage)) {
-    s.f = dev_alloc(h, 2 * (size_t)Q * N * elem_bytes(h->storage));
+    s.f = dev_alloc(h, (size_t)state_arrays(h->storage) * N * elem_bytes(h->storage));
     return s.f != nullptr;
   }
-  // one allocation: f* then the float4 colour scalars (256-byte aligned)
-  const size_t fb = ((size_t)Q * N * elem_bytes(h->storage) + 255) & ~(size_t)255;
+  // one allocation: f* (or the moment coefficients) then the float4 colour
+  // scalars (256-byte aligned)
+  const size_t fb = ((size_t)state_arrays(h->storage) * N * elem_bytes(h->storage) + 255) & ~(size_t)255;
   char* base = (char*)dev_alloc(h, fb + N * sizeof(float4));
   if (!base) return false;
   s.f = base;
@@ -212,8 +214,10 @@ int validate(const lb_grid* gr, const lb_params* p) {
   }
   if (!fin(p->g[0]) || !fin(p->g[1]) || !fin(p->g[2])) return set_err(LB_EINVAL, "g must be finite");
   if (p->g_mode < 0 || p->g_mode > 2) return set_err(LB_EINVAL, "g_mode must be 0, 1 or 2");
-  if (p->storage < 0 || p->storage > 3) return set_err(LB_EINVAL, "unknown storage format");
+  if (p->storage < 0 || p->storage > 4) return set_err(LB_EINVAL, "unknown storage format");
   if (p->collision < 0 || p->collision > 1) return set_err(LB_EINVAL, "collision must be 0 (BGK) or 1 (regularised)");
+  if (p->storage == LB_STORAGE_MOMENT_F32 && p->collision != 1)
+    return set_err(LB_EINVAL, "the moment storage holds the regularised collision only (collision = 1)");
   return LB_OK;
 }
 
@@ -738,7 +742,7 @@ int lb_save(lb_handle* h, const char* path) {
     if (storage_is_twoset(h->storage)) {
       e = cudaMemcpyAsync(buf.data(), s.f, sb, cudaMemcpyDeviceToHost, h->stream);
     } else {
-      const size_t fb = (size_t)Q * N * elem_bytes(h->storage);
+      const size_t fb = (size_t)state_arrays(h->storage) * N * elem_bytes(h->storage);
       e = cudaMemcpyAsync(buf.data(), s.f, fb, cudaMemcpyDeviceToHost, h->stream);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(buf.data() + fb, s.sv, N * sizeof(float4), cudaMemcpyDeviceToHost, h->stream);
@@ -789,7 +793,7 @@ int lb_load(lb_handle* h, const char* path) {
     if (storage_is_twoset(h->storage)) {
       e = cudaMemcpyAsync(s.f, buf.data(), sb, cudaMemcpyHostToDevice, h->stream);
     } else {
-      const size_t fb = (size_t)Q * N * elem_bytes(h->storage);
+      const size_t fb = (size_t)state_arrays(h->storage) * N * elem_bytes(h->storage);
       e = cudaMemcpyAsync(s.f, buf.data(), fb, cudaMemcpyHostToDevice, h->stream);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(s.sv, buf.data() + fb, N * sizeof(float4), cudaMemcpyHostToDevice, h->stream);
@@ -828,7 +832,7 @@ int lb_copy_state(lb_handle* dst, lb_handle* src) {
     if (storage_is_twoset(src->storage)) {
       e = cudaMemcpyAsync(b.f, a.f, state_bytes(src), cudaMemcpyDeviceToDevice, dst->stream);
     } else {
-      const size_t fb = (size_t)Q * N * elem_bytes(src->storage);
+      const size_t fb = (size_t)state_arrays(src->storage) * N * elem_bytes(src->storage);
       e = cudaMemcpyAsync(b.f, a.f, fb, cudaMemcpyDeviceToDevice, dst->stream);
       if (e == cudaSuccess) e = cudaMemcpyAsync(b.sv, a.sv, N * sizeof(float4), cudaMemcpyDeviceToDevice, dst->stream);
     }
@@ -1015,7 +1019,8 @@ int lb_batch_create(int32_t nruns, const lb_grid* grids, const lb_params* params
     if (rc) return rc;
     if (params[r].storage != params[0].storage) return set_err(LB_EINVAL, "all runs of a batch share one storage");
   }
-  if (params[0].storage == LB_STORAGE_TWOSET_F64) return set_err(LB_EINVAL, "batches support FP32/FP16 storage only");
+  if (params[0].storage == LB_STORAGE_TWOSET_F64 || params[0].storage == LB_STORAGE_MOMENT_F32)
+    return set_err(LB_EINVAL, "batches support the two-set and reduced FP32/FP16 storages only");
   lb_batch* b = new lb_batch();
   b->storage = params[0].storage;
   cudaError_t e = cudaStreamCreate(&b->own_stream);

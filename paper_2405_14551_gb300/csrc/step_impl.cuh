@@ -63,24 +63,39 @@ struct Store<0> {  // LB_STORAGE_TWOSET_F32
   using R = float;
   using E = float;
   static constexpr bool TWOSET = true;
+  static constexpr bool MOMENT = false;
 };
 template <>
 struct Store<1> {  // LB_STORAGE_REDUCED_F32
   using R = float;
   using E = float;
   static constexpr bool TWOSET = false;
+  static constexpr bool MOMENT = false;
 };
 template <>
 struct Store<2> {  // LB_STORAGE_REDUCED_F16
   using R = float;
   using E = __half;
   static constexpr bool TWOSET = false;
+  static constexpr bool MOMENT = false;
 };
 template <>
 struct Store<3> {  // LB_STORAGE_TWOSET_F64
   using R = double;
   using E = double;
   static constexpr bool TWOSET = true;
+  static constexpr bool MOMENT = false;
+};
+// LB_STORAGE_MOMENT_F32: the coefficients of f*_i = w_i (alpha + beta.c_i +
+// c_i.Gamma.c_i) in ten arrays [k][N]: alpha, beta_x, beta_y, beta_z,
+// Gamma_xx, Gamma_yy, Gamma_zz, 2 Gamma_xy, 2 Gamma_xz, 2 Gamma_yz; the colour
+// scalars as in the reduced storage.
+template <>
+struct Store<4> {
+  using R = float;
+  using E = float;
+  static constexpr bool TWOSET = false;
+  static constexpr bool MOMENT = true;
 };
 
 template <int ST>
@@ -97,6 +112,32 @@ __device__ __forceinline__ typename Store<ST>::E encode(typename Store<ST>::R v,
     return __float2half_rn((v - wgt<float>(i)) * F16_SCALE);
   } else {
     return v;
+  }
+}
+
+// Stored post-collision total population f*_dir of node src (single set
+// storages).  Reduced: the stored value.  Moment storage (Sec. IV.C, Eq.
+// eq:llb-pull): w_i (alpha + beta.c + c.Gamma.c) of the node's coefficients at
+// c = c_i, or at c = -c_i = c_opp(i) when bb (bounce-back from the node
+// itself, dir = opp(i)); only the coefficients that c_i touches are read.
+template <int ST, typename I>
+__device__ __forceinline__ typename Store<ST>::R load_fs(const typename Store<ST>::E* __restrict__ f, I N, I dir, I src,
+                                                         int i, bool bb) {
+  using R = typename Store<ST>::R;
+  if constexpr (Store<ST>::MOMENT) {
+    R lin = R(0), quad = R(0);
+    if (cx(i)) lin += R(cx(i)) * f[(I)1 * N + src];
+    if (cy(i)) lin += R(cy(i)) * f[(I)2 * N + src];
+    if (cz(i)) lin += R(cz(i)) * f[(I)3 * N + src];
+    if (cx(i)) quad += f[(I)4 * N + src];
+    if (cy(i)) quad += f[(I)5 * N + src];
+    if (cz(i)) quad += f[(I)6 * N + src];
+    if (cx(i) && cy(i)) quad += R(cx(i) * cy(i)) * f[(I)7 * N + src];
+    if (cx(i) && cz(i)) quad += R(cx(i) * cz(i)) * f[(I)8 * N + src];
+    if (cy(i) && cz(i)) quad += R(cy(i) * cz(i)) * f[(I)9 * N + src];
+    return wgt<R>(i) * (f[src] + quad + (bb ? -lin : lin));
+  } else {
+    return decode<ST>(f[dir * N + src], i);
   }
 }
 
@@ -181,7 +222,7 @@ __device__ __forceinline__ void pull_node(const View<ST>& S, const Geo& g, const
       }
     } else {
       // single set: f^A_dir(src) = s f*_dir + w c_dir.v/|c_dir| (recolouring, Eq. ome3_1)
-      const R fs = decode<ST>(S.f[(size_t)dir * N + src], i);
+      const R fs = load_fs<ST, size_t>(S.f, N, (size_t)dir, (size_t)src, i, bb);
       const float4 sv = S.sv[src];
       const R s = sv.x;
       const R cv = R(cx(i)) * R(sv.y) + R(cy(i)) * R(sv.z) + R(cz(i)) * R(sv.w);
@@ -345,7 +386,7 @@ __device__ __forceinline__ void pull_reduced_tile(const View<ST>& S, const Geo& 
       sl = bb ? cl : sl;
       dir = bb ? (I)opp(i) : dir;
     }
-    const R fs = decode<ST>(S.f[dir * N + (I)src], i);
+    const R fs = load_fs<ST, I>(S.f, N, dir, (I)src, i, bb);
     const float4 sv = svt[sl];
     const R s = sv.x;
     R cv = R(0);
@@ -501,9 +542,9 @@ __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const
       rA += va;
       rB += vb;
     } else if constexpr (TOTALS) {
-      f[i] = decode<ST>(S.f[dir * N + (I)src], i);
+      f[i] = load_fs<ST, I>(S.f, N, dir, (I)src, i, bb);
     } else {
-      const R fs = decode<ST>(S.f[dir * N + (I)src], i);
+      const R fs = load_fs<ST, I>(S.f, N, dir, (I)src, i, bb);
       const float4 sv = S.sv[src];
       const R s = sv.x;
       R cv = R(0);
@@ -921,6 +962,27 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       Pxz -= rho * u0 * u2;
       Pyz -= rho * u1 * u2;
       trP = Pxx + Pyy + Pzz;
+    }
+    if constexpr (Store<ST>::MOMENT) {
+      // f*_i = w_i (alpha + beta.c_i + c_i.Gamma.c_i): the equilibrium, the
+      // relaxed Hermite orders 1-2, the perturbation (B_i = w_i (|c_i|^2 - 2/3))
+      // and the Guo source below are each w_i times a quadratic form in c_i
+      // (Eqs. disteq, distnoneq, LBpostmom; the host admits this storage with
+      // the regularised collision only)
+      const R kP = keep * R(4.5), hg9 = R(0.5) * g9;
+      const R bF = g3 - R(1.5) * keep;  // beta = 3 rho u + (3 guo - 1.5 keep) F
+      O.f[(I)0 * N + (I)self] = r0 + gm3uF - R(1.5) * keep * trP + (R(2) / R(3)) * A2g;
+      O.f[(I)1 * N + (I)self] = r3 * u0 + bF * F0;
+      O.f[(I)2 * N + (I)self] = r3 * u1 + bF * F1;
+      O.f[(I)3 * N + (I)self] = r3 * u2 + bF * F2;
+      O.f[(I)4 * N + (I)self] = r45 * u0 * u0 + g9 * u0 * F0 + A2ig * gr[0] * gr[0] - A2g + kP * Pxx;
+      O.f[(I)5 * N + (I)self] = r45 * u1 * u1 + g9 * u1 * F1 + A2ig * gr[1] * gr[1] - A2g + kP * Pyy;
+      O.f[(I)6 * N + (I)self] = r45 * u2 * u2 + g9 * u2 * F2 + A2ig * gr[2] * gr[2] - A2g + kP * Pzz;
+      O.f[(I)7 * N + (I)self] = R(2) * (r45 * u0 * u1 + hg9 * (u0 * F1 + F0 * u1) + A2ig * gr[0] * gr[1] + kP * Pxy);
+      O.f[(I)8 * N + (I)self] = R(2) * (r45 * u0 * u2 + hg9 * (u0 * F2 + F0 * u2) + A2ig * gr[0] * gr[2] + kP * Pxz);
+      O.f[(I)9 * N + (I)self] = R(2) * (r45 * u1 * u2 + hg9 * (u1 * F2 + F1 * u2) + A2ig * gr[1] * gr[2] + kP * Pyz);
+      O.sv[self] = make_float4(sA, segamp * gr[0], segamp * gr[1], segamp * gr[2]);
+      continue;
     }
     {  // rest direction
       const R W = wgt<R>(REST);

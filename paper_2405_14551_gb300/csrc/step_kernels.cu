@@ -1,5 +1,6 @@
 // Storage-format dispatch of the step launchers.
 #include "internal.h"
+#include "lattice.cuh"
 
 namespace lbcg {
 
@@ -29,6 +30,7 @@ cudaError_t launch_phi(int storage, const Geo& g, const StateBuf& in, void* phi,
     case 1: return launch_phi_t<1>(g, in, phi, st);
     case 2: return launch_phi_t<2>(g, in, phi, st);
     case 3: return launch_phi_t<3>(g, in, phi, st);
+    case 4: return launch_phi_t<4>(g, in, phi, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -40,6 +42,7 @@ cudaError_t launch_nc(int storage, int variant, const Geo& g, const Phys& p, con
     case 1: return launch_nc_t<1>(variant, g, p, phi, hnc, st);
     case 2: return launch_nc_t<2>(variant, g, p, phi, hnc, st);
     case 3: return launch_nc_t<3>(variant, g, p, phi, hnc, st);
+    case 4: return launch_nc_t<4>(variant, g, p, phi, hnc, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -52,6 +55,7 @@ cudaError_t launch_step(int storage, int loader, bool write_state, bool write_fi
     case 1: return launch_step_s<1>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
     case 2: return launch_step_s<2>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
     case 3: return launch_step_s<3>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
+    case 4: return launch_step_s<4>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -64,6 +68,7 @@ cudaError_t launch_export(int storage, int loader, const Geo& g, const Phys& p, 
     case 1: return launch_export_t<1>(loader, g, p, in, init, x0, y0, z0, bx, by, bz, outA, outB, st);
     case 2: return launch_export_t<2>(loader, g, p, in, init, x0, y0, z0, bx, by, bz, outA, outB, st);
     case 3: return launch_export_t<3>(loader, g, p, in, init, x0, y0, z0, bx, by, bz, outA, outB, st);
+    case 4: return launch_export_t<4>(loader, g, p, in, init, x0, y0, z0, bx, by, bz, outA, outB, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -91,6 +96,7 @@ int sm_count_host() {
 }
 
 size_t elem_bytes(int storage) { return storage == 3 ? 8 : (storage == 2 ? 2 : 4); }
+int state_arrays(int storage) { return storage == 4 ? MOMENT_COEFS : (storage == 0 || storage == 3 ? 2 * Q : Q); }
 bool storage_is_twoset(int storage) { return storage == 0 || storage == 3; }
 bool storage_is_f64(int storage) { return storage == 3; }
 

@@ -1,0 +1,14 @@
+// Step kernels instantiated for storage 4 (moment storage of the regularised
+// collision, FP32).  Batches do not take this storage.
+#include "step_launch.cuh"
+
+namespace lbcg {
+
+template cudaError_t launch_phi_t<4>(const Geo&, const StateBuf&, void*, cudaStream_t);
+template cudaError_t launch_nc_t<4>(int, const Geo&, const Phys&, const void*, unsigned char*, cudaStream_t);
+template cudaError_t launch_step_s<4>(int, bool, bool, int, const Geo&, const Phys&, const StateBuf&, const InitBuf&,
+                                         const void*, const unsigned char*, StateBuf, void*, unsigned*, cudaStream_t);
+template cudaError_t launch_export_t<4>(int, const Geo&, const Phys&, const StateBuf&, const InitBuf&, int, int, int,
+                                          int, int, int, double*, double*, cudaStream_t);
+
+}  // namespace lbcg

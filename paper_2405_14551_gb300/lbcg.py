@@ -17,12 +17,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbcg.so")
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE, LB_EIO = 0, -1, -2, -3, -4, -5, -6, -7
-STORAGE = {"twoset_f32": 0, "reduced_f32": 1, "reduced_f16": 2, "twoset_f64": 3}
+STORAGE = {"twoset_f32": 0, "reduced_f32": 1, "reduced_f16": 2, "twoset_f64": 3, "moment_f32": 4}
 FIELD_NAMES = ("phi", "rho", "ux", "uy", "uz", "rhoA", "rhoB", "Frx", "Fry", "Frz", "h", "gx", "gy", "gz")
 FIELD_BIT = {n: 1 << k for k, n in enumerate(FIELD_NAMES)}
 ALL_FIELDS = (1 << len(FIELD_NAMES)) - 1
 # algorithmic bytes per node update (one read + one write of the stored state)
-BYTES_PER_NODE = {0: 2 * 27 * 4 * 2, 1: (27 + 4) * 4 * 2, 2: (27 * 2 + 4 * 4) * 2, 3: 2 * 27 * 8 * 2}
+BYTES_PER_NODE = {0: 2 * 27 * 4 * 2, 1: (27 + 4) * 4 * 2, 2: (27 * 2 + 4 * 4) * 2, 3: 2 * 27 * 8 * 2,
+                  4: (10 + 4) * 4 * 2}
 
 
 class LBError(RuntimeError):

@@ -57,6 +57,7 @@ def test_validation_without_gpu(lib):
         (L.make_grid(4, 4, 4), L.make_params(A_h=0.1, h_min=4.0, h_max=3.0)),
         (L.make_grid(4, 4, 4), L.make_params(g_mode=3)),
         (L.make_grid(4, 4, 4), L.make_params(storage=7)),
+        (L.make_grid(4, 4, 4), L.make_params(storage="moment_f32")),  # moment storage needs collision = 1
         (L.make_grid(4, 4, 4), L.make_params(g=(float("nan"), 0.0, 0.0))),
         (L.make_grid(1 << 11, 1 << 11, 1 << 10), L.make_params()),
     ]

@@ -206,13 +206,13 @@ def test_mass_conservation_fp32_long():
 
 def test_checkpoint_resume_bitwise(tmp_path):
     wl = W.droplet_pair(32, 32, 48, R=7.0, sep=17.0)
-    for storage in ("twoset_f32", "reduced_f16"):
-        a = make_gpu(wl, storage=storage)
+    for storage, coll in (("twoset_f32", 0), ("reduced_f16", 0), ("moment_f32", 1)):
+        a = make_gpu(wl, storage=storage, collision=coll)
         a.step(100)
         path = str(tmp_path / f"ck_{storage}.bin")
         a.save(path)
         a.step(100)
-        b = make_gpu(wl, storage=storage)
+        b = make_gpu(wl, storage=storage, collision=coll)
         b.load(path)
         assert b.t == 100
         b.step(100)
@@ -245,13 +245,13 @@ def test_copy_state_bitwise():
     the source."""
     import paper_2405_14551_gb300.lbcg as L
     wl = W.droplet_pair(32, 32, 48, R=7.0, sep=17.0)
-    for storage in ("twoset_f32", "reduced_f16"):
-        a = make_gpu(wl, storage=storage)
-        c = make_gpu(wl, storage=storage)
+    for storage, coll in (("twoset_f32", 0), ("reduced_f16", 0), ("moment_f32", 1)):
+        a = make_gpu(wl, storage=storage, collision=coll)
+        c = make_gpu(wl, storage=storage, collision=coll)
         c.step(2)
         L.lb_copy_state(c.h, a.h)  # a has not stepped: the initial fields
         a.step(23)
-        b = make_gpu(wl, storage=storage)
+        b = make_gpu(wl, storage=storage, collision=coll)
         L.lb_copy_state(b.h, a.h)
         assert b.t == 23
         a.step(9)
@@ -288,7 +288,7 @@ def test_regularised_reconstruction_matches_oracle():
 
 
 @pytest.mark.parametrize("storage,tol", [("twoset_f32", 1e-5), ("reduced_f32", 1e-5), ("reduced_f16", None),
-                                         ("twoset_f64", 1e-11)])
+                                         ("twoset_f64", 1e-11), ("moment_f32", 1e-5)])
 def test_regularised_collision_matches_oracle(storage, tol):
     """The regularised collision (collision = 1) against the oracle's: small
     droplet at tau 0.8 (where it differs from BGK) with a channel wall pair,
@@ -310,3 +310,36 @@ def test_regularised_collision_matches_oracle(storage, tol):
     b = make_oracle(wl)  # BGK differs at tau != 1: the flag reaches the collision
     b.step(120)
     assert field_errors(b.fields(), o.fields(), ("ux",))["ux"] > 1e-9
+
+
+def test_moment_storage_matches_reduced_and_oracle():
+    """Moment storage (ten quadratic-form coefficients of f*_i per node plus
+    the colour scalars) of the regularised collision: periodic droplet pair
+    2.8 nodes apart with the mirror-opposite force and near contact.  After 5
+    steps its fields match the oracle's within FP32 round-off with an
+    identical near-contact map (later, FP32 and FP64 take some near-contact
+    roundings differently, as for every FP32 storage); over 80 steps they
+    agree with the reduced single-set storage, which runs the same arithmetic
+    on 27 stored populations, and so do the populations it exports (rebuilt
+    from the neighbours' coefficients)."""
+    wl = W.Workload("mom", (24, 20, 36), 0, dict(W.BASE, tau_a=0.75, tau_b=1.2, A_h=0.1, g=(0.0, 0.0, 1e-5),
+                                                   g_mode=2), 80,
+                    centres=np.array([[11.6, 9.7, 11.3], [12.3, 10.4, 24.2]]), radii=np.array([5.2, 4.9]))
+    m = make_gpu(wl, storage="moment_f32", collision=1)
+    r = make_gpu(wl, storage="reduced_f32", collision=1)
+    o = make_oracle(wl, collision=1)
+    for sim in (m, r, o):
+        sim.step(5)
+    fm, fo = m.fields(f64=True), o.fields()
+    e = field_errors(fm, fo, CMP_FIELDS)
+    assert max(e.values()) <= 1e-5, e
+    np.testing.assert_array_equal(fm["h"], fo["h"])
+    assert fm["h"].max() > 0  # the near-contact force is active
+    for sim in (m, r):
+        sim.step(75)
+    fm, fr = m.fields(f64=True), r.fields(f64=True)
+    assert max(field_errors(fm, fr, CMP_FIELDS).values()) <= 2e-6
+    np.testing.assert_array_equal(fm["h"], fr["h"])
+    box = (3, 2, 5, 8, 7, 9)
+    (ma, mb), (ra, rb) = m.populations(box), r.populations(box)
+    assert np.abs(ma - ra).max() <= 2e-6 and np.abs(mb - rb).max() <= 2e-6

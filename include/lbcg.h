@@ -58,7 +58,9 @@ extern "C" {
  * population is w_i times a quadratic form in c_i, so a node stores the ten
  * coefficients (alpha, beta, Gamma) of f*_i = w_i (alpha + beta.c_i +
  * c_i.Gamma.c_i) plus the colour scalars (s, v) of REDUCED_F32; the pulling
- * node evaluates them.  FP32, 56 B per node per lattice (112 B per node
+ * node evaluates them.  FP32 records (alpha, beta) [N] float4, (Gamma_xx,
+ * Gamma_yy, Gamma_zz, 2 Gamma_xy) [N] float4, (2 Gamma_xz, 2 Gamma_yz) [N]
+ * float2, then (s, v) [N] float4: 56 B per node per lattice (112 B per node
  * update).  Requires collision = 1 (LB_EINVAL otherwise). */
 #define LB_STORAGE_MOMENT_F32 4
 

@@ -87,9 +87,11 @@ struct Store<3> {  // LB_STORAGE_TWOSET_F64
   static constexpr bool MOMENT = false;
 };
 // LB_STORAGE_MOMENT_F32: the coefficients of f*_i = w_i (alpha + beta.c_i +
-// c_i.Gamma.c_i) in ten arrays [k][N]: alpha, beta_x, beta_y, beta_z,
-// Gamma_xx, Gamma_yy, Gamma_zz, 2 Gamma_xy, 2 Gamma_xz, 2 Gamma_yz; the colour
-// scalars as in the reduced storage.
+// c_i.Gamma.c_i) in three arrays of 16- and 8-byte records, so that a
+// direction reads at most three vectors: qa[N] = (alpha, beta_x, beta_y,
+// beta_z), qb[N] = (Gamma_xx, Gamma_yy, Gamma_zz, 2 Gamma_xy) from float 4N
+// on, qc[N] = (2 Gamma_xz, 2 Gamma_yz) from float 8N on; the colour scalars
+// as in the reduced storage.
 template <>
 struct Store<4> {
   using R = float;
@@ -125,17 +127,24 @@ __device__ __forceinline__ typename Store<ST>::R load_fs(const typename Store<ST
                                                          int i, bool bb) {
   using R = typename Store<ST>::R;
   if constexpr (Store<ST>::MOMENT) {
+    const float4 qa = reinterpret_cast<const float4*>(f)[src];
     R lin = R(0), quad = R(0);
-    if (cx(i)) lin += R(cx(i)) * f[(I)1 * N + src];
-    if (cy(i)) lin += R(cy(i)) * f[(I)2 * N + src];
-    if (cz(i)) lin += R(cz(i)) * f[(I)3 * N + src];
-    if (cx(i)) quad += f[(I)4 * N + src];
-    if (cy(i)) quad += f[(I)5 * N + src];
-    if (cz(i)) quad += f[(I)6 * N + src];
-    if (cx(i) && cy(i)) quad += R(cx(i) * cy(i)) * f[(I)7 * N + src];
-    if (cx(i) && cz(i)) quad += R(cx(i) * cz(i)) * f[(I)8 * N + src];
-    if (cy(i) && cz(i)) quad += R(cy(i) * cz(i)) * f[(I)9 * N + src];
-    return wgt<R>(i) * (f[src] + quad + (bb ? -lin : lin));
+    if (cx(i)) lin += R(cx(i)) * qa.y;
+    if (cy(i)) lin += R(cy(i)) * qa.z;
+    if (cz(i)) lin += R(cz(i)) * qa.w;
+    if (cx(i) || cy(i) || cz(i)) {
+      const float4 qb = reinterpret_cast<const float4*>(f + (I)4 * N)[src];
+      if (cx(i)) quad += qb.x;
+      if (cy(i)) quad += qb.y;
+      if (cz(i)) quad += qb.z;
+      if (cx(i) && cy(i)) quad += R(cx(i) * cy(i)) * qb.w;
+    }
+    if ((cx(i) && cz(i)) || (cy(i) && cz(i))) {
+      const float2 qc = reinterpret_cast<const float2*>(f + (I)8 * N)[src];
+      if (cx(i) && cz(i)) quad += R(cx(i) * cz(i)) * qc.x;
+      if (cy(i) && cz(i)) quad += R(cy(i) * cz(i)) * qc.y;
+    }
+    return wgt<R>(i) * (qa.x + quad + (bb ? -lin : lin));
   } else {
     return decode<ST>(f[dir * N + src], i);
   }
@@ -971,16 +980,17 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       // the regularised collision only)
       const R kP = keep * R(4.5), hg9 = R(0.5) * g9;
       const R bF = g3 - R(1.5) * keep;  // beta = 3 rho u + (3 guo - 1.5 keep) F
-      O.f[(I)0 * N + (I)self] = r0 + gm3uF - R(1.5) * keep * trP + (R(2) / R(3)) * A2g;
-      O.f[(I)1 * N + (I)self] = r3 * u0 + bF * F0;
-      O.f[(I)2 * N + (I)self] = r3 * u1 + bF * F1;
-      O.f[(I)3 * N + (I)self] = r3 * u2 + bF * F2;
-      O.f[(I)4 * N + (I)self] = r45 * u0 * u0 + g9 * u0 * F0 + A2ig * gr[0] * gr[0] - A2g + kP * Pxx;
-      O.f[(I)5 * N + (I)self] = r45 * u1 * u1 + g9 * u1 * F1 + A2ig * gr[1] * gr[1] - A2g + kP * Pyy;
-      O.f[(I)6 * N + (I)self] = r45 * u2 * u2 + g9 * u2 * F2 + A2ig * gr[2] * gr[2] - A2g + kP * Pzz;
-      O.f[(I)7 * N + (I)self] = R(2) * (r45 * u0 * u1 + hg9 * (u0 * F1 + F0 * u1) + A2ig * gr[0] * gr[1] + kP * Pxy);
-      O.f[(I)8 * N + (I)self] = R(2) * (r45 * u0 * u2 + hg9 * (u0 * F2 + F0 * u2) + A2ig * gr[0] * gr[2] + kP * Pxz);
-      O.f[(I)9 * N + (I)self] = R(2) * (r45 * u1 * u2 + hg9 * (u1 * F2 + F1 * u2) + A2ig * gr[1] * gr[2] + kP * Pyz);
+      reinterpret_cast<float4*>(O.f)[self] =
+          make_float4(r0 + gm3uF - R(1.5) * keep * trP + (R(2) / R(3)) * A2g, r3 * u0 + bF * F0, r3 * u1 + bF * F1,
+                      r3 * u2 + bF * F2);
+      reinterpret_cast<float4*>(O.f + (I)4 * N)[self] =
+          make_float4(r45 * u0 * u0 + g9 * u0 * F0 + A2ig * gr[0] * gr[0] - A2g + kP * Pxx,
+                      r45 * u1 * u1 + g9 * u1 * F1 + A2ig * gr[1] * gr[1] - A2g + kP * Pyy,
+                      r45 * u2 * u2 + g9 * u2 * F2 + A2ig * gr[2] * gr[2] - A2g + kP * Pzz,
+                      R(2) * (r45 * u0 * u1 + hg9 * (u0 * F1 + F0 * u1) + A2ig * gr[0] * gr[1] + kP * Pxy));
+      reinterpret_cast<float2*>(O.f + (I)8 * N)[self] =
+          make_float2(R(2) * (r45 * u0 * u2 + hg9 * (u0 * F2 + F0 * u2) + A2ig * gr[0] * gr[2] + kP * Pxz),
+                      R(2) * (r45 * u1 * u2 + hg9 * (u1 * F2 + F1 * u2) + A2ig * gr[1] * gr[2] + kP * Pyz));
       O.sv[self] = make_float4(sA, segamp * gr[0], segamp * gr[1], segamp * gr[2]);
       continue;
     }

@@ -217,14 +217,89 @@ cudaError_t launch_laplace(int storage, const Geo& g, const void* fields, double
 // droplet count: union-find over fluid nodes with phi > 0, 6-connected,
 // periodic on open axes.  Roots hook the larger label under the smaller with
 // atomicCAS; every loop is bounded and reports through the status word.
+// A first pass joins the links inside 32 x 8 x 8 tiles in shared memory and
+// writes, per node, the global index of its tile-local root (the smallest
+// index of its tile-local component); the global pass then joins only the
+// links that cross tile faces.
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void k_cc_init(Geo g, const R* __restrict__ phi, int* __restrict__ L) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x)
-    L[i] = (!node_solid(g, i) && phi[i] > R(0)) ? (int)i : -1;
+constexpr int CC_TX = 32, CC_TY = 8, CC_TZ = 8, CC_TN = CC_TX * CC_TY * CC_TZ;
+
+__device__ __forceinline__ int cc_find_local(int* L, int i) {
+  for (int it = 0; it < CC_TN; ++it) {
+    const int p = L[i];
+    if (p == i) return i;
+    const int gp = L[p];
+    if (gp != p) L[i] = gp;  // path halving; parents only move to ancestors
+    i = p;
+  }
+  return -1;
 }
 
-// Root of i.  Every parent label is smaller than its child's (init: L[i] = i;
+template <typename R>
+__global__ void __launch_bounds__(256) k_cc_local(Geo g, const R* __restrict__ phi, int* __restrict__ Lg,
+                                                  unsigned* status) {
+  __shared__ int L[CC_TN];
+  const int x0 = blockIdx.x * CC_TX, y0 = blockIdx.y * CC_TY, z0 = blockIdx.z * CC_TZ;
+  for (int k = threadIdx.x; k < CC_TN; k += blockDim.x) {
+    const int x = x0 + k % CC_TX, y = y0 + (k / CC_TX) % CC_TY, z = z0 + k / (CC_TX * CC_TY);
+    bool on = false;
+    if (x < g.nx && y < g.ny && z < g.nz) {
+      const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+      on = !node_solid(g, i) && phi[i] > R(0);
+    }
+    L[k] = on ? k : -1;
+  }
+  __syncthreads();
+  bool ok = true;
+  for (int k = threadIdx.x; k < CC_TN; k += blockDim.x) {
+    if (L[k] < 0) continue;
+    const int lx = k % CC_TX, ly = (k / CC_TX) % CC_TY, lz = k / (CC_TX * CC_TY);
+    const int nb[3] = {lx + 1 < CC_TX ? k + 1 : -1, ly + 1 < CC_TY ? k + CC_TX : -1,
+                       lz + 1 < CC_TZ ? k + CC_TX * CC_TY : -1};
+    for (int a = 0; a < 3; ++a) {
+      if (nb[a] < 0 || L[nb[a]] < 0) continue;
+      int ra = k, rb = nb[a];
+      bool done = false;
+      for (int it = 0; it < CC_TN && !done; ++it) {
+        ra = cc_find_local(L, ra);
+        rb = cc_find_local(L, rb);
+        if (ra < 0 || rb < 0) break;
+        if (ra == rb) {
+          done = true;
+          break;
+        }
+        if (ra < rb) {
+          const int t = ra;
+          ra = rb;
+          rb = t;
+        }
+        const int old = atomicCAS(&L[ra], ra, rb);
+        if (old == ra) done = true;
+        else ra = old;
+      }
+      ok = ok && done;
+    }
+  }
+  if (!ok) atomicOr(status, 2u);
+  __syncthreads();
+  for (int k = threadIdx.x; k < CC_TN; k += blockDim.x) {
+    const int x = x0 + k % CC_TX, y = y0 + (k / CC_TX) % CC_TY, z = z0 + k / (CC_TX * CC_TY);
+    if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
+    const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+    int r = L[k] < 0 ? -1 : cc_find_local(L, k);
+    if (L[k] >= 0 && r < 0) {
+      atomicOr(status, 2u);
+      r = k;
+    }
+    Lg[i] = r < 0 ? -1
+                  : (int)((long long)(x0 + r % CC_TX) +
+                          (long long)g.nx * ((long long)(y0 + (r / CC_TX) % CC_TY) +
+                                             (long long)g.ny * (z0 + r / (CC_TX * CC_TY))));
+  }
+}
+
+// Root of i.  Every parent label is smaller than its child's (the tile pass
+// points every node at the smallest index of its tile component;
 // a root is only ever hooked under a smaller root), so each node met on the
 // way may be pointed at its grandparent (path halving, as in intermediate
 // pointer jumping): the writes only shorten paths and keep the forest valid
@@ -255,6 +330,8 @@ __global__ void k_cc_union(Geo g, int* __restrict__ Lp, unsigned* status) {
       int v[3] = {x, y, z};
       const int nn[3] = {g.nx, g.ny, g.nz};
       const int wall[3] = {g.wx, g.wy, g.wz};
+      const int tile[3] = {CC_TX, CC_TY, CC_TZ};
+      if ((v[a] + 1) % tile[a] != 0 && v[a] + 1 < nn[a]) continue;  // joined by the tile pass
       v[a] += 1;
       if (v[a] >= nn[a]) {
         if (wall[a]) continue;
@@ -298,10 +375,11 @@ cudaError_t launch_cc(int storage, const Geo& g, const void* fields, int* labels
                       cudaStream_t st) {
   const long long need = (g.N + 255) / 256;
   const int blocks = (int)(need < 8192 ? need : 8192);
+  const dim3 tiles((g.nx + CC_TX - 1) / CC_TX, (g.ny + CC_TY - 1) / CC_TY, (g.nz + CC_TZ - 1) / CC_TZ);
   if (storage_is_f64(storage))
-    k_cc_init<double><<<blocks, 256, 0, st>>>(g, reinterpret_cast<const double*>(fields), labels);
+    k_cc_local<double><<<tiles, 256, 0, st>>>(g, reinterpret_cast<const double*>(fields), labels, status);
   else
-    k_cc_init<float><<<blocks, 256, 0, st>>>(g, reinterpret_cast<const float*>(fields), labels);
+    k_cc_local<float><<<tiles, 256, 0, st>>>(g, reinterpret_cast<const float*>(fields), labels, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_cc_union<<<blocks, 256, 0, st>>>(g, labels, status);

@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--storage", default="twoset_f32")
+    ap.add_argument("--collision", type=int, default=None,
+                    help="0 BGK, 1 regularised (default: 1 for the moment storage, else 0)")
     ap.add_argument("--no-extra", action="store_true", help="skip the other storage formats")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep measurement")
@@ -262,6 +264,8 @@ def other_storages(args, L, make, stream, tile, nc_tile, world, nodes, maxall, p
     for other, coll in (("reduced_f32", 0), ("reduced_f16", 0), (args.storage, 1), ("moment_f32", 1)):
         if other == args.storage and coll == 0:
             continue
+        if other == "moment_f32" and args.storage == "moment_f32" and coll == 1 and f"{other}_regularised" in extra:
+            continue
         s2 = make(other, collision=coll)
         L.lb_set_nc_tile(s2.h, nc_tile)
         s2.step(3)
@@ -472,7 +476,8 @@ def main():
 
     barrier, maxall = ranks.barrier, ranks.maxall
 
-    sim = make(storage)
+    collision = args.collision if args.collision is not None else (1 if storage == "moment_f32" else 0)
+    sim = make(storage, collision)
     # autotune the tiles of the fused kernel and of the near-contact scan
     # (independent kernels): time every shape, keep the fastest of each
     tile_ms, nc_ms = [], []
@@ -543,7 +548,8 @@ def main():
             "vs_baseline": None,
             "dtype": "f64" if storage == "twoset_f64" else "f32",
             "data": "synthetic",
-            "config": {"workload": wl.name, "storage": storage, "walls": "y", "seed": SEED,
+            "config": {"workload": wl.name, "storage": storage, "collision": "regularised" if collision else "bgk",
+                       "walls": "y", "seed": SEED,
                        "dispersed_fraction": round(wl.info.get("phi_d", 0.0), 4), "droplets": wl.info.get("droplets"),
                        "A_h": wl.params["A_h"], "h_min": wl.params["h_min"], "tile": best_tile,
                        "tile_ms": [round(v, 4) for v in tile_ms], "nc_tile": best_nc,

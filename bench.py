@@ -335,14 +335,16 @@ def batch_extra(args, L, W, stream):
             "speedup": round(ms_seq / mb, 3)}
 
 
-def surrogate_extra(L, stream, ntraj=24, iters=4000, cycles=20, spinup=2000):
+def surrogate_extra(L, stream, ntraj=24, iters=4000, cycles=100, spinup=2000):
     """The learned surrogate on the 128x128x256 dense emulsion: trajectories
     from the LB itself (seeded emulsions, 2000 spin-up steps, snapshots 50
     steps apart: the slow, late-time regime of a long run), a training run of
     the BF16 U-Net on the library's tcgen05 kernels, its per-jump phi error on
     held-out pairs against the persistence forecast, and the controller (50 LB
-    steps + one jump, plain-LB judge until a jump passes and then every 4th,
-    phi tolerance 1e-2) timed against plain LB from the same state."""
+    steps + one jump, plain-LB judge until a jump passes, then every 4th, the
+    interval doubling up to every 16th after passes with margin; phi
+    tolerance 1e-2) timed against plain LB from the same state over 10000
+    steps (100 cycles), with the final phi difference and droplet counts."""
     import time
     import torch
     from paper_2405_14551_gb300 import surrogate as S

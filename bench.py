@@ -166,7 +166,7 @@ class ClockSampler:
 # 128x128x256, tile 2, divided by its nodes; the kernel's traffic grows with the
 # node count) together with a digest of the kernel sources it was taken on: a
 # changed kernel reports null until it is captured again.
-K_STEP_TRAFFIC = {"twoset_f32": (420.16, "c72325126429cbdb")}
+K_STEP_TRAFFIC = {"twoset_f32": (419.85, "b277b7cc4e35238f")}
 
 
 def kernel_digest():

@@ -7,11 +7,17 @@
 // The weight gradient is the GEMM
 //   dW^T[M = taps x Cin][N = Cout] = sum_v X[v + off_t][ci] dY[v][co]
 // with K = voxels; its operands are MN-major (channels contiguous).
-// One CTA of 128 threads owns a 128-row accumulator in tensor memory (one
-// lane per row, FP32), operands are staged through two shared-memory buffers
-// in the no-swizzle core-matrix layout, one thread issues the UMMAs and
-// commits them to an mbarrier per buffer.  Every wait is bounded; a wait that
-// gives up sets bit 4 of the status word.
+// Grids with nx % 8 == 0 and ny % 16 == 0 (every level of the network) take
+// the spatially tiled, pipelined kernels k_conv_fwd_pipe and
+// k_conv_wgrad_pipe: persistent CTAs with copy, UMMA-issue and epilogue
+// warps handing shared-memory buffers and tensor-memory accumulators over
+// through mbarriers, the input block of a tile staged once per channel
+// chunk.  Other grids and the 1x1x1 head take k_conv_fwd / k_conv_wgrad: one
+// CTA of 128 threads owns a 128-row accumulator in tensor memory (one lane
+// per row, FP32), operands are gathered through two shared-memory buffers in
+// the no-swizzle core-matrix layout, one thread issues the UMMAs and commits
+// them to an mbarrier per buffer.  Every wait is bounded; a wait that gives
+// up sets bit 4 of the status word.
 #include <cuda_bf16.h>
 
 #include <string>
@@ -213,6 +219,9 @@ __global__ void __launch_bounds__(128, 1)
 // that every plane is initialised before it is accumulated.
 //
 // Without MERGE a step is one tap: TZ UMMAs of CT columns.
+// Decoder layers read their input in place: channels [0, cs) from X, the
+// rest from X2 at the parent voxel (nearest x2 upsampling), a chunk lying
+// wholly in one source, so the concatenated tensor is never written.
 // Accumulators are double buffered (2 TZ CT <= 512 columns), so the epilogue
 // of one work item overlaps the UMMAs of the next.  Every wait is bounded; a
 // wait that gives up sets bit 4 of the status word and the CTA winds down.
@@ -586,7 +595,10 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
 // A pass is (M block j, group of (dx, dy) taps, slice of P channels); every
 // CTA accumulates its pass over its run of blocks in tensor memory and adds
 // the result to dW with FP32 atomics once.  Warp roles and bounded waits as
-// in the forward kernel.
+// in the forward kernel; up to four staged blocks are in flight, and a copy
+// thread signals a block nst - 2 blocks after issuing it (nst = staged
+// slots: two with four, one with three, at once with two), so the slot it
+// refills next was handed over earlier.
 constexpr int WCONV_HPLANE = 180 * 16;           // bytes of one staged halo plane
 constexpr int WCONV_HBYTES = 16 * WCONV_HPLANE;  // the 16 planes of an M block
 

@@ -101,6 +101,37 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def fp32_alu_peak():
+    """FP32 arithmetic roof of this GPU, measured: cuBLAS SGEMM 8192^3 with
+    TF32 disabled (FMA pipes only), best of 5 back to back, CUDA events.  The
+    FP16-deviation storage moves so few bytes that its fused kernel is judged
+    against this roof as well as against the copy bandwidth."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        g = torch.Generator(device="cuda").manual_seed(0)
+        a = torch.randn(n, n, device="cuda", generator=g)
+        b = torch.randn(n, n, device="cuda", generator=g)
+        for _ in range(2):
+            torch.matmul(a, b)
+        best = None
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b
+        torch.cuda.empty_cache()
+        return round(2.0 * n ** 3 / (best / 1e3) / 1e12, 1)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -530,6 +561,9 @@ def main():
     del sim
     torch.cuda.empty_cache()
     extra = {} if args.no_extra else other_storages(args, L, make, stream, best_tile, best_nc, world, nodes, maxall, peak)
+    if not args.no_extra:
+        extra["fp32_alu"] = {"sgemm_tflops": fp32_alu_peak(),
+                             "how": "cuBLAS SGEMM 8192^3 with TF32 off, best of 5 (FMA pipes only)"}
     if not args.no_batch and not args.shape:
         extra["batch"] = batch_extra(args, L, W, stream)
     if not args.no_surrogate and not args.shape and world == 1:

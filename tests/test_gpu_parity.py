@@ -129,6 +129,25 @@ def test_degenerate_grids(shape, walls):
     assert max(e.values()) <= 1e-12, e
 
 
+@pytest.mark.parametrize("shape,walls", [((1, 1, 1), 0), ((3, 3, 3), 0b111), ((5, 3, 4), 0b010), ((2, 7, 3), 0b100),
+                                         ((33, 17, 9), 0b010)])
+def test_moment_storage_degenerate_and_ragged_grids(shape, walls):
+    """The moment storage on grids smaller than a tile, walled on every side,
+    and ragged against every tile edge: regularised collision against the
+    oracle's within FP32 round-off after 10 steps (bounce-back evaluates the
+    node's own coefficients at -c_i)."""
+    wl = W.Workload("tiny", shape, walls, dict(W.BASE, tau_a=0.8, tau_b=1.1, A_h=0.1, g=(1e-4, 2e-4, -1e-4),
+                                                 g_mode=1), 10,
+                    centres=np.array([[0.5 * shape[0] + 0.3, 0.5 * shape[1] - 0.2, 0.5 * shape[2] + 0.1]]),
+                    radii=np.array([max(1.2, 0.3 * min(shape))]))
+    o = make_oracle(wl, collision=1)
+    s = make_gpu(wl, storage="moment_f32", collision=1)
+    o.step(10)
+    s.step(10)
+    e = field_errors(s.fields(f64=True), o.fields())
+    assert max(e.values()) <= 1e-5, e
+
+
 def test_tile_shapes_give_identical_results():
     """Every tile of the fused kernel and of the near-contact scan (paired
     differently) gives bitwise the same fields."""

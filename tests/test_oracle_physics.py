@@ -121,3 +121,44 @@ def test_pair_mirror_symmetry_short_horizon():
     assert np.abs(f["uz"] + mz(f["uz"])).max() < 1e-12
     np.testing.assert_array_equal(f["h"], mz(f["h"]))
     assert (f["h"] > 0).sum() > 0
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.3])
+def test_reconstruction_matches_chapman_enskog_in_poiseuille(tau):
+    """Reading C17 (regularised reconstruction, Pi^neq = -rho cs2 tau_bar
+    (grad u + grad u^T) from the stencil gradient): in a steady forced
+    Poiseuille channel the populations rebuilt from (phi, rho, u) carry the
+    same non-equilibrium momentum flux as the populations the LB itself
+    relaxed to (the Chapman-Enskog first-order part; the parabolic profile
+    makes the central difference exact), and the same density and momentum."""
+    ny, g = 34, 2e-6
+    kw = dict(shape=(4, ny, 4), walls=0b010, tau_a=tau, tau_b=tau, g=(0, 0, g), g_mode=1)
+    s = _sim(**kw)
+    s.init_fields(-np.ones((4, ny, 4)))
+    s.step(30000 if tau > 1 else 20000)
+    f = s.fields()
+    fa, fb = s.get_populations()
+    # populations come in the canonical order i = (cx+1) + 3(cy+1) + 9(cz+1)
+    i = np.arange(27)
+    c = np.stack([i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1], axis=1).astype(np.float64)
+
+    def moments(fa, fb):
+        ft = (fa + fb).reshape(27, 4, ny, 4)[:, 0, :, 0]  # [dir][y] at x = z = 0
+        rho = ft.sum(0)
+        j = np.einsum("ia,iy->ay", c, ft)
+        pi = np.einsum("ia,ib,iy->aby", c, c, ft)
+        return rho, j, pi
+
+    r = _sim(**kw)
+    r.reconstruct(f["phi"], f["rho"], np.stack([f["ux"], f["uy"], f["uz"]]))
+    rho0, j0, pi0 = moments(fa, fb)
+    rho1, j1, pi1 = moments(*r.get_populations())
+    inner = slice(3, ny - 3)
+    np.testing.assert_allclose(rho1[inner], rho0[inner], rtol=1e-12)
+    # momentum: the reconstruction stores rho u, the lattice holds rho u - F/2
+    np.testing.assert_allclose(j1[2, inner] - 0.5 * g * rho0[inner], j0[2, inner], rtol=1e-6, atol=1e-15)
+    # the shear stress Pi_yz (the only non-equilibrium part of this flow)
+    s_lb, s_rec = pi0[1, 2, inner], pi1[1, 2, inner]
+    assert np.abs(s_lb).max() > 1e-5
+    # equal to round-off (a factor-2 or tau slip would be off by tens of %)
+    np.testing.assert_allclose(s_rec, s_lb, rtol=1e-8, atol=1e-9 * np.abs(s_lb).max())

@@ -362,3 +362,27 @@ def test_moment_storage_matches_reduced_and_oracle():
     box = (3, 2, 5, 8, 7, 9)
     (ma, mb), (ra, rb) = m.populations(box), r.populations(box)
     assert np.abs(ma - ra).max() <= 2e-6 and np.abs(mb - rb).max() <= 2e-6
+
+
+def test_instability_is_reported_not_hidden():
+    """Failure detection without a GPU fault: the fused kernel flags a
+    non-positive or non-finite density in the status word and lb_check
+    returns LB_EUNSTABLE; a negative density planted at one node trips it on
+    the first step, and a sound state reports nothing."""
+    import paper_2405_14551_gb300.lbcg as L
+    nx = ny = nz = 16
+    phi = -np.ones((nz, ny, nx), dtype=np.float32)
+    rho = np.ones_like(phi)
+    rho[5, 6, 7] = -0.5
+    s = L.Sim(nx, ny, nz)
+    s.init_fields(phi, rho, np.zeros((3, nz, ny, nx), dtype=np.float32))
+    s.step(1)
+    with pytest.raises(L.LBError) as ei:
+        s.check()
+    assert ei.value.code == L.LB_EUNSTABLE
+    s.close()
+    ok = L.Sim(nx, ny, nz)  # a sound state reports nothing
+    ok.init_fields(phi, np.ones_like(phi), np.zeros((3, nz, ny, nx), dtype=np.float32))
+    ok.step(20)
+    ok.check()
+    ok.close()

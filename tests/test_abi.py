@@ -109,3 +109,17 @@ def test_conv_argument_checks_without_gpu(lib):
                                      None) == L.LB_EINVAL  # ny % 16
     assert lib.lbnn_conv3d_fwd_upcat(buf, 32, buf, 64, buf, None, buf, None, 32, 0, 16, 16, 3, 1, 0, 1, st,
                                      None) == L.LB_EINVAL  # odd nz
+
+
+def test_storage_formats_agree_between_header_and_binding():
+    """The binding's storage names, and the algorithmic bytes per node update
+    it reports, follow the LB_STORAGE_* formats the header defines."""
+    import paper_2405_14551_gb300.lbcg as L
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbcg.h")).read()
+    defs = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"#define LB_STORAGE_(\w+) (\d+)", hdr)}
+    assert defs == L.STORAGE
+    # one read + one write of the stored state per node update
+    per_lattice = {"twoset_f32": 2 * 27 * 4, "reduced_f32": 27 * 4 + 16, "reduced_f16": 27 * 2 + 16,
+                   "twoset_f64": 2 * 27 * 8, "moment_f32": 10 * 4 + 16}
+    for name, st in L.STORAGE.items():
+        assert L.BYTES_PER_NODE[st] == 2 * per_lattice[name], name

@@ -136,3 +136,36 @@ def test_wall_stops_scan():
     s.init_fields(phi)
     f = s.fields()
     assert np.all(f["h"] == 0)
+
+
+@pytest.mark.parametrize("name", ["diagonal_film", "two_to_one_film"])
+def test_oblique_film_hand_counted(name):
+    """Films whose normal is off the lattice axes (tests/golden/nc_oblique_film.json):
+    the scan's targets are x + lround(k n_out) with a non-axis normal, so the
+    rounding decides which nodes are visited (a diagonal ray visits s + 2
+    twice; a (2, 1) ray steps over the opposite interface of the outer layer)."""
+    with open(os.path.join(GOLDEN, "nc_oblique_film.json")) as fh:
+        case = {c["name"]: c for c in json.load(fh)["cases"]}[name]
+    nx, ny, a, b, nz = case["nx"], case["ny"], case["a"], case["b"], 2
+    prof = np.array([1, 1, 0.5, -0.5, -1, -0.5, 0.5, 1], dtype=np.float64)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    s_of = (a * x + b * y) % 8
+    phi = np.broadcast_to(prof[s_of][None], (nz, ny, nx)).copy()
+    p = oracle.make_params(nx, ny, nz, A_h=0.1, h_min=3.0, h_max=3.0)
+    sim = oracle.OracleSim(p)
+    sim.init_fields(phi)
+    f = sim.fields()
+    for s in range(8):
+        m = np.broadcast_to(s_of == s, (nz, ny, nx))
+        assert np.all(f["h"][m] == case["h_s"][str(s)]), (s, np.unique(f["h"][m]))
+        np.testing.assert_allclose(f["gz"][m], 0.0, atol=1e-15)
+        if "g_s" in case:
+            np.testing.assert_allclose(f["gx"][m], case["g_s"][str(s)], atol=1e-15)
+            np.testing.assert_allclose(f["gy"][m], case["g_s"][str(s)], atol=1e-15)
+        if str(s) in case.get("gx_s", {}):
+            np.testing.assert_allclose(f["gx"][m], case["gx_s"][str(s)], atol=1e-15)
+            np.testing.assert_allclose(f["gy"][m], case["gy_s"][str(s)], atol=1e-15)
+        # F_rep = (A_h/2) grad phi where h > 0, else 0 (Eq. near_cont_force, reading C9)
+        on = case["h_s"][str(s)] > 0
+        np.testing.assert_allclose(f["Frx"][m], 0.05 * f["gx"][m] if on else 0.0, atol=1e-17)
+        np.testing.assert_allclose(f["Fry"][m], 0.05 * f["gy"][m] if on else 0.0, atol=1e-17)

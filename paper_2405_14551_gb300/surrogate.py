@@ -335,7 +335,8 @@ def generate_pairs(seeds, shape=(128, 128, 256), K=50, spinup=200, snaps=6, stor
     p = workload_params()
     sim = L.Sim(*shape, walls=0b010, stream=stream, storage=storage, **p)
     for seed in seeds:
-        phi, _ = W.dense_emulsion_phi(shape, 0b010, int(seed), device=torch.device("cuda", torch.cuda.current_device()))
+        phi, _ = W.dense_emulsion_phi(shape, 0b010, int(seed), device=torch.device("cuda", torch.cuda.current_device()),
+                                      film=W.DENSE_FILM)
         sim.init_fields(phi)
         sim.step(spinup)
         snaps_t = []

@@ -162,3 +162,28 @@ def test_reconstruction_matches_chapman_enskog_in_poiseuille(tau):
     assert np.abs(s_lb).max() > 1e-5
     # equal to round-off (a factor-2 or tau slip would be off by tens of %)
     np.testing.assert_allclose(s_rec, s_lb, rtol=1e-8, atol=1e-9 * np.abs(s_lb).max())
+
+
+@pytest.mark.slow
+def test_dense_emulsion_films_hold_with_near_contact():
+    """The dense-emulsion seeding (power cells eroded by 6-node films, twice
+    h_min; reading C15) on a small walled channel: with the near-contact
+    force the five droplets stay apart, without it they merge within 400
+    steps (the force "prevents droplet merging", near-contact paragraph of
+    Sec. III.C.1).  With the 3.2-node films of a 0.7 target fraction the
+    droplets merge within 200 steps with or without the force, so the
+    seeding keeps films of 2 h_min."""
+    from paper_2405_14551_gb300 import workloads as W
+    shape = (40, 48, 40)
+    phi, info = W.dense_emulsion_phi(shape, 0b010, 3, film=W.DENSE_FILM)
+    assert info["droplets"] == 5
+    counts = {}
+    for A_h in (0.1, 0.0):
+        s = _sim(shape=shape, walls=0b010, A_h=A_h, h_min=3.0, h_max=3.0, g=(0.0, 0.0, 1e-6), g_mode=1)
+        s.init_fields(phi.astype(np.float64))
+        counts[A_h] = []
+        for _ in range(4):
+            s.step(100)
+            counts[A_h].append(s.droplet_count())
+    assert counts[0.1] == [5, 5, 5, 5], counts
+    assert counts[0.0][-1] == 1 and counts[0.0][0] < 5, counts

@@ -69,6 +69,25 @@ def test_dense_emulsion_fraction_walls_and_seed():
     assert np.any(phi3 != phi)
 
 
+def test_dense_emulsion_film_seeding():
+    """The bench's seeding: cells eroded by a film of DENSE_FILM nodes.  Every
+    +1 node lies at least half a film from its cell's faces and from the
+    walls, so two droplets are never closer than the film."""
+    shape, walls = (64, 48, 80), 0b010
+    phi, info = W.dense_emulsion_phi(shape, walls, seed=5, film=W.DENSE_FILM)
+    rng = np.random.default_rng(5)
+    cen, rad = W.rsa_spheres(shape, walls, rng, 8.0, 12.0, max_fail=400)
+    owner, margin = W.power_cell_margin(shape, walls, cen, rad, 12.0)
+    fl = W.fluid_mask(shape, walls)
+    inside = phi > 0
+    assert np.all(margin[inside] >= 0.5 * W.DENSE_FILM) and np.all(fl[inside])
+    assert np.all(phi[fl & (margin < 0.5 * W.DENSE_FILM)] == -1.0)
+    assert info["film"] == W.DENSE_FILM and abs(info["phi_d"] - float(inside[fl].mean())) < 1e-12
+    # a thinner film reaches a larger fraction, bounded by the 0.7 of the fraction mode
+    assert info["phi_d"] < W.dense_emulsion_phi(shape, walls, seed=5, phi_d=0.7)[1]["phi_d"]
+    assert len(np.unique(owner[inside])) == info["droplets"] == len(rad)
+
+
 def test_batch_sweep_ranges_and_seed():
     runs = W.batch_sweep()
     assert len(runs) == 64

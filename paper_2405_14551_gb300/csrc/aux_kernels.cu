@@ -3,6 +3,7 @@
 // The reductions are the only FP64 arithmetic of the FP32 path: per-block
 // partial sums in a fixed partition and a fixed tree order, then one block
 // sums the partials in a fixed order, so results are bitwise reproducible.
+#include "../../include/lbcg.h"
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -77,6 +78,9 @@ cudaError_t launch_phi_from_init(int storage, const Geo& g, const float* phi0, v
 // ---------------------------------------------------------------------------
 constexpr int RED_THREADS = 256;
 constexpr int RED_MAX_BLOCKS = 1024;
+// the allocation-free reduction keeps one partial per block in a static array
+// of LB_STATIC_REDUCE_MAX_BLOCKS entries
+static_assert(RED_MAX_BLOCKS <= LB_STATIC_REDUCE_MAX_BLOCKS, "static partials too small for the reduction");
 
 int reduce_blocks(long long N) {
   long long b = (N + RED_THREADS * 8 - 1) / (RED_THREADS * 8);

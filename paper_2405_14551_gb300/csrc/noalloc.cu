@@ -31,7 +31,10 @@ std::mutex g_setup_mutex;
 
 // Device address of the partials array on the current device.  Host code only
 // sees a host-side stand-in under the array's name, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The
+// cached address belongs to the device's primary context: after a
+// cudaDeviceReset of that device it no longer refers to the array (see the
+// declaration in lbcg.h).
 int partials_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -58,6 +61,8 @@ extern "C" int lb_reduce_fields_f64_static(const void* fields, int fields_are_f6
   if (walls & ~7u) return lbcg::report_error(LB_EINVAL, "walls uses bits 0..2 only");
   const long long N = (long long)nx * ny * nz;
   if (N > 0x7fffffffLL) return lbcg::report_error(LB_EINVAL, "grid has more than 2^31-1 nodes");
+  // defensive: reduce_blocks never exceeds RED_MAX_BLOCKS, which a
+  // static_assert in aux_kernels.cu keeps within the static array
   if (lbcg::reduce_blocks(N) > LB_STATIC_REDUCE_MAX_BLOCKS)
     return lbcg::report_error(LB_EINVAL, "grid needs more partial sums than the static scratch holds");
   double* partials = nullptr;

@@ -3,8 +3,9 @@
 
 Default workload: the confined dense emulsion, 256x256x512 nodes, walls at
 y=0/255, 70 % dispersed phase, near-contact force on, FP32 two population
-sets.  A "step" is one full LB time step (phase-field pass, near-contact
-scan, fused collide-recolour-force-stream pass) over the whole box; the state
+sets.  A "step" is one full LB time step over the whole box: one kernel
+that stages phi, runs the near-contact scan, pulls, collides, recolours,
+stores and accumulates the next step's component densities; the state
 (14.5 GB) is far larger than L2 (129 MB), so no flush is needed between
 steps.
 
@@ -47,8 +48,10 @@ def parse():
     ap.add_argument("--shape", default=None, help="nx,ny,nz of a smaller emulsion (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-tune", action="store_true", help="use --tile without autotuning")
-    ap.add_argument("--tile", type=int, default=0, help="tile of the fused kernel when --no-tune is given")
-    ap.add_argument("--nc-tile", type=int, default=0, help="tile of the near-contact scan when --no-tune is given")
+    ap.add_argument("--tile", type=int, default=0, help="tile of the step kernel when --no-tune is given")
+    ap.add_argument("--conv", nargs="+", default=None, metavar="ARG",
+                    help="MODE NX NY NZ CIN COUT [REPS]: time one surrogate convolution call instead "
+                         "(MODE fwd, upcat or wgrad; used by the convolution profiles)")
     return ap.parse_args()
 
 
@@ -192,12 +195,12 @@ class ClockSampler:
                 "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
 
 
-# DRAM bytes per node of one fused-step launch, read from an ncu capture
+# DRAM bytes per node of one step launch, read from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of k_step on the dense emulsion
-# 128x128x256, tile 2, divided by its nodes; the kernel's traffic grows with the
-# node count) together with a digest of the kernel sources it was taken on: a
-# changed kernel reports null until it is captured again.
-K_STEP_TRAFFIC = {"twoset_f32": (419.85, "b277b7cc4e35238f")}
+# 128x128x256 with the given tile, divided by its nodes; the kernel's traffic
+# grows with the node count) together with a digest of the kernel sources it
+# was taken on: a changed kernel reports null until it is captured again.
+K_STEP_TRAFFIC = {}  # storage -> (bytes per node, source digest, tile)
 
 
 def kernel_digest():
@@ -286,7 +289,7 @@ def end_to_end(args, L, sim, wl, nodes, world, barrier, maxall):
             "region": "lb_init_fields(host phi) + lb_step(K) + lb_fields(phi,rho,u -> host)"}
 
 
-def other_storages(args, L, make, stream, tile, nc_tile, world, nodes, maxall, peak):
+def other_storages(args, L, make, stream, tile, world, nodes, maxall, peak):
     """The reduced FP32 and FP16-deviation formats on the same workload, the
     regularised collision in the bench's own storage, and the moment storage
     of the regularised collision (ten coefficients + colour scalars per node)."""
@@ -298,14 +301,13 @@ def other_storages(args, L, make, stream, tile, nc_tile, world, nodes, maxall, p
         if other == "moment_f32" and args.storage == "moment_f32" and coll == 1 and f"{other}_regularised" in extra:
             continue
         s2 = make(other, collision=coll)
-        L.lb_set_nc_tile(s2.h, nc_tile)
         s2.step(3)
         best, t2ms = tile, None
-        if not args.no_tune:  # the fused tile of each storage tuned on its own
+        if not args.no_tune:  # the tile of each storage tuned on its own
             for tl in range(5):
                 L.lb_set_tile(s2.h, tl)
                 s2.step(2)
-                _, km, _ = L.lb_step_timed(s2.h, 4)
+                km = L.lb_step_timed(s2.h, 4)
                 if t2ms is None or km < t2ms:
                     best, t2ms = tl, km
         L.lb_set_tile(s2.h, best)
@@ -319,13 +321,12 @@ def other_storages(args, L, make, stream, tile, nc_tile, world, nodes, maxall, p
         s2.check()
         m2 = maxall(e0.elapsed_time(e1))
         v2 = world * nodes * args.steps / (m2 / 1e3) / 1e6
-        pm, sm, nm = L.lb_step_timed(s2.h, 20)
+        sm = L.lb_step_timed(s2.h, 20)
         b2 = L.BYTES_PER_NODE[L.STORAGE[other]]
         extra[other if coll == 0 else f"{other}_regularised"] = {"MLUPS": round(v2, 1), "bytes_per_node": b2, "tile": best,
                         "whole_step_frac": round(b2 * v2 * 1e6 / world / 1e9 / peak, 4),
-                        "fused_kernel_ms": round(sm, 4), "phase_field_ms": round(pm, 4),
-                        "near_contact_ms": round(nm, 4),
-                        "fused_kernel_GBps": round(b2 * nodes / (sm / 1e3) / 1e9, 1)}
+                        "step_kernel_ms": round(sm, 4),
+                        "step_kernel_GBps": round(b2 * nodes / (sm / 1e3) / 1e9, 1)}
         s2.close()
         del s2
         torch.cuda.empty_cache()
@@ -412,7 +413,7 @@ def surrogate_extra(L, stream, ntraj=24, iters=4000, cycles=100, spinup=2000):
         fwd_ms = e0.elapsed_time(e1) / 5
         del trajs, test
         p = S.workload_params()
-        phi, _ = W.dense_emulsion_phi(shape, 0b010, 1001, device=torch.device("cuda"))
+        phi, _ = W.dense_emulsion_phi(shape, 0b010, 1001, device=torch.device("cuda"), film=W.DENSE_FILM)
         a = L.Sim(nx, ny, nz, walls=0b010, stream=stream, **p)
         b = L.Sim(nx, ny, nz, walls=0b010, stream=stream, **p)
         for s_ in (a, b):
@@ -462,8 +463,70 @@ def cpu_baseline(wl):
             "kind": "oracle", "sample": f"{desc}, 4 FP64 steps after 1 warm-up ({dt:.1f} s)"}
 
 
+def conv_call(argv):
+    """Time one call of a surrogate convolution kernel on random BF16 data.
+
+    MODE fwd (lbnn_conv3d_fwd), upcat (lbnn_conv3d_fwd_upcat with a third of
+    CIN at full resolution and the rest at half resolution) or wgrad
+    (lbnn_conv3d_wgrad); 3x3x3 taps, x and z periodic, y zero-padded.  Prints
+    the CUDA-event time of the last of REPS launches (default 3) and the FLOP
+    rate of the implicit GEMM (2 x 27 x CIN x COUT per voxel)."""
+    import ctypes
+    import torch
+    import paper_2405_14551_gb300.lbcg as L
+    mode = argv[0]
+    nx, ny, nz, cin, cout = (int(v) for v in argv[1:6])
+    reps = int(argv[6]) if len(argv) > 6 else 3
+    lib = L.load_library()
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream()
+    sp = ctypes.c_void_p(st.cuda_stream)
+    status = torch.zeros(4, dtype=torch.int32, device=dev)
+
+    def P(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    nv = nx * ny * nz
+    g = torch.Generator(device=dev).manual_seed(0)
+    with torch.cuda.stream(st):
+        w = (torch.randn(cout, 27, cin, device=dev, generator=g) * 0.05).to(torch.bfloat16)
+        b = torch.zeros(cout, device=dev)
+        cs = cin // 3 if mode == "upcat" else cin
+        x = torch.randn(nv, cs, device=dev, generator=g).to(torch.bfloat16)
+        x2 = torch.randn(nv // 8, cin - cs, device=dev, generator=g).to(torch.bfloat16) if mode == "upcat" else None
+        y = torch.empty(nv, cout, device=dev, dtype=torch.bfloat16)
+        gy = torch.randn(nv, cout, device=dev, generator=g).to(torch.bfloat16) if mode == "wgrad" else None
+        dw = torch.zeros(cout, 27, cin, device=dev) if mode == "wgrad" else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(reps):
+            if i == reps - 1:
+                e0.record(st)
+            if mode == "fwd":
+                rc = lib.lbnn_conv3d_fwd(P(x), cin, P(w), 27, P(b), P(y), None, cout, 0, nx, ny, nz, 1, 5, 1,
+                                         P(status), sp)
+            elif mode == "upcat":
+                rc = lib.lbnn_conv3d_fwd_upcat(P(x), cs, P(x2), cin - cs, P(w), P(b), P(y), None, cout, 0, nx, ny, nz,
+                                               1, 5, 1, P(status), sp)
+            elif mode == "wgrad":
+                rc = lib.lbnn_conv3d_wgrad(P(gy), cout, P(x), cin, 27, P(dw), nx, ny, nz, 1, 5, 64, P(status), sp)
+            else:
+                raise SystemExit(f"unknown mode {mode}")
+            if rc:
+                raise SystemExit(f"{mode}: {lib.lb_last_error().decode()}")
+        e1.record(st)
+        st.synchronize()
+    ms = e0.elapsed_time(e1)
+    if int(status.sum().item()):
+        raise SystemExit(f"{mode}: a kernel gave up a bounded wait (status {status.tolist()})")
+    flop = 2.0 * nv * 27 * cin * cout
+    print(f"{mode} {nx}x{ny}x{nz} {cin}->{cout}: {ms * 1e3:.1f} us, {flop / ms / 1e9:.1f} TFLOP/s")
+
+
 def main():
     args = parse()
+    if args.conv:
+        conv_call(args.conv)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -480,7 +543,7 @@ def main():
                 dev = torch.device("cuda", 0)  # input geometry only; the timed arm is the CPU oracle
         except ImportError:
             pass
-        wl_phi, _ = W.dense_emulsion_phi(SHAPE, 0b010, SEED, device=dev)
+        wl_phi, _ = W.dense_emulsion_phi(SHAPE, 0b010, SEED, device=dev, film=W.DENSE_FILM)
         params = dict(W.BASE, A_h=0.1, h_min=3.0, h_max=3.0, g=(0.0, 0.0, 1e-6), g_mode=1)
         reference_arm(args, params, wl_phi)
         return
@@ -511,22 +574,15 @@ def main():
 
     collision = args.collision if args.collision is not None else (1 if storage == "moment_f32" else 0)
     sim = make(storage, collision)
-    # autotune the tiles of the fused kernel and of the near-contact scan
-    # (independent kernels): time every shape, keep the fastest of each
-    tile_ms, nc_ms = [], []
+    # autotune the tile of the step kernel: time every shape, keep the fastest
+    tile_ms = []
     sim.step(max(3, args.warmup))
     for tile in range(0 if args.no_tune else 5):
         L.lb_set_tile(sim.h, tile)
-        L.lb_set_nc_tile(sim.h, min(tile, 3))
-        sim.step(16)
-        _, kms, nms = L.lb_step_timed(sim.h, 6)
-        tile_ms.append(kms)
-        if tile < 4:
-            nc_ms.append(nms)
+        sim.step(12)
+        tile_ms.append(L.lb_step_timed(sim.h, 6))
     best_tile = int(np.argmin(tile_ms)) if tile_ms else args.tile
-    best_nc = int(np.argmin(nc_ms)) if nc_ms else args.nc_tile
     L.lb_set_tile(sim.h, best_tile)
-    L.lb_set_nc_tile(sim.h, best_nc)
     sim.step(args.warmup)
     sim.check()
 
@@ -548,19 +604,19 @@ def main():
     clocks = clk.summary()
 
     # live per-kernel timing (CUDA events on the library's stream)
-    phi_ms, step_ms, nc_kms = L.lb_step_timed(sim.h, 20)
+    step_ms = L.lb_step_timed(sim.h, 20)
     peak, peak_kind = peaks()
     bpn = L.BYTES_PER_NODE[stid]
     achieved = bpn * nodes / (step_ms / 1e3) / 1e9
     tr = K_STEP_TRAFFIC.get(storage)
-    traffic = round(tr[0] * nodes) if (tr and tr[1] == kernel_digest() and best_tile == 2) else None
+    traffic = round(tr[0] * nodes) if (tr and tr[1] == kernel_digest() and best_tile == tr[2]) else None
     step_frac = bpn * value * 1e6 / world / 1e9 / peak
 
     e2e = None if args.no_e2e else end_to_end(args, L, sim, wl, nodes, world, barrier, maxall)
     sim.close()
     del sim
     torch.cuda.empty_cache()
-    extra = {} if args.no_extra else other_storages(args, L, make, stream, best_tile, best_nc, world, nodes, maxall, peak)
+    extra = {} if args.no_extra else other_storages(args, L, make, stream, best_tile, world, nodes, maxall, peak)
     if not args.no_extra:
         extra["fp32_alu"] = {"sgemm_tflops": fp32_alu_peak(),
                              "how": "cuBLAS SGEMM 8192^3 with TF32 off, best of 5 (FMA pipes only)"}
@@ -588,13 +644,12 @@ def main():
                        "walls": "y", "seed": SEED,
                        "dispersed_fraction": round(wl.info.get("phi_d", 0.0), 4), "droplets": wl.info.get("droplets"),
                        "A_h": wl.params["A_h"], "h_min": wl.params["h_min"], "tile": best_tile,
-                       "tile_ms": [round(v, 4) for v in tile_ms], "nc_tile": best_nc,
-                       "nc_tile_ms": [round(v, 4) for v in nc_ms],
+                       "tile_ms": [round(v, 4) for v in tile_ms],
                        "l2": "state far larger than L2, no flush", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": "k_step (fused)",
-                         "peak_kind": peak_kind, "kernel_ms": round(step_ms, 4), "phase_field_ms": round(phi_ms, 4),
-                         "near_contact_ms": round(nc_kms, 4),
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": "k_step (the whole step: one launch)",
+                         "peak_kind": peak_kind, "kernel_ms": round(step_ms, 4),
                          "bytes_per_node": bpn, "whole_step_frac": round(step_frac, 4)},
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -35,7 +35,8 @@ extern "C" {
 #define LB_EINVAL -1    /* an argument failed host-side validation; no GPU work was issued */
 #define LB_ENOMEM -2    /* a device or host allocation failed */
 #define LB_ECUDA -3     /* a CUDA runtime call failed (detail in lb_last_error) */
-#define LB_EUNSTABLE -4 /* the device status word saw a non-finite or non-positive density */
+#define LB_EUNSTABLE -4 /* the device status word saw a density that is not finite, not positive or not below 4
+                           (64 in FP64 storage), the range of the fixed-point density sums */
 #define LB_ETIMEOUT -5  /* a bounded device wait gave up */
 #define LB_ESTATE -6    /* the call is not valid in the handle's current state */
 #define LB_EIO -7       /* file read/write failed or the file is not a checkpoint of this grid */
@@ -119,8 +120,10 @@ typedef struct {
 
 /* Create a handle on the current CUDA device.  Validates grid and params on
  * the host (LB_EINVAL, nothing allocated), then allocates two population
- * lattices in the chosen storage, a phase-field array and the initial-field
- * arrays.  *out receives the handle (caller-owned; release with lb_destroy). */
+ * lattices in the chosen storage, three accumulators of the component
+ * densities (8 bytes per node each, 16 in FP64 storage) that carry phi from
+ * one step to the next, and the initial-field arrays.  *out receives the
+ * handle (caller-owned; release with lb_destroy). */
 int lb_create(const lb_grid* grid, const lb_params* params, const lb_alloc* alloc, lb_handle** out);
 
 /* Release all device memory of the handle (after synchronising its stream). */
@@ -147,32 +150,27 @@ int lb_init_droplets(lb_handle* h, int32_t n, const double* centres, const doubl
 int lb_init_fields(lb_handle* h, const float* phi, const float* rho, const float* u, int regularised,
                    int is_device);
 
-/* Advance nsteps >= 0 time steps, asynchronously on the handle's stream
- * (each step: phase-field pass; with A_h != 0 the near-contact scan of
- * Eqs. stress_jump / near_cont_force, which writes the distance h of every
- * node; then the fused collide-recolour-force-stream pass).  Runs of steps
- * are replayed from a captured CUDA graph. */
+/* Advance nsteps >= 0 time steps, asynchronously on the handle's stream.
+ * Each step is one kernel over tiles of nodes: it stages phi of the tile and
+ * a halo, runs the near-contact scan of Eqs. stress_jump / near_cont_force
+ * for the tile's interface nodes (with A_h != 0), pulls, collides, recolours
+ * and stores every node (one read and one write of the population state),
+ * and adds each stored component population to the density sums of the node
+ * that pulls it next, which give phi at the next step (Eq. order_param).
+ * Runs of 12 steps are replayed from a captured CUDA graph. */
 int lb_step(lb_handle* h, int64_t nsteps);
 
-/* Choose the tile shape of the fused step kernel (0..4: 32x8x4, 32x8x8,
- * 32x8x4 with a register cap for 3 CTAs per SM, 64x4x4, 32x8x4 capped for 4
- * CTAs per SM, nodes per CTA); used by the autotuner.  Results do not
- * depend on the tile.  lb_get_tile returns the current index. */
+/* Choose the tile shape of the step kernel (0..4: 32x8x4, 32x8x8, 32x8x4
+ * with a register cap for 3 CTAs per SM, 32x8x8 capped for 3 CTAs per SM,
+ * 32x8x4 capped for 4 CTAs per SM, nodes per CTA); used by the autotuner.
+ * Results do not depend on the tile (bit for bit).  lb_get_tile returns the
+ * current index. */
 int lb_set_tile(lb_handle* h, int tile);
 int lb_get_tile(const lb_handle* h);
 
-/* Choose the tile shape of the near-contact scan kernel (0..3: 32x8x8,
- * 32x8x4, 32x8x16, 32x4x16 nodes per CTA; FP64 storage always uses 32x8x4);
- * used by the autotuner.  Results do not
- * depend on it.  LB_EINVAL outside 0..3; lb_get_nc_tile returns the index. */
-int lb_set_nc_tile(lb_handle* h, int variant);
-int lb_get_nc_tile(const lb_handle* h);
-
-/* Advance nsteps >= 1 steps without graph replay, recording CUDA events on
- * the handle's stream around every kernel.  Synchronises the stream; ms[0]
- * receives the mean duration of the phase-field pass, ms[1] that of the
- * fused step kernel and ms[2] that of the near-contact scan (0 without near
- * contact), in milliseconds (host array of 3 doubles). */
+/* Advance nsteps >= 1 steps without graph replay, recording a CUDA event on
+ * the handle's stream after every step kernel.  Synchronises the stream;
+ * *ms receives the mean duration of one step kernel in milliseconds. */
 int lb_step_timed(lb_handle* h, int64_t nsteps, double* ms);
 
 /* Steps taken since the last initialisation. */
@@ -251,7 +249,8 @@ int lb_surrogate_cycle(lb_handle* h, lb_handle* judge, int32_t K, double vol_tol
                        double* phi_err);
 
 /* Synchronise the stream and read the device status word: LB_OK or
- * LB_EUNSTABLE once any step met a non-finite or non-positive density. */
+ * LB_EUNSTABLE once any step met a density that is not finite, not positive
+ * or not below 4 (64 in FP64 storage). */
 int lb_check(lb_handle* h);
 
 /* Checkpoint: raw population state, step counter, grid, parameters and a
@@ -292,11 +291,11 @@ int32_t lb_batch_size(const lb_batch* b);
 int64_t lb_batch_nodes(const lb_batch* b);
 int lb_batch_set_stream(lb_batch* b, void* stream);
 
-/* Advance every run by nsteps: per step one persistent launch of the
- * phase-field pass, one of the near-contact scan (when a run has A_h != 0)
- * and one of the fused pass over the work list of all runs' (run, tile)
- * items, replayed from a captured CUDA graph.  All runs must be
- * initialised; the first step of freshly initialised runs is taken per run. */
+/* Advance every run by nsteps: per step one persistent launch over the work
+ * list of all runs' (run, tile) items (the step of lb_step on each tile),
+ * replayed from a captured CUDA graph.  All runs must be initialised and at
+ * the same lattice parity; the first step of freshly initialised runs is
+ * taken per run. */
 int lb_batch_step(lb_batch* b, int64_t nsteps);
 
 /* The one-run-at-a-time baseline: lb_step on each run in turn. */
@@ -334,7 +333,10 @@ int lb_batch_check(lb_batch* b);
  * that device current; make that first call before any stream capture.
  * Every call shares the one array: calls that overlap on the GPU (concurrent
  * streams) race and must be serialised by the caller.  Nothing needs
- * clearing between calls: every partial and every output is overwritten. */
+ * clearing between calls: every partial and every output is overwritten.
+ * The address found by the first call stays in use for the life of the
+ * process; after a cudaDeviceReset of a device, do not call this entry point
+ * on that device again. */
 #define LB_STATIC_REDUCE_MAX_BLOCKS 1024
 int lb_reduce_fields_f64_static(const void* fields, int fields_are_f64, int32_t nx, int32_t ny, int32_t nz,
                                 uint32_t walls, double* out, void* stream);

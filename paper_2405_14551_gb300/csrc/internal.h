@@ -28,7 +28,6 @@ struct Phys {
   double phi_I;
   double g[3];
   int g_mode;
-  int halo;   // phi tile halo of the near-contact pass: K + 1 (1 without near contact)
   int collision;  // 0 BGK, 1 regularised
 };
 
@@ -51,16 +50,34 @@ struct InitBuf {
 
 enum Loader { LOAD_PULL = 0, LOAD_FIELDS = 1 };
 
-// One run of a batch, as seen by the batched persistent kernels.
+// Where a step reads phi(t): the accumulator of the previous step, or a
+// plain array of the compute type (the initial fields' phi).  Exactly one is
+// non-null.
+struct PhiSrc {
+  const void* phi;
+  const unsigned long long* acc;
+};
+
+// Accumulators written by a step: out receives the component densities of
+// the next time level (all zero before the step); the step zeroes its own
+// nodes of zero (read by the step before, written by the step after).
+struct AccBufs {
+  unsigned long long* out;
+  unsigned long long* zero;
+};
+
+// 64-bit words of one node's accumulator: 1 (FP32 storages, both component
+// sums packed), 2 (FP64).
+inline int acc_words(int storage) { return storage == 3 ? 2 : 1; }
+
+// One run of a batch, as seen by the batched persistent kernel.
 struct RunDesc {
   Geo g;
   Phys p;
   StateBuf S[2];
-  void* phi;
-  unsigned char* hnc;  // near-contact distance per node
+  unsigned long long* acc[3];  // accumulator rotation (see AccBufs)
   int tiles_x, tiles_y, tiles_z;
-  long long tile_begin;   // first work item of this run in the step list
-  long long chunk_begin;  // first 256-node chunk of this run in the phase-field list
+  long long tile_begin;  // first work item of this run
 };
 
 // Tile shapes of the fused step kernel (x, y extent of the thread block and z
@@ -79,28 +96,28 @@ bool storage_is_twoset(int storage);
 bool storage_is_f64(int storage);
 
 // --- step_kernels.cu -------------------------------------------------------
-// phase-field pass: phi[N] (float, or double for FP64 storage) from pulled populations
-cudaError_t launch_phi(int storage, const Geo& g, const StateBuf& in, void* phi, cudaStream_t st);
-// near-contact pass: hnc[N] from phi; launches nothing when p.A_h == 0.
-// variant indexes the near-contact tile shapes (kNcTiles).
-cudaError_t launch_nc(int storage, int variant, const Geo& g, const Phys& p, const void* phi, unsigned char* hnc,
-                      cudaStream_t st);
-constexpr int NUM_NC_VARIANTS = 4;
-// fused step; tile index into kTiles (only tile 0 for non-hot variants)
+// halo of the phi tile a step stages: 1 without near contact, else 4 (scan
+// length K <= 3) or 7 (K <= 6)
+inline int stage_halo(const Phys& p) { return p.A_h == 0.0 ? 1 : (p.K <= 3 ? 4 : 7); }
+// rebuild the accumulator of the current time level from the populations of in
+cudaError_t launch_phi_acc(int storage, const Geo& g, const StateBuf& in, unsigned long long* acc, cudaStream_t st);
+// one step (write_state) and/or the fields of the current level (write_fields);
+// tile indexes kTiles (only tile 0 for the variants that are not hot)
 cudaError_t launch_step(int storage, int loader, bool write_state, bool write_fields, int tile, const Geo& g,
-                        const Phys& p, const StateBuf& in, const InitBuf& init, const void* phi,
-                        const unsigned char* hnc, StateBuf out, void* fields, unsigned* status, cudaStream_t st);
+                        const Phys& p, const StateBuf& in, const InitBuf& init, PhiSrc src, AccBufs ab, StateBuf out,
+                        void* fields, unsigned* status, cudaStream_t st);
 // export pre-collision populations of a box, canonical order, as double
 cudaError_t launch_export(int storage, int loader, const Geo& g, const Phys& p, const StateBuf& in,
                           const InitBuf& init, int x0, int y0, int z0, int bx, int by, int bz, double* outA,
                           double* outB, cudaStream_t st);
 
-// batched step over runs[0..nruns): phase-field pass, near-contact pass (when
-// halo_max > 1, i.e. some run has A_h != 0) and fused pass, each a persistent
-// launch of blocks_per_sm x SMs CTAs; parity selects S[parity] as input
-cudaError_t launch_batched(int storage, const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles,
-                           int tile, int halo_max, long long max_nodes, int parity, int blocks_per_sm,
-                           unsigned* status, cudaStream_t st);
+// batched step over runs[0..nruns): one persistent launch of blocks_per_sm x
+// SMs CTAs; parity selects S[parity] as input, k the accumulator phase
+// (runs read acc[k], add into acc[(k+1)%3], clear acc[(k+2)%3]); halo is the
+// largest stage_halo of the runs
+cudaError_t launch_batched(int storage, const RunDesc* d_runs, int nruns, long long ntiles, int tile, int halo,
+                           long long max_nodes, int parity, int k, int blocks_per_sm, unsigned* status,
+                           cudaStream_t st);
 int sm_count_host();
 
 // --- aux_kernels.cu ----------------------------------------------------------

@@ -1,9 +1,11 @@
 // C-ABI runtime of the colour-gradient LB library (declared in include/lbcg.h).
 //
-// A handle owns two population lattices (ping-pong), the phase-field side
-// array, the initial-field arrays and small scratch buffers.  Steps are issued
-// asynchronously on the handle's stream; runs of steps replay a captured CUDA
-// graph of STEPS_PER_GRAPH steps (two kernels per step).
+// A handle owns two population lattices (ping-pong), three accumulators of
+// the component densities that carry phi from one step to the next (see
+// step_impl.cuh), the initial-field arrays and small scratch buffers.  Steps
+// are issued asynchronously on the handle's stream, one kernel per step; runs
+// of steps replay a captured CUDA graph of STEPS_PER_GRAPH steps, one graph
+// per (lattice parity, accumulator phase).
 #include <cuda_runtime.h>
 #include <sys/stat.h>
 
@@ -26,7 +28,9 @@ using namespace lbcg;
 
 namespace {
 
-constexpr int STEPS_PER_GRAPH = 16;
+// a multiple of 2 (lattice parity) and 3 (accumulator phase): a replay
+// leaves both where they were
+constexpr int STEPS_PER_GRAPH = 12;
 constexpr uint32_t CKPT_MAGIC = 0x4742434cu;  // "LCBG"
 constexpr uint32_t CKPT_VERSION = 2;  // 2: lb_params carries the collision model
 
@@ -82,8 +86,12 @@ struct lb_handle {
 
   StateBuf S[2]{};
   int cur = 0;
-  void* phi = nullptr;      // R[N]
-  unsigned char* hnc = nullptr;  // near-contact distance per node (A_h != 0 only)
+  void* phi = nullptr;      // R[N]: phi of the initial fields
+  // accumulators of the component densities: acc[phi_acc] holds phi of the
+  // current time level, acc[(phi_acc + 1) % 3] is all zero; phi_acc = -1:
+  // phi is in the phi array (initial state) and all three are zero
+  unsigned long long* acc[3] = {nullptr, nullptr, nullptr};
+  int phi_acc = -1;
   float* init_phi = nullptr;
   float* init_rho = nullptr;
   float* init_u = nullptr;
@@ -98,8 +106,7 @@ struct lb_handle {
   bool initialised = false;
   int64_t t = 0;
   int tile = 0;
-  int nc_tile = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // [cur * 3 + phi_acc]
   uint64_t graph_launches = 0;  // kernel launches in one replay
   lbcg::SurrogateState* surrogate = nullptr;  // its device buffers are owned like the rest
 };
@@ -187,7 +194,7 @@ InitBuf init_buf(const lb_handle* h) {
 }
 
 void drop_graphs(lb_handle* h) {
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 6; ++k) {
     if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
     h->graph[k] = nullptr;
   }
@@ -221,45 +228,63 @@ int validate(const lb_grid* gr, const lb_params* p) {
   return LB_OK;
 }
 
-// Near-contact pass on the current phi (nothing without near contact).
-cudaError_t issue_nc(lb_handle* h) {
-  if (h->p.A_h == 0.0) return cudaSuccess;
+size_t acc_bytes(const lb_handle* h) { return (size_t)h->g.N * (size_t)acc_words(h->storage) * 8; }
+
+// Clear the three accumulators (phi then lives in the phi array).
+cudaError_t reset_acc(lb_handle* h) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMemsetAsync(h->acc[k], 0, acc_bytes(h), h->stream);
+  h->phi_acc = -1;
+  return e;
+}
+
+// Rebuild phi of the current population state into acc[0] (after populations
+// were loaded or copied in), acc[1] and acc[2] zero.
+cudaError_t rebuild_acc(lb_handle* h) {
+  cudaError_t e = reset_acc(h);
+  if (e == cudaSuccess) e = launch_phi_acc(h->storage, h->g, h->S[h->cur], h->acc[0], h->stream);
   g_launches += 1;
-  return launch_nc(h->storage, h->nc_tile, h->g, h->p, h->phi, h->hnc, h->stream);
+  h->phi_acc = 0;
+  return e;
+}
+
+// Where the current phi is read from, and the accumulators a step writes.
+PhiSrc phi_src(const lb_handle* h) {
+  if (h->phi_acc < 0) return PhiSrc{h->phi, nullptr};
+  return PhiSrc{nullptr, h->acc[h->phi_acc]};
+}
+AccBufs acc_bufs(const lb_handle* h) {
+  const int k = h->phi_acc < 0 ? 2 : h->phi_acc;  // from the phi array: every accumulator is zero
+  return AccBufs{h->acc[(k + 1) % 3], h->acc[(k + 2) % 3]};
 }
 
 // Issue one step (no graph).
 int issue_step(lb_handle* h) {
   const int nxt = h->cur ^ 1;
-  if (h->mode == 0) {
-    LB_CUDA(issue_nc(h));
-    LB_CUDA(launch_step(h->storage, LOAD_FIELDS, true, false, 0, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->hnc, h->S[nxt], nullptr, h->status, h->stream));
-    g_launches += 1;
-  } else {
-    LB_CUDA(launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream));
-    LB_CUDA(issue_nc(h));
-    LB_CUDA(launch_step(h->storage, LOAD_PULL, true, false, h->tile, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->hnc, h->S[nxt], nullptr, h->status, h->stream));
-    g_launches += 2;
-  }
+  const bool fresh = h->mode == 0;
+  LB_CUDA(launch_step(h->storage, fresh ? LOAD_FIELDS : LOAD_PULL, true, false, fresh ? 0 : h->tile, h->g, h->p,
+                      h->S[h->cur], init_buf(h), phi_src(h), acc_bufs(h), h->S[nxt], nullptr, h->status, h->stream));
+  g_launches += 1;
+  h->phi_acc = ((h->phi_acc < 0 ? 2 : h->phi_acc) + 1) % 3;
   h->cur = nxt;
   h->mode = 1;
   h->t += 1;
   return LB_OK;
 }
 
-int build_graph(lb_handle* h, int parity) {
+int graph_key(const lb_handle* h) { return h->cur * 3 + h->phi_acc; }
+
+int build_graph(lb_handle* h) {
   cudaGraph_t graph = nullptr;
-  const int save_cur = h->cur;
+  const int save_cur = h->cur, save_acc = h->phi_acc, key = graph_key(h);
   const int64_t save_t = h->t;
   const uint64_t save_l = g_launches.load();
-  h->cur = parity;
   LB_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int rc = LB_OK;
   for (int k = 0; k < STEPS_PER_GRAPH && rc == LB_OK; ++k) rc = issue_step(h);
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   h->cur = save_cur;
+  h->phi_acc = save_acc;
   h->t = save_t;
   h->graph_launches = g_launches.load() - save_l;
   g_launches = save_l;
@@ -268,7 +293,7 @@ int build_graph(lb_handle* h, int parity) {
     return rc;
   }
   if (e != cudaSuccess) return cuda_err(e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&h->graph[parity], graph, 0);
+  e = cudaGraphInstantiate(&h->graph[key], graph, 0);
   cudaGraphDestroy(graph);
   return cuda_err(e, "cudaGraphInstantiate");
 }
@@ -286,18 +311,10 @@ int compute_fields(lb_handle* h) {
   if (!h->initialised) return set_err(LB_ESTATE, "handle not initialised");
   int rc = ensure_fields(h);
   if (rc) return rc;
-  if (h->mode == 0) {
-    LB_CUDA(issue_nc(h));
-    LB_CUDA(launch_step(h->storage, LOAD_FIELDS, false, true, 0, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->hnc, h->S[h->cur ^ 1], h->fields, h->status, h->stream));
-    g_launches += 1;
-  } else {
-    LB_CUDA(launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream));
-    LB_CUDA(issue_nc(h));
-    LB_CUDA(launch_step(h->storage, LOAD_PULL, false, true, 0, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->hnc, h->S[h->cur ^ 1], h->fields, h->status, h->stream));
-    g_launches += 2;
-  }
+  LB_CUDA(launch_step(h->storage, h->mode == 0 ? LOAD_FIELDS : LOAD_PULL, false, true, 0, h->g, h->p, h->S[h->cur],
+                      init_buf(h), phi_src(h), AccBufs{nullptr, nullptr}, h->S[h->cur ^ 1], h->fields, h->status,
+                      h->stream));
+  g_launches += 1;
   return LB_OK;
 }
 
@@ -361,7 +378,6 @@ int lb_create(const lb_grid* grid, const lb_params* params, const lb_alloc* allo
   p.phi_I = params->phi_I;
   for (int a = 0; a < 3; ++a) p.g[a] = params->g[a];
   p.g_mode = params->g_mode;
-  p.halo = params->A_h != 0.0 ? p.K + 1 : 1;
   p.collision = params->collision;
   if (alloc && alloc->alloc && alloc->free) {
     h->alloc = *alloc;
@@ -376,7 +392,7 @@ int lb_create(const lb_grid* grid, const lb_params* params, const lb_alloc* allo
   const size_t N = (size_t)h->g.N;
   bool ok = alloc_state(h, h->S[0]) && alloc_state(h, h->S[1]);
   ok = ok && (h->phi = dev_alloc(h, N * real_bytes(h->storage))) != nullptr;
-  if (h->p.A_h != 0.0) ok = ok && (h->hnc = (unsigned char*)dev_alloc(h, N)) != nullptr;
+  for (int k = 0; k < 3; ++k) ok = ok && (h->acc[k] = (unsigned long long*)dev_alloc(h, acc_bytes(h))) != nullptr;
   ok = ok && (h->init_phi = (float*)dev_alloc(h, N * sizeof(float))) != nullptr;
   ok = ok && (h->red = (double*)dev_alloc(h, ((size_t)reduce_blocks(h->g.N) * 8 + 16) * sizeof(double))) != nullptr;
   ok = ok && (h->status = (unsigned*)dev_alloc(h, 256)) != nullptr;
@@ -385,7 +401,8 @@ int lb_create(const lb_grid* grid, const lb_params* params, const lb_alloc* allo
     lb_destroy(h);
     return set_err(LB_ENOMEM, "device allocation failed");
   }
-  if ((e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream)) != cudaSuccess) {
+  if ((e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream)) != cudaSuccess ||
+      (e = reset_acc(h)) != cudaSuccess) {
     lb_destroy(h);
     return cuda_err(e, "cudaMemsetAsync");
   }
@@ -445,6 +462,7 @@ int lb_init_droplets(lb_handle* h, int32_t n, const double* centres, const doubl
   cudaError_t e = launch_init_droplets(h->g, n, dbuf, dbuf ? dbuf + 3 * n : nullptr, width, h->init_phi, nullptr,
                                        nullptr, h->stream);
   if (e == cudaSuccess) e = launch_phi_from_init(h->storage, h->g, h->init_phi, h->phi, h->stream);
+  if (e == cudaSuccess) e = reset_acc(h);
   g_launches += 2;
   if (dbuf) {
     cudaStreamSynchronize(h->stream);
@@ -477,6 +495,7 @@ int lb_init_fields(lb_handle* h, const float* phi, const float* rho, const float
     LB_CUDA(cudaMemcpyAsync(h->init_u, u, 3 * N * sizeof(float), kind, h->stream));
   }
   LB_CUDA(launch_phi_from_init(h->storage, h->g, h->init_phi, h->phi, h->stream));
+  LB_CUDA(reset_acc(h));
   g_launches += 1;
   if (!is_device) LB_CUDA(cudaStreamSynchronize(h->stream));
   h->use_rho = rho != nullptr;
@@ -498,11 +517,11 @@ int lb_step(lb_handle* h, int64_t nsteps) {
     --nsteps;
   }
   while (nsteps >= STEPS_PER_GRAPH) {
-    const int par = h->cur;
-    if (!h->graph[par] && (rc = build_graph(h, par))) return rc;
-    LB_CUDA(cudaGraphLaunch(h->graph[par], h->stream));
+    const int key = graph_key(h);
+    if (!h->graph[key] && (rc = build_graph(h))) return rc;
+    LB_CUDA(cudaGraphLaunch(h->graph[key], h->stream));
     g_launches += h->graph_launches;
-    h->t += STEPS_PER_GRAPH;  // even number of steps: parity unchanged
+    h->t += STEPS_PER_GRAPH;  // parity and accumulator phase unchanged
     nsteps -= STEPS_PER_GRAPH;
   }
   while (nsteps-- > 0)
@@ -516,50 +535,28 @@ int lb_step_timed(lb_handle* h, int64_t nsteps, double* ms) {
   if (!h->initialised) return set_err(LB_ESTATE, "handle not initialised");
   int rc;
   if (h->mode == 0 && (rc = issue_step(h))) return rc;
-  std::vector<cudaEvent_t> ev((size_t)(4 * nsteps));
+  std::vector<cudaEvent_t> ev((size_t)(nsteps + 1));
   for (auto& e : ev) LB_CUDA(cudaEventCreate(&e));
-  cudaError_t err = cudaSuccess;
+  cudaError_t err = cudaEventRecord(ev[0], h->stream);
   for (int64_t k = 0; k < nsteps && err == cudaSuccess; ++k) {
-    const int nxt = h->cur ^ 1;
-    cudaEventRecord(ev[4 * k], h->stream);
-    err = launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream);
-    cudaEventRecord(ev[4 * k + 1], h->stream);
-    if (err == cudaSuccess) err = issue_nc(h);
-    cudaEventRecord(ev[4 * k + 2], h->stream);
-    if (err == cudaSuccess)
-      err = launch_step(h->storage, LOAD_PULL, true, false, h->tile, h->g, h->p, h->S[h->cur], init_buf(h), h->phi,
-                        h->hnc, h->S[nxt], nullptr, h->status, h->stream);
-    cudaEventRecord(ev[4 * k + 3], h->stream);
-    g_launches += 2;
-    h->cur = nxt;
-    h->t += 1;
+    if ((rc = issue_step(h))) {
+      for (auto& e : ev) cudaEventDestroy(e);
+      return rc;
+    }
+    err = cudaEventRecord(ev[(size_t)k + 1], h->stream);
   }
   if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
-  double s[3] = {0, 0, 0};
+  double s = 0.0;
   for (int64_t k = 0; k < nsteps && err == cudaSuccess; ++k) {
-    for (int j = 0; j < 3 && err == cudaSuccess; ++j) {
-      float a = 0;
-      err = cudaEventElapsedTime(&a, ev[4 * k + j], ev[4 * k + j + 1]);
-      s[j] += a;
-    }
+    float a = 0;
+    err = cudaEventElapsedTime(&a, ev[(size_t)k], ev[(size_t)k + 1]);
+    s += a;
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (err != cudaSuccess) return cuda_err(err, "lb_step_timed");
-  ms[0] = s[0] / (double)nsteps;  // phase field
-  ms[1] = s[2] / (double)nsteps;  // fused step
-  ms[2] = s[1] / (double)nsteps;  // near-contact scan
+  *ms = s / (double)nsteps;
   return LB_OK;
 }
-
-int lb_set_nc_tile(lb_handle* h, int variant) {
-  if (!h) return set_err(LB_EINVAL, "null handle");
-  if (variant < 0 || variant >= NUM_NC_VARIANTS) return set_err(LB_EINVAL, "near-contact tile index out of range");
-  if (variant != h->nc_tile) drop_graphs(h);
-  h->nc_tile = variant;
-  return LB_OK;
-}
-
-int lb_get_nc_tile(const lb_handle* h) { return h ? h->nc_tile : -1; }
 
 int lb_set_tile(lb_handle* h, int tile) {
   if (!h) return set_err(LB_EINVAL, "null handle");
@@ -633,12 +630,9 @@ int lb_get_populations(lb_handle* h, int32_t x0, int32_t y0, int32_t z0, int32_t
   const size_t M = (size_t)bx * by * bz;
   double* d = (double*)dev_alloc(h, 2 * (size_t)Q * M * sizeof(double));
   if (!d) return set_err(LB_ENOMEM, "export buffer allocation failed");
-  cudaError_t e = cudaSuccess;
-  if (h->mode == 1) e = launch_phi(h->storage, h->g, h->S[h->cur], h->phi, h->stream);
-  if (e == cudaSuccess)
-    e = launch_export(h->storage, h->mode == 0 ? LOAD_FIELDS : LOAD_PULL, h->g, h->p, h->S[h->cur], init_buf(h), x0,
+  cudaError_t e = launch_export(h->storage, h->mode == 0 ? LOAD_FIELDS : LOAD_PULL, h->g, h->p, h->S[h->cur], init_buf(h), x0,
                       y0, z0, bx, by, bz, d, d + (size_t)Q * M, h->stream);
-  g_launches += 2;
+  g_launches += 1;
   if (e == cudaSuccess) e = cudaMemcpyAsync(fA, d, (size_t)Q * M * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(fB, d + (size_t)Q * M, (size_t)Q * M * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -798,8 +792,10 @@ int lb_load(lb_handle* h, const char* path) {
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(s.sv, buf.data() + fb, N * sizeof(float4), cudaMemcpyHostToDevice, h->stream);
     }
+    if (e == cudaSuccess) e = rebuild_acc(h);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_err(e, "checkpoint upload");
+    drop_graphs(h);
     h->mode = 1;
   } else {
     int32_t flags[2];
@@ -836,6 +832,7 @@ int lb_copy_state(lb_handle* dst, lb_handle* src) {
       e = cudaMemcpyAsync(b.f, a.f, fb, cudaMemcpyDeviceToDevice, dst->stream);
       if (e == cudaSuccess) e = cudaMemcpyAsync(b.sv, a.sv, N * sizeof(float4), cudaMemcpyDeviceToDevice, dst->stream);
     }
+    if (e == cudaSuccess) e = rebuild_acc(dst);
   } else if (e == cudaSuccess) {
     e = cudaMemcpyAsync(dst->init_phi, src->init_phi, N * sizeof(float), cudaMemcpyDeviceToDevice, dst->stream);
     if (e == cudaSuccess && src->use_rho) {
@@ -849,8 +846,10 @@ int lb_copy_state(lb_handle* dst, lb_handle* src) {
       e = cudaMemcpyAsync(dst->init_u, src->init_u, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, dst->stream);
     }
     if (e == cudaSuccess) e = launch_phi_from_init(dst->storage, dst->g, dst->init_phi, dst->phi, dst->stream);
+    if (e == cudaSuccess) e = reset_acc(dst);
   }
   if (e != cudaSuccess) return cuda_err(e, "copy state");
+  drop_graphs(dst);
   dst->mode = src->mode;
   dst->use_rho = src->use_rho;
   dst->use_u = src->use_u;
@@ -872,21 +871,21 @@ struct lb_batch {
   cudaStream_t own_stream = nullptr;
   RunDesc* d_runs = nullptr;
   std::vector<RunDesc> h_runs;
-  long long nchunks = 0, ntiles = 0, max_nodes = 0, total_nodes = 0;
-  int halo_max = 1;
+  long long ntiles = 0, max_nodes = 0, total_nodes = 0;
+  int halo = 1;  // largest staging halo of the runs
   int tile = 0;
   int blocks_per_sm = 2;
   bool dirty = true;
   uint64_t graph_launches = 0;  // kernel launches in one replay
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // [parity * 3 + phase]
 };
 
 namespace {
 
-constexpr int BATCH_STEPS_PER_GRAPH = 16;
+constexpr int BATCH_STEPS_PER_GRAPH = 12;  // a multiple of 2 and 3, as STEPS_PER_GRAPH
 
 void batch_drop_graphs(lb_batch* b) {
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 6; ++k) {
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
     b->graph[k] = nullptr;
   }
@@ -894,8 +893,8 @@ void batch_drop_graphs(lb_batch* b) {
 
 int batch_descriptors(lb_batch* b) {
   const Tile& T = kTiles[b->tile];
-  long long tb = 0, cb = 0;
-  b->halo_max = 1;
+  long long tb = 0;
+  b->halo = 1;
   b->max_nodes = 0;
   b->h_runs.resize(b->runs.size());
   for (size_t r = 0; r < b->runs.size(); ++r) {
@@ -905,20 +904,16 @@ int batch_descriptors(lb_batch* b) {
     d.p = h->p;
     d.S[0] = h->S[0];
     d.S[1] = h->S[1];
-    d.phi = h->phi;
-    d.hnc = h->hnc;
+    for (int k = 0; k < 3; ++k) d.acc[k] = h->acc[k];
     d.tiles_x = (h->g.nx + T.tx - 1) / T.tx;
     d.tiles_y = (h->g.ny + T.ty - 1) / T.ty;
     d.tiles_z = (h->g.nz + T.tz - 1) / T.tz;
     d.tile_begin = tb;
-    d.chunk_begin = cb;
     tb += (long long)d.tiles_x * d.tiles_y * d.tiles_z;
-    cb += (h->g.N + 255) / 256;
-    b->halo_max = std::max(b->halo_max, h->p.halo);
+    b->halo = std::max(b->halo, stage_halo(h->p));
     b->max_nodes = std::max(b->max_nodes, h->g.N);
   }
   b->ntiles = tb;
-  b->nchunks = cb;
   LB_CUDA(cudaMemcpyAsync(b->d_runs, b->h_runs.data(), sizeof(RunDesc) * b->h_runs.size(), cudaMemcpyHostToDevice,
                           b->stream));
   LB_CUDA(cudaStreamSynchronize(b->stream));
@@ -926,19 +921,20 @@ int batch_descriptors(lb_batch* b) {
   return LB_OK;
 }
 
-int batch_issue(lb_batch* b, int parity) {
-  LB_CUDA(launch_batched(b->storage, b->d_runs, (int)b->runs.size(), b->nchunks, b->ntiles, b->tile, b->halo_max,
-                         b->max_nodes, parity, b->blocks_per_sm, b->runs[0]->status, b->stream));
-  g_launches += b->halo_max > 1 ? 3 : 2;
+// one batched step from lattice parity `parity` and accumulator phase k
+int batch_issue(lb_batch* b, int parity, int k) {
+  LB_CUDA(launch_batched(b->storage, b->d_runs, (int)b->runs.size(), b->ntiles, b->tile, b->halo, b->max_nodes,
+                         parity, k, b->blocks_per_sm, b->runs[0]->status, b->stream));
+  g_launches += 1;
   return LB_OK;
 }
 
-int batch_build_graph(lb_batch* b, int parity) {
+int batch_build_graph(lb_batch* b, int parity, int phase) {
   cudaGraph_t graph = nullptr;
   const uint64_t save_l = g_launches.load();
   LB_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   int rc = LB_OK;
-  for (int k = 0; k < BATCH_STEPS_PER_GRAPH && rc == LB_OK; ++k) rc = batch_issue(b, parity ^ (k & 1));
+  for (int k = 0; k < BATCH_STEPS_PER_GRAPH && rc == LB_OK; ++k) rc = batch_issue(b, parity ^ (k & 1), (phase + k) % 3);
   cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
   b->graph_launches = g_launches.load() - save_l;
   g_launches = save_l;
@@ -947,12 +943,13 @@ int batch_build_graph(lb_batch* b, int parity) {
     return rc;
   }
   if (e != cudaSuccess) return cuda_err(e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&b->graph[parity], graph, 0);
+  e = cudaGraphInstantiate(&b->graph[parity * 3 + phase], graph, 0);
   cudaGraphDestroy(graph);
   return cuda_err(e, "cudaGraphInstantiate");
 }
 
-// bring every run to the population state and a common parity
+// bring every run to the population state, a common parity and a common
+// accumulator phase (the accumulators of a run are renamed, not copied)
 int batch_prepare(lb_batch* b) {
   for (lb_handle* h : b->runs) {
     if (!h->initialised) return set_err(LB_ESTATE, "a run of the batch is not initialised");
@@ -961,9 +958,18 @@ int batch_prepare(lb_batch* b) {
       if (rc) return rc;
     }
   }
-  const int par = b->runs[0]->cur;
-  for (lb_handle* h : b->runs)
+  const int par = b->runs[0]->cur, k0 = b->runs[0]->phi_acc;
+  for (lb_handle* h : b->runs) {
     if (h->cur != par) return set_err(LB_ESTATE, "runs of the batch are at different parities");
+    if (h->phi_acc != k0) {
+      unsigned long long* old[3] = {h->acc[0], h->acc[1], h->acc[2]};
+      for (int j = 0; j < 3; ++j) h->acc[j] = old[(j - k0 + h->phi_acc + 3) % 3];
+      h->phi_acc = k0;
+      drop_graphs(h);
+      b->dirty = true;
+      batch_drop_graphs(b);
+    }
+  }
   if (b->dirty) return batch_descriptors(b);
   return LB_OK;
 }
@@ -972,6 +978,7 @@ void batch_advance(lb_batch* b, int64_t n) {
   for (lb_handle* h : b->runs) {
     h->t += n;
     h->cur ^= (int)(n & 1);
+    h->phi_acc = (int)((h->phi_acc + n) % 3);
   }
 }
 
@@ -990,7 +997,7 @@ std::string batch_key(const lb_batch* b) {
   std::vector<std::string> shapes;
   for (lb_handle* h : b->runs) {
     std::ostringstream os;
-    os << h->g.nx << "x" << h->g.ny << "x" << h->g.nz << "w" << h->grid.walls << "h" << h->p.halo;
+    os << h->g.nx << "x" << h->g.ny << "x" << h->g.nz << "w" << h->grid.walls << "h" << stage_halo(h->p);
     shapes.push_back(os.str());
   }
   std::sort(shapes.begin(), shapes.end());
@@ -1113,15 +1120,15 @@ int lb_batch_step(lb_batch* b, int64_t nsteps) {
     --nsteps;
   }
   while (nsteps >= BATCH_STEPS_PER_GRAPH) {
-    const int par = b->runs[0]->cur;
-    if (!b->graph[par] && (rc = batch_build_graph(b, par))) return rc;
-    LB_CUDA(cudaGraphLaunch(b->graph[par], b->stream));
+    const int par = b->runs[0]->cur, ph = b->runs[0]->phi_acc, key = par * 3 + ph;
+    if (!b->graph[key] && (rc = batch_build_graph(b, par, ph))) return rc;
+    LB_CUDA(cudaGraphLaunch(b->graph[key], b->stream));
     g_launches += b->graph_launches;
     batch_advance(b, BATCH_STEPS_PER_GRAPH);
     nsteps -= BATCH_STEPS_PER_GRAPH;
   }
   while (nsteps-- > 0) {
-    if ((rc = batch_issue(b, b->runs[0]->cur))) return rc;
+    if ((rc = batch_issue(b, b->runs[0]->cur, b->runs[0]->phi_acc))) return rc;
     batch_advance(b, 1);
   }
   return LB_OK;
@@ -1154,6 +1161,7 @@ int lb_batch_autotune(lb_batch* b, int32_t steps, int use_cache, double* result)
   // the timed steps advanced the runs: return every run to its initial state
   for (lb_handle* h : b->runs) {
     cudaError_t e = launch_phi_from_init(h->storage, h->g, h->init_phi, h->phi, h->stream);
+    if (e == cudaSuccess) e = reset_acc(h);
     g_launches += 1;
     if (e != cudaSuccess && rc == LB_OK) rc = cuda_err(e, "autotune reset");
     h->mode = 0;
@@ -1199,12 +1207,12 @@ int batch_tune(lb_batch* b, int32_t steps, int use_cache, double* result) {
     for (int bps : bps_opts) {
       if ((rc = lb_batch_set_tile(b, tile, bps)) || (rc = batch_prepare(b))) break;
       for (int k = 0; k < 2 && rc == LB_OK; ++k) {
-        rc = batch_issue(b, b->runs[0]->cur);
+        rc = batch_issue(b, b->runs[0]->cur, b->runs[0]->phi_acc);
         batch_advance(b, 1);
       }
       cudaEventRecord(e0, b->stream);
       for (int k = 0; k < steps && rc == LB_OK; ++k) {
-        rc = batch_issue(b, b->runs[0]->cur);
+        rc = batch_issue(b, b->runs[0]->cur, b->runs[0]->phi_acc);
         batch_advance(b, 1);
       }
       cudaEventRecord(e1, b->stream);

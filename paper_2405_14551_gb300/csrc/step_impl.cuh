@@ -1,25 +1,37 @@
 #pragma once
-// Device code of the fused time step of the two-component colour-gradient LB scheme on D3Q27
+// Device code of the time step of the two-component colour-gradient LB scheme on D3Q27
 // (arXiv 2405.14551, Sec. III.B-III.D) for sm_103a.
 //
-// A step is three passes over the lattice:
-//   1. k_phi: pull the populations of every node and write its phase field
-//      phi = (rhoA - rhoB)/(rhoA + rhoB) (Eq. order_param) to a side array.
-//      The colour gradient and the near-contact scan of a node need phi of
-//      the current time level up to h_max + 1 nodes away, which exists only
-//      after every neighbour has been pulled; this pass provides it.
-//   2. k_nc (only with near contact, A_h != 0): per CTA a tile of phi plus a
-//      halo of K + 1 nodes in shared memory; every interface node scans along
-//      its outward normal (Eqs. stress_jump, near_cont_force) and the found
-//      distance h (0: none) is written as one byte per node.
-//   3. k_step: per CTA a tile of (TX x TY x TZ) nodes stages phi of the tile
-//      plus a one-node halo in shared memory; every thread then pulls the 27
-//      (x2) populations of its node (periodic wrap, halfway bounce-back at
-//      solid neighbours, Sec. III.D), takes the moments, the colour gradient
-//      from the tile, the repulsion from h, forms the Guo-shifted velocity,
-//      relaxes the total populations (BGK), adds the perturbation Omega^(2)
-//      and the forcing source, recolours (Eqs. ome3_1/2) and stores the
-//      post-collision state once.
+// A step is one kernel, k_step, over CTA tiles of TX x TY x TZ nodes (TX x TY
+// threads, TZ nodes per thread):
+//   1. stage phi(t) of the tile plus a halo of H nodes in shared memory.  phi
+//      is not stored between steps as an array of its own: the step before
+//      accumulated the component densities rhoA, rhoB of every node on the
+//      write side (item 4), and the staging decodes
+//      phi = (rhoA - rhoB)/(rhoA + rhoB) (Eq. order_param) from them;
+//   2. with near contact (A_h != 0, halo H > K): every interface node of the
+//      tile scans along its outward normal (Eqs. stress_jump,
+//      near_cont_force); the distance h stays in shared memory;
+//   3. every thread pulls the 27 (x2) populations of its nodes (periodic
+//      wrap, halfway bounce-back at solid neighbours, Sec. III.D), takes the
+//      moments, the colour gradient from the staged tile, the repulsion from
+//      h, the Guo-shifted velocity, relaxes the total populations (BGK), adds
+//      the perturbation Omega^(2) and the forcing source, recolours (Eqs.
+//      ome3_1/2) and stores the post-collision state once;
+//   4. each post-collision component population f*^k_i(x) is also what the
+//      node x + c_i pulls at the next step (x itself, as direction opp(i),
+//      when x + c_i is solid), so it is x's contribution to rho_k there.  The
+//      CTA sums the contributions over its tile plus a one-node ring in
+//      shared memory as fixed-point integers and adds the sums to a global
+//      accumulator with 64-bit integer atomics.  Integer sums are exact, so
+//      phi(t+1) does not depend on the order of the additions (tile shape,
+//      CTA schedule, batching), and it equals what a pull of the stored
+//      populations gives (k_phi_acc rebuilds it that way after a load).
+// The accumulators rotate over three buffers: a step reads phi(t) from one,
+// adds phi(t+1) into the next (zeroed by the step before) and zeroes its own
+// nodes of the third (read by the step before and not read again).  The
+// populations are read and written once per step; the accumulators add 8 B
+// read, 16 B atomically updated and 8 B zeroed per node (FP32 storages).
 // Populations are structure-of-arrays [dir][z][y][x]: for a fixed direction
 // consecutive threads read consecutive addresses (coalesced).
 #include <cstdio>
@@ -117,34 +129,46 @@ __device__ __forceinline__ typename Store<ST>::E encode(typename Store<ST>::R v,
   }
 }
 
+// Rounded products without contraction: the sending and the pulling node
+// must form the same component populations bit for bit (see colour_split).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Moment storage (Sec. IV.C, Eq. eq:llb-pull): f*_i = w_i (alpha + beta.c +
+// c.Gamma.c) of a node's coefficients at c = c_i, or at c = -c_i when bb
+// (bounce-back from the node itself, dir = opp(i)).  Only the coefficients
+// that c_i touches enter; the products with c components are exact (+-1).
+template <typename R>
+__device__ __forceinline__ R eval_moment(const float4& qa, const float4& qb, const float2& qc, int i, bool bb) {
+  R lin = R(0), quad = R(0);
+  if (cx(i)) lin += R(cx(i)) * qa.y;
+  if (cy(i)) lin += R(cy(i)) * qa.z;
+  if (cz(i)) lin += R(cz(i)) * qa.w;
+  if (cx(i)) quad += qb.x;
+  if (cy(i)) quad += qb.y;
+  if (cz(i)) quad += qb.z;
+  if (cx(i) && cy(i)) quad += R(cx(i) * cy(i)) * qb.w;
+  if (cx(i) && cz(i)) quad += R(cx(i) * cz(i)) * qc.x;
+  if (cy(i) && cz(i)) quad += R(cy(i) * cz(i)) * qc.y;
+  return mul_rn(wgt<R>(i), qa.x + quad + (bb ? -lin : lin));
+}
+
 // Stored post-collision total population f*_dir of node src (single set
-// storages).  Reduced: the stored value.  Moment storage (Sec. IV.C, Eq.
-// eq:llb-pull): w_i (alpha + beta.c + c.Gamma.c) of the node's coefficients at
-// c = c_i, or at c = -c_i = c_opp(i) when bb (bounce-back from the node
-// itself, dir = opp(i)); only the coefficients that c_i touches are read.
+// storages).  Reduced: the stored value.  Moment storage: the node's
+// quadratic form (eval_moment); only the records that c_i touches are read.
 template <int ST, typename I>
 __device__ __forceinline__ typename Store<ST>::R load_fs(const typename Store<ST>::E* __restrict__ f, I N, I dir, I src,
                                                          int i, bool bb) {
   using R = typename Store<ST>::R;
   if constexpr (Store<ST>::MOMENT) {
     const float4 qa = reinterpret_cast<const float4*>(f)[src];
-    R lin = R(0), quad = R(0);
-    if (cx(i)) lin += R(cx(i)) * qa.y;
-    if (cy(i)) lin += R(cy(i)) * qa.z;
-    if (cz(i)) lin += R(cz(i)) * qa.w;
-    if (cx(i) || cy(i) || cz(i)) {
-      const float4 qb = reinterpret_cast<const float4*>(f + (I)4 * N)[src];
-      if (cx(i)) quad += qb.x;
-      if (cy(i)) quad += qb.y;
-      if (cz(i)) quad += qb.z;
-      if (cx(i) && cy(i)) quad += R(cx(i) * cy(i)) * qb.w;
-    }
-    if ((cx(i) && cz(i)) || (cy(i) && cz(i))) {
-      const float2 qc = reinterpret_cast<const float2*>(f + (I)8 * N)[src];
-      if (cx(i) && cz(i)) quad += R(cx(i) * cz(i)) * qc.x;
-      if (cy(i) && cz(i)) quad += R(cy(i) * cz(i)) * qc.y;
-    }
-    return wgt<R>(i) * (qa.x + quad + (bb ? -lin : lin));
+    float4 qb = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 qc = make_float2(0.f, 0.f);
+    if (cx(i) || cy(i) || cz(i)) qb = reinterpret_cast<const float4*>(f + (I)4 * N)[src];
+    if ((cx(i) && cz(i)) || (cy(i) && cz(i))) qc = reinterpret_cast<const float2*>(f + (I)8 * N)[src];
+    return eval_moment<R>(qa, qb, qc, i, bb);
   } else {
     return decode<ST>(f[dir * N + src], i);
   }
@@ -185,6 +209,19 @@ __device__ __forceinline__ bool is_solid(const Geo& g, int x, int y, int z) {
          (g.wz && (z == 0 || z == g.nz - 1));
 }
 
+__device__ __forceinline__ bool near_wall(const Geo& g, int x, int y, int z) {
+  return (g.wx && (x <= 1 || x >= g.nx - 2)) || (g.wy && (y <= 1 || y >= g.ny - 2)) ||
+         (g.wz && (z <= 1 || z >= g.nz - 2));
+}
+
+// Whether the box [x0 - d, x0 + TX - 1 + d] x ... (a tile and its halo of d
+// nodes) holds a solid layer or leaves the box on a walled axis.
+__device__ __forceinline__ bool region_walled(const Geo& g, int x0, int y0, int z0, int tx, int ty, int tz, int d) {
+  return (g.wx && (x0 - d <= 0 || x0 + tx - 1 + d >= g.nx - 1)) ||
+         (g.wy && (y0 - d <= 0 || y0 + ty - 1 + d >= g.ny - 1)) ||
+         (g.wz && (z0 - d <= 0 || z0 + tz - 1 + d >= g.nz - 1));
+}
+
 template <int ST>
 struct View {
   using E = typename Store<ST>::E;
@@ -198,6 +235,26 @@ __host__ __device__ __forceinline__ View<ST> view(const StateBuf& b) {
   v.f = reinterpret_cast<typename Store<ST>::E*>(b.f);
   v.sv = b.sv;
   return v;
+}
+
+// Component split of a single-set population as the pulling node rebuilds it
+// (recolouring, Eq. ome3_1, evaluated one step later): f^A_i = s f*_i +
+// w_i c_i.v/|c_i|, f^B_i = f*_i - f^A_i, with (s, v) the colour scalars of the
+// node that stored f*_i.  bb: bounce-back, the node's own f*_opp(i) pulled as
+// direction i, whose segregation term is the negative of direction i's.  The
+// rounding is explicit, so the sender of a value (step_nodes) and its puller
+// form the same f^A_i, f^B_i bit for bit.
+template <typename R, bool MAYBB>
+__device__ __forceinline__ void colour_split(R fs, const float4& sv, int i, bool bb, R& va, R& vb) {
+  R cv = R(0);
+  if (cx(i)) cv += R(cx(i)) * R(sv.y);
+  if (cy(i)) cv += R(cy(i)) * R(sv.z);
+  if (cz(i)) cv += R(cz(i)) * R(sv.w);
+  const R k = wgt<R>(i) * inv_norm<R>(i);  // folded to one constant per direction
+  R seg = mul_rn(k, cv);
+  if constexpr (MAYBB) seg = bb ? -seg : seg;
+  va = fma_rn(R(sv.x), fs, seg);
+  vb = fs - va;
 }
 
 // Pull the pre-collision populations of node `self` (streaming, Eq. eq:lbm):
@@ -219,32 +276,21 @@ __device__ __forceinline__ void pull_node(const View<ST>& S, const Geo& g, const
     const bool bb = n.sx[a] | n.sy[b] | n.sz[c];
     const long long src = bb ? self : (long long)n.xs[a] + (long long)g.nx * ((long long)n.ys[b] + (long long)g.ny * n.zs[c]);
     const int dir = bb ? opp(i) : i;
+    R va, vb;
     if constexpr (Store<ST>::TWOSET) {
-      const R va = decode<ST>(S.f[(size_t)dir * N + src], i);
-      const R vb = decode<ST>(S.f[(size_t)(Q + dir) * N + src], i);
+      va = decode<ST>(S.f[(size_t)dir * N + src], i);
+      vb = decode<ST>(S.f[(size_t)(Q + dir) * N + src], i);
       f[i] = va + vb;
-      rA += va;
-      rB += vb;
-      if constexpr (COMP) {
-        fa[i] = va;
-        fb[i] = vb;
-      }
     } else {
-      // single set: f^A_dir(src) = s f*_dir + w c_dir.v/|c_dir| (recolouring, Eq. ome3_1)
       const R fs = load_fs<ST, size_t>(S.f, N, (size_t)dir, (size_t)src, i, bb);
-      const float4 sv = S.sv[src];
-      const R s = sv.x;
-      const R cv = R(cx(i)) * R(sv.y) + R(cy(i)) * R(sv.z) + R(cz(i)) * R(sv.w);
-      const R seg = (bb ? R(-1) : R(1)) * wgt<R>(i) * inv_norm<R>(i) * cv;
-      const R va = s * fs + seg;
-      const R vb = (R(1) - s) * fs - seg;
+      colour_split<R, true>(fs, S.sv[src], i, bb, va, vb);
       f[i] = fs;
-      rA += va;
-      rB += vb;
-      if constexpr (COMP) {
-        fa[i] = va;
-        fb[i] = vb;
-      }
+    }
+    rA += va;
+    rB += vb;
+    if constexpr (COMP) {
+      fa[i] = va;
+      fb[i] = vb;
     }
   }
 }
@@ -320,58 +366,15 @@ __device__ __forceinline__ void fields_node(const InitBuf& I, const Geo& g, cons
   }
 }
 
-// ---------------------------------------------------------------------------
-// pass 1: phase field
-// ---------------------------------------------------------------------------
-// pull_fast is defined with the fused step below
+// Pull for the hot path: totals f_i and component densities.  WALLFREE: no
+// neighbour of the node is solid (no bounce-back test).  IDX32: every
+// population offset fits in 32 bits.  TOTALS (single-set storages): only the
+// totals f_i; the neighbours' colour scalars are not read and rA, rB are left
+// to the caller.
 template <int ST, bool WALLFREE, bool IDX32, bool TOTALS>
 __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const Nbr& n, int self,
                                           typename Store<ST>::R f[Q], typename Store<ST>::R& rA,
-                                          typename Store<ST>::R& rB);
-
-__device__ __forceinline__ bool near_wall(const Geo& g, int x, int y, int z) {
-  return (g.wx && (x <= 1 || x >= g.nx - 2)) || (g.wy && (y <= 1 || y >= g.ny - 2)) ||
-         (g.wz && (z <= 1 || z >= g.nz - 2));
-}
-
-// phase field of one node from its pulled populations
-template <int ST, bool IDX32>
-__device__ __forceinline__ void phi_node(const View<ST>& S, const Geo& g, long long idx,
-                                         typename Store<ST>::R* __restrict__ phi) {
-  using R = typename Store<ST>::R;
-  const int x = (int)(idx % g.nx);
-  const long long yz = idx / g.nx;
-  const int y = (int)(yz % g.ny);
-  const int z = (int)(yz / g.ny);
-  if (is_solid(g, x, y, z)) {
-    phi[idx] = R(0);
-    return;
-  }
-  Nbr n;
-  make_nbr(g, x, y, z, n);
-  R f[Q], rA, rB;
-  if (near_wall(g, x, y, z))
-    pull_fast<ST, false, IDX32, false>(S, g, n, (int)idx, f, rA, rB);
-  else
-    pull_fast<ST, true, IDX32, false>(S, g, n, (int)idx, f, rA, rB);
-  phi[idx] = (rA - rB) / (rA + rB);
-}
-
-template <int ST, bool IDX32>
-__global__ void __launch_bounds__(256) k_phi(View<ST> S, Geo g, typename Store<ST>::R* __restrict__ phi) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride)
-    phi_node<ST, IDX32>(S, g, idx, phi);
-}
-
-// Reduced storage: the same pass over CTA tiles.  Every node combines the
-// colour scalars (s, v) of its 27 source nodes; the tile's scalars plus a
-// one-node halo are staged in shared memory once, so those reads leave the
-// L1/L2 path.  Same arithmetic in the same order as phi_node.
-template <int ST, bool WALLFREE, bool IDX32>
-__device__ __forceinline__ void pull_reduced_tile(const View<ST>& S, const Geo& g, const Nbr& n, int self,
-                                                  const float4* svt, int cl, int SX, int SXY,
-                                                  typename Store<ST>::R& rA, typename Store<ST>::R& rB) {
+                                          typename Store<ST>::R& rB) {
   using R = typename Store<ST>::R;
   using I = typename std::conditional<IDX32, unsigned, size_t>::type;
   const I N = (I)g.N;
@@ -386,84 +389,323 @@ __device__ __forceinline__ void pull_reduced_tile(const View<ST>& S, const Geo& 
   for (int i = 0; i < Q; ++i) {
     const int a = 1 - cx(i), b = 1 - cy(i), c = 1 - cz(i);
     int src = n.xs[a] + rb[b][c];
-    int sl = cl - cx(i) - SX * cy(i) - SXY * cz(i);
     I dir = (I)i;
     bool bb = false;
     if constexpr (!WALLFREE) {
       bb = n.sx[a] | n.sy[b] | n.sz[c];
       src = bb ? self : src;
-      sl = bb ? cl : sl;
       dir = bb ? (I)opp(i) : dir;
     }
-    const R fs = load_fs<ST, I>(S.f, N, dir, (I)src, i, bb);
-    const float4 sv = svt[sl];
-    const R s = sv.x;
-    R cv = R(0);
-    if (cx(i)) cv += R(cx(i)) * R(sv.y);
-    if (cy(i)) cv += R(cy(i)) * R(sv.z);
-    if (cz(i)) cv += R(cz(i)) * R(sv.w);
-    R seg = wgt<R>(i) * inv_norm<R>(i) * cv;
-    if constexpr (!WALLFREE) seg = bb ? -seg : seg;
-    const R va = s * fs + seg;
-    rA += va;
-    rB += (fs - va);
-  }
-}
-
-template <int ST, int TX, int TY, int TZ, bool IDX32>
-__global__ void __launch_bounds__(TX* TY) k_phi_tiled(View<ST> S, Geo g, typename Store<ST>::R* __restrict__ phi) {
-  using R = typename Store<ST>::R;
-  extern __shared__ __align__(16) float4 svt[];
-  constexpr int SX = TX + 2, SY = TY + 2, SZ = TZ + 2, SXY = SX * SY;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-  // stage (s, v) of the tile + halo: periodic axes wrap; beyond a wall the
-  // entry is never read (a solid source is replaced by the node itself)
-  for (int row = threadIdx.y; row < SY * SZ; row += TY) {
-    const int ly = row % SY, lz = row / SY;
-    int gy = y0 - 1 + ly, gz = z0 - 1 + lz;
-    bool out = false;
-    if ((unsigned)gy >= (unsigned)g.ny) {
-      if (g.wy) out = true;
-      else gy = ((gy % g.ny) + g.ny) % g.ny;
+    if constexpr (Store<ST>::TWOSET) {
+      const R va = decode<ST>(S.f[dir * N + (I)src], i);
+      const R vb = decode<ST>(S.f[((I)Q + dir) * N + (I)src], i);
+      f[i] = va + vb;
+      rA += va;
+      rB += vb;
+    } else if constexpr (TOTALS) {
+      f[i] = load_fs<ST, I>(S.f, N, dir, (I)src, i, bb);
+    } else {
+      const R fs = load_fs<ST, I>(S.f, N, dir, (I)src, i, bb);
+      R va, vb;
+      colour_split<R, !WALLFREE>(fs, S.sv[src], i, bb, va, vb);
+      f[i] = fs;
+      rA += va;
+      rB += vb;
     }
-    if ((unsigned)gz >= (unsigned)g.nz) {
-      if (g.wz) out = true;
-      else gz = ((gz % g.nz) + g.nz) % g.nz;
-    }
-    for (int lx = threadIdx.x; lx < SX; lx += TX) {
-      int gx = x0 - 1 + lx;
-      bool o = out;
-      if ((unsigned)gx >= (unsigned)g.nx) {
-        if (g.wx) o = true;
-        else gx = ((gx % g.nx) + g.nx) % g.nx;
-      }
-      svt[row * SX + lx] = o ? make_float4(0.f, 0.f, 0.f, 0.f)
-                             : S.sv[(size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * gz)];
-    }
-  }
-  __syncthreads();
-  for (int lz = 0; lz < TZ; ++lz) {
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
-    if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
-    const int self = x + g.nx * (y + g.ny * z);
-    if (is_solid(g, x, y, z)) {
-      phi[self] = R(0);
-      continue;
-    }
-    Nbr n;
-    make_nbr(g, x, y, z, n);
-    const int cl = (lz + 1) * SXY + (threadIdx.y + 1) * SX + (threadIdx.x + 1);
-    R rA, rB;
-    if (near_wall(g, x, y, z))
-      pull_reduced_tile<ST, false, IDX32>(S, g, n, self, svt, cl, SX, SXY, rA, rB);
-    else
-      pull_reduced_tile<ST, true, IDX32>(S, g, n, self, svt, cl, SX, SXY, rA, rB);
-    phi[self] = (rA - rB) / (rA + rB);
   }
 }
 
 // ---------------------------------------------------------------------------
-// passes 2 and 3: near-contact scan and fused step
+// write-side accumulation of the next time level's component densities
+// ---------------------------------------------------------------------------
+// Each contribution f*^k_i is rounded to a multiple of 2^-SHIFT and summed as
+// an integer.  FP32 storages: SHIFT = 28 (component sums within +-8, step
+// 3.7e-9, below the FP32 rounding of a density near 1), the two sums of a
+// node packed in one 64-bit word (rhoA in the high half, rhoB in the low
+// half, two's complement), so one atomic adds both.  FP64: SHIFT = 56 (sums
+// within +-128, step 1.4e-17), two 64-bit words per node.  RHO_MAX bounds the
+// density that the status check accepts, so that no sum leaves its range.
+template <typename R>
+struct Acc;
+template <>
+struct Acc<float> {
+  static constexpr int W = 1;  // 64-bit words per node
+  using S = int;               // shared-memory partial sum of one component
+  static constexpr float RHO_MAX = 4.0f;
+  __device__ static __forceinline__ S q(float v) { return __float2int_rn(v * 268435456.0f); }
+  __device__ static __forceinline__ void add_shared(S* p, S v) { atomicAdd(p, v); }
+  __device__ static __forceinline__ unsigned long long pack(S a, S b) {
+    return ((unsigned long long)(unsigned)a << 32) + (unsigned long long)(long long)b;
+  }
+  // add the partial sums (a, b) of one node; zero partials add nothing
+  __device__ static __forceinline__ void flush(unsigned long long* acc, size_t node, S a, S b) {
+    const unsigned long long w = pack(a, b);
+    if (w) atomicAdd(acc + node, w);
+  }
+  __device__ static __forceinline__ void store(unsigned long long* acc, size_t node, S a, S b) {
+    acc[node] = pack(a, b);
+  }
+  __device__ static __forceinline__ void zero(unsigned long long* acc, size_t node) { acc[node] = 0ull; }
+  // phi = (rhoA - rhoB)/(rhoA + rhoB) of one packed word.  The halves are
+  // rhoA and rhoB in units of 2^-28; with densities below RHO_MAX (< 2^30
+  // units) the difference and the sum are exact 32-bit integers, each rounded
+  // once to FP32, and the quotient is taken with the fast reciprocal (about 2
+  // ulp; every stage of phi uses this one function, so results are
+  // reproducible).  phi feeds the colour gradient and the near-contact scan
+  // only; the component densities come from the sums themselves (densities).
+  __device__ static __forceinline__ float phi_word(unsigned long long w) {
+    const int lo = (int)(unsigned)w;
+    const int hi = (int)(unsigned)(w >> 32) + (int)((unsigned)lo >> 31);  // undo the borrow of a negative low half
+    return __fdividef((float)(hi - lo), (float)(hi + lo));
+  }
+  __device__ static __forceinline__ float phi(const unsigned long long* acc, size_t node) {
+    return phi_word(acc[node]);
+  }
+  // rhoA and rhoB of a node, each rounded once
+  __device__ static __forceinline__ void densities(const unsigned long long* acc, size_t node, float& a, float& b) {
+    const unsigned long long w = acc[node];
+    const int lo = (int)(unsigned)w;
+    const int hi = (int)(unsigned)(w >> 32) + (int)((unsigned)lo >> 31);
+    a = (float)hi * (1.0f / 268435456.0f);
+    b = (float)lo * (1.0f / 268435456.0f);
+  }
+};
+template <>
+struct Acc<double> {
+  static constexpr int W = 2;
+  using S = long long;
+  static constexpr double RHO_MAX = 64.0;
+  __device__ static __forceinline__ S q(double v) { return __double2ll_rn(v * 72057594037927936.0); }
+  __device__ static __forceinline__ void add_shared(S* p, S v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+  }
+  __device__ static __forceinline__ void flush(unsigned long long* acc, size_t node, S a, S b) {
+    if (a) atomicAdd(acc + 2 * node, (unsigned long long)a);
+    if (b) atomicAdd(acc + 2 * node + 1, (unsigned long long)b);
+  }
+  __device__ static __forceinline__ void store(unsigned long long* acc, size_t node, S a, S b) {
+    acc[2 * node] = (unsigned long long)a;
+    acc[2 * node + 1] = (unsigned long long)b;
+  }
+  __device__ static __forceinline__ void zero(unsigned long long* acc, size_t node) {
+    acc[2 * node] = 0ull;
+    acc[2 * node + 1] = 0ull;
+  }
+  __device__ static __forceinline__ double phi_words(unsigned long long wa, unsigned long long wb) {
+    const long long a = (long long)wa, b = (long long)wb;
+    return (double)(a - b) / (double)(a + b);
+  }
+  __device__ static __forceinline__ double phi(const unsigned long long* acc, size_t node) {
+    return phi_words(acc[2 * node], acc[2 * node + 1]);
+  }
+  __device__ static __forceinline__ void densities(const unsigned long long* acc, size_t node, double& a, double& b) {
+    a = (double)(long long)acc[2 * node] * (1.0 / 72057594037927936.0);
+    b = (double)(long long)acc[2 * node + 1] * (1.0 / 72057594037927936.0);
+  }
+};
+
+// The integer sums of the component populations a node pulls (the same
+// values, hence the same sums, as the senders accumulated).
+template <int ST, bool WALLFREE, bool IDX32>
+__device__ __forceinline__ void pull_acc(const View<ST>& S, const Geo& g, const Nbr& n, int self,
+                                         typename Acc<typename Store<ST>::R>::S& sa,
+                                         typename Acc<typename Store<ST>::R>::S& sb) {
+  using R = typename Store<ST>::R;
+  using A = Acc<R>;
+  using I = typename std::conditional<IDX32, unsigned, size_t>::type;
+  const I N = (I)g.N;
+  sa = 0;
+  sb = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int a = 1 - cx(i), b = 1 - cy(i), c = 1 - cz(i);
+    const bool bb = WALLFREE ? false : (n.sx[a] | n.sy[b] | n.sz[c]);
+    const I src = bb ? (I)self : (I)n.xs[a] + (I)g.nx * ((I)n.ys[b] + (I)g.ny * (I)n.zs[c]);
+    const I dir = bb ? (I)opp(i) : (I)i;
+    R va, vb;
+    if constexpr (Store<ST>::TWOSET) {
+      va = decode<ST>(S.f[dir * N + src], i);
+      vb = decode<ST>(S.f[((I)Q + dir) * N + src], i);
+    } else {
+      const R fs = load_fs<ST, I>(S.f, N, dir, src, i, bb);
+      colour_split<R, !WALLFREE>(fs, S.sv[src], i, bb, va, vb);
+    }
+    sa += A::q(va);
+    sb += A::q(vb);
+  }
+}
+
+// Rebuild the accumulator of the current time level from stored populations
+// (after a checkpoint load or a state copy): one node per thread.
+template <int ST, bool IDX32>
+__global__ void __launch_bounds__(256) k_phi_acc(View<ST> S, Geo g, unsigned long long* __restrict__ acc) {
+  using A = Acc<typename Store<ST>::R>;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
+    const int x = (int)(idx % g.nx);
+    const long long yz = idx / g.nx;
+    const int y = (int)(yz % g.ny);
+    const int z = (int)(yz / g.ny);
+    if (is_solid(g, x, y, z)) {
+      A::zero(acc, (size_t)idx);
+      continue;
+    }
+    Nbr n;
+    make_nbr(g, x, y, z, n);
+    typename A::S sa, sb;
+    if (near_wall(g, x, y, z))
+      pull_acc<ST, false, IDX32>(S, g, n, (int)idx, sa, sb);
+    else
+      pull_acc<ST, true, IDX32>(S, g, n, (int)idx, sa, sb);
+    A::store(acc, (size_t)idx, sa, sb);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory layout of a tile
+// ---------------------------------------------------------------------------
+// phi of the tile plus a halo of H nodes (HX along x: 1 without near
+// contact, else H rounded up to a multiple of 4 so that rows start on 16-byte
+// vectors), the component partial sums over the tile plus a one-node ring,
+// and with near contact the scan queue, the distance h of each tile node and
+// the queue counter.
+constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+
+template <typename R, int TX, int TY, int TZ, int H>
+struct Layout {
+  static constexpr int HX = H == 1 ? 1 : (H + 3) / 4 * 4;
+  static constexpr int SX = TX + 2 * HX, SY = TY + 2 * H, SZ = TZ + 2 * H, SXY = SX * SY, NS = SXY * SZ;
+  static constexpr int EX = TX + 2, EY = TY + 2, EZ = TZ + 2, EXY = EX * EY, E = EXY * EZ;
+  static constexpr int NT = TX * TY * TZ;
+  using S = typename Acc<R>::S;
+  static constexpr size_t off_acc = align16(sizeof(R) * (size_t)NS);
+  static constexpr size_t off_queue = off_acc + align16(2 * sizeof(S) * (size_t)E);
+  static constexpr size_t off_h = off_queue + (H > 1 ? align16(2 * (size_t)NT) : 0);
+  static constexpr size_t off_count = off_h + (H > 1 ? align16((size_t)NT) : 0);
+  static constexpr size_t bytes = off_count + 16;
+};
+
+template <typename R, bool FROM_ACC>
+struct PhiLoad {
+  // nodes per 16-byte vector
+  static constexpr int V = FROM_ACC ? 16 / (8 * Acc<R>::W) : 16 / (int)sizeof(R);
+  using Raw = typename std::conditional<FROM_ACC, ulonglong2,
+                                        typename std::conditional<sizeof(R) == 4, float4, double2>::type>::type;
+  __device__ static __forceinline__ R one(const PhiSrc& s, size_t node) {
+    if constexpr (FROM_ACC) return Acc<R>::phi(s.acc, node);
+    else return reinterpret_cast<const R*>(s.phi)[node];
+  }
+  // the V consecutive nodes from `node` (a multiple of V) as one load ...
+  __device__ static __forceinline__ Raw ld(const PhiSrc& s, size_t node) {
+    if constexpr (FROM_ACC) return *reinterpret_cast<const ulonglong2*>(s.acc + Acc<R>::W * node);
+    else return *reinterpret_cast<const Raw*>(reinterpret_cast<const R*>(s.phi) + node);
+  }
+  // ... and their phi
+  __device__ static __forceinline__ void dec(const Raw& w, R* out) {
+    if constexpr (FROM_ACC) {
+      if constexpr (Acc<R>::W == 1) {
+        out[0] = Acc<float>::phi_word(w.x);
+        out[1] = Acc<float>::phi_word(w.y);
+      } else {
+        out[0] = Acc<double>::phi_words(w.x, w.y);
+      }
+    } else {
+      const R* r = reinterpret_cast<const R*>(&w);
+#pragma unroll
+      for (int j = 0; j < V; ++j) out[j] = r[j];
+    }
+  }
+};
+
+// Stage phi of the tile plus its halo (Layout) in shared memory; solid and
+// beyond-wall nodes get the marker PHI_SOLID, periodic axes wrap.  The block
+// is walked as one flat list (of 16-byte vectors when the rows allow it), so
+// no lane idles on a short row.  No barrier.
+template <typename R, bool FROM_ACC, int TX, int TY, int TZ, int H>
+__device__ __forceinline__ void stage_phi(const PhiSrc& src, const Geo& g, R* sp, int x0, int y0, int z0) {
+  using L = Layout<R, TX, TY, TZ, H>;
+  using PL = PhiLoad<R, FROM_ACC>;
+  constexpr int V = PL::V;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  if constexpr (H > 1) {
+    static_assert(L::HX % V == 0 && TX % V == 0, "vector staging needs whole vectors per row");
+  }
+  if (H > 1 && g.nx % V == 0) {
+    // every vector lies wholly inside or wholly outside the box along x; NB
+    // vectors per thread are loaded before any is decoded, so their latencies
+    // overlap
+    constexpr int QR = (H > 1 ? L::SX : V) / V, NQ = QR * L::SY * L::SZ, NB = 4;
+    using Raw = typename PL::Raw;
+    for (int q0 = tid; q0 < NQ; q0 += NB * TX * TY) {
+      Raw raw[NB];
+      int meta[NB];  // row * QR + qx, or -1 beyond the block
+      unsigned fill = 0;  // bit b: vector b is solid or beyond a wall (no load)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int q = q0 + b * TX * TY;
+        meta[b] = -1;
+        if (q >= NQ) continue;
+        meta[b] = q;
+        const int qx = q % QR, row = q / QR;
+        const int ly = row % L::SY, lz = row / L::SY;
+        int gy = y0 - H + ly, gz = z0 - H + lz;
+        bool rsolid = false;
+        if (g.wy) rsolid |= (gy <= 0 || gy >= g.ny - 1);
+        else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
+        if (g.wz) rsolid |= (gz <= 0 || gz >= g.nz - 1);
+        else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
+        const int gx0 = x0 - L::HX + qx * V;
+        bool inside = gx0 >= 0 && gx0 < g.nx;
+        int gxl = gx0;
+        if (!inside && !g.wx) {
+          gxl = ((gx0 % g.nx) + g.nx) % g.nx;
+          inside = true;
+        }
+        if (inside && !rsolid) raw[b] = PL::ld(src, (size_t)gxl + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * gz));
+        else fill |= 1u << b;
+        if (rsolid) fill |= 1u << (NB + b);
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        if (meta[b] < 0) continue;
+        const int qx = meta[b] % QR, row = meta[b] / QR;
+        R v[V];
+        if ((fill >> b) & 1u) {
+#pragma unroll
+          for (int j = 0; j < V; ++j) v[j] = R(PHI_SOLID);
+        } else {
+          PL::dec(raw[b], v);
+        }
+        const bool rsolid = (fill >> (NB + b)) & 1u;
+        const int gx0 = x0 - L::HX + qx * V;
+        R* dst = sp + (size_t)row * L::SX + qx * V;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const int xj = gx0 + j;
+          const bool solid = rsolid || (g.wx && (xj <= 0 || xj >= g.nx - 1));
+          dst[j] = solid ? R(PHI_SOLID) : v[j];
+        }
+      }
+    }
+  } else {
+    for (int q = tid; q < L::NS; q += TX * TY) {
+      const int lx = q % L::SX, row = q / L::SX;
+      const int ly = row % L::SY, lz = row / L::SY;
+      int gx = x0 - L::HX + lx, gy = y0 - H + ly, gz = z0 - H + lz;
+      bool solid = false;
+      if (g.wx) solid |= (gx <= 0 || gx >= g.nx - 1);
+      else if ((unsigned)gx >= (unsigned)g.nx) gx = ((gx % g.nx) + g.nx) % g.nx;
+      if (g.wy) solid |= (gy <= 0 || gy >= g.ny - 1);
+      else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
+      if (g.wz) solid |= (gz <= 0 || gz >= g.nz - 1);
+      else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
+      sp[q] = solid ? R(PHI_SOLID) : PL::one(src, (size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * gz));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// colour gradient and near-contact scan on the staged tile
 // ---------------------------------------------------------------------------
 // Colour gradient grad phi(p) = (1/cs2) sum_i w_i c_i phi(p + c_i) on the
 // shared tile; a solid neighbour contributes phi(p) (neutral wetting).  Tiles
@@ -514,166 +756,22 @@ __device__ __forceinline__ void tile_grad(const R* sp, int c, int SX, int SXY, R
   gr[2] = gz * k72;
 }
 
-// Pull for the hot path: totals f_i and component densities.  WALLFREE: no
-// neighbour of the node is solid (no bounce-back test).  IDX32: every
-// population offset fits in 32 bits.  TOTALS (reduced storage): only the
-// totals f_i; the neighbours' colour scalars are not read and rA, rB are left
-// to the caller.
-template <int ST, bool WALLFREE, bool IDX32, bool TOTALS>
-__device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const Nbr& n, int self,
-                                          typename Store<ST>::R f[Q], typename Store<ST>::R& rA,
-                                          typename Store<ST>::R& rB) {
-  using R = typename Store<ST>::R;
-  using I = typename std::conditional<IDX32, unsigned, size_t>::type;
-  const I N = (I)g.N;
-  int rb[3][3];
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) rb[b][c] = g.nx * (n.ys[b] + g.ny * n.zs[c]);
-  rA = R(0);
-  rB = R(0);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int a = 1 - cx(i), b = 1 - cy(i), c = 1 - cz(i);
-    int src = n.xs[a] + rb[b][c];
-    I dir = (I)i;
-    bool bb = false;
-    if constexpr (!WALLFREE) {
-      bb = n.sx[a] | n.sy[b] | n.sz[c];
-      src = bb ? self : src;
-      dir = bb ? (I)opp(i) : dir;
-    }
-    if constexpr (Store<ST>::TWOSET) {
-      const R va = decode<ST>(S.f[dir * N + (I)src], i);
-      const R vb = decode<ST>(S.f[((I)Q + dir) * N + (I)src], i);
-      f[i] = va + vb;
-      rA += va;
-      rB += vb;
-    } else if constexpr (TOTALS) {
-      f[i] = load_fs<ST, I>(S.f, N, dir, (I)src, i, bb);
-    } else {
-      const R fs = load_fs<ST, I>(S.f, N, dir, (I)src, i, bb);
-      const float4 sv = S.sv[src];
-      const R s = sv.x;
-      R cv = R(0);
-      if (cx(i)) cv += R(cx(i)) * R(sv.y);
-      if (cy(i)) cv += R(cy(i)) * R(sv.z);
-      if (cz(i)) cv += R(cz(i)) * R(sv.w);
-      R seg = wgt<R>(i) * inv_norm<R>(i) * cv;
-      if constexpr (!WALLFREE) seg = bb ? -seg : seg;
-      const R va = s * fs + seg;
-      f[i] = fs;
-      rA += va;
-      rB += (fs - va);
-    }
-  }
-}
-
-// Stage phi of a tile (TX x TY x SZ - 2H own nodes) plus a halo of HX nodes
-// along x and H along y and z in shared memory (row length TX + 2 HX), one
-// (y, z) row per thread row: solid and beyond-wall nodes get the marker
-// PHI_SOLID; periodic axes wrap.  Returns (to every thread) whether the
-// staged block holds no solid node.
-template <typename R, int TX, int TY>
-__device__ __forceinline__ bool stage_phi(const R* __restrict__ phi, const Geo& g, int HX, int H, int SZ, R* sp,
-                                          int x0, int y0, int z0) {
-  const int SX = TX + 2 * HX, SY = TY + 2 * H;
-  const int SXY = SX * SY;
-  bool any_solid = false;
-  for (int row = threadIdx.y; row < SY * SZ; row += TY) {
-    const int ly = row % SY, lz = row / SY;
-    int gy = y0 - H + ly, gz = z0 - H + lz;
-    bool rsolid = false;
-    if (g.wy) rsolid |= (gy <= 0 || gy >= g.ny - 1);
-    else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
-    if (g.wz) rsolid |= (gz <= 0 || gz >= g.nz - 1);
-    else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
-    const long long rbase = (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
-    R* srow = sp + (size_t)lz * SXY + (size_t)ly * SX;
-    for (int lx = threadIdx.x; lx < SX; lx += TX) {
-      int gx = x0 - HX + lx;
-      bool solid = rsolid;
-      if (g.wx) solid |= (gx <= 0 || gx >= g.nx - 1);
-      else if ((unsigned)gx >= (unsigned)g.nx) gx = ((gx % g.nx) + g.nx) % g.nx;
-      any_solid |= solid;
-      srow[lx] = solid ? R(PHI_SOLID) : phi[rbase + gx];
-    }
-  }
-  return !__syncthreads_or(any_solid);
-}
-
-// The same staging with 16-byte loads and stores, for a lattice whose rows
-// are whole 16-byte vectors (nx a multiple of V = 16 / sizeof(R)) and a tile
-// whose x halo HX and start x0 are multiples of V: every vector then lies
-// wholly inside or wholly outside the box along x.  The block is walked as
-// one flat list of vectors, so no lane idles on a short row remainder.
-template <typename R, int TX, int TY, int HX, int H, int SZ>
-__device__ __forceinline__ bool stage_phi_vec(const R* __restrict__ phi, const Geo& g, R* sp, int x0, int y0,
-                                              int z0) {
-  constexpr int V = 16 / sizeof(R);
-  static_assert(HX % V == 0 && TX % V == 0, "vector staging needs aligned rows");
-  constexpr int SX = TX + 2 * HX, SY = TY + 2 * H, QR = SX / V, NQ = QR * SY * SZ;
-  using VT = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
-  bool any_solid = false;
-  for (int q = threadIdx.y * TX + threadIdx.x; q < NQ; q += TX * TY) {
-    const int qx = q % QR, row = q / QR;
-    const int ly = row % SY, lz = row / SY;
-    int gy = y0 - H + ly, gz = z0 - H + lz;
-    bool rsolid = false;
-    if (g.wy) rsolid |= (gy <= 0 || gy >= g.ny - 1);
-    else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
-    if (g.wz) rsolid |= (gz <= 0 || gz >= g.nz - 1);
-    else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
-    const int gx0 = x0 - HX + qx * V;  // first x of the vector
-    R v[V];
-    bool vsolid[V];
-    bool inside = gx0 >= 0 && gx0 < g.nx;
-    int gxl = gx0;
-    if (!inside && !g.wx) {  // periodic wrap of a whole vector
-      gxl = ((gx0 % g.nx) + g.nx) % g.nx;
-      inside = true;
-    }
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      const int xj = gx0 + j;
-      vsolid[j] = rsolid || (g.wx && (xj <= 0 || xj >= g.nx - 1));
-    }
-    if (inside && !rsolid) {
-      const long long rbase = (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
-      const VT w = *reinterpret_cast<const VT*>(phi + rbase + gxl);
-      const R* wr = reinterpret_cast<const R*>(&w);
-#pragma unroll
-      for (int j = 0; j < V; ++j) v[j] = wr[j];
-    }
-    VT o;
-    R* orr = reinterpret_cast<R*>(&o);
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      orr[j] = vsolid[j] ? R(PHI_SOLID) : v[j];
-      any_solid |= vsolid[j];
-    }
-    *reinterpret_cast<VT*>(sp + (size_t)row * SX + qx * V) = o;
-  }
-  return !__syncthreads_or(any_solid);
-}
-
 // Near-contact scan of one interface node (Eqs. stress_jump, near_cont_force):
 // step along the outward normal n_out = -grad phi/|grad phi| by round(k n_out),
-// k = 1..K (K = H - 1); the first target that is an interface node
-// (|phi| < phi_I, |grad phi| >= NC_GRAD_MIN) with a normal antiparallel to
-// the node's own gives h = k; 0 when there is none.  The scan stops at a
-// wall layer.  sp is the phi tile with halo H, c the node's tile index, gr
-// and gg = |gr| its gradient.
-template <typename R, bool WALLFREE, int H, int SX, int SXY>
-__device__ __forceinline__ int nc_scan(const R* sp, int c, int x, int y, int z, const Geo& g, const Phys& P,
-                                       const R gr[3], R gg) {
+// k = 1..K; the first target that is an interface node (|phi| < phi_I,
+// |grad phi| >= NC_GRAD_MIN) with a normal antiparallel to the node's own
+// gives h = k; 0 when there is none.  The scan stops at a wall layer.  sp is
+// the phi tile with a halo of at least K + 1, c the node's tile index, gr and
+// gg = |gr| its gradient.
+template <typename R, bool WALLFREE>
+__device__ __forceinline__ int nc_scan(const R* sp, int c, int SX, int SXY, int K, int x, int y, int z, const Geo& g,
+                                       const Phys& P, const R gr[3], R gg) {
   const R phi_I = R(P.phi_I);
   const R inv = R(-1) / gg;
   const R no0 = gr[0] * inv, no1 = gr[1] * inv, no2 = gr[2] * inv;
 #pragma unroll 1
-  for (int k = 1; k < H; ++k) {
-    // |n_out| = 1, so |d| <= k <= K < H; the clamp also covers non-finite normals
+  for (int k = 1; k <= K; ++k) {
+    // |n_out| = 1, so |d| <= k <= K; the clamp also covers non-finite normals
     const int dx = max(-k, min(k, (int)round_(R(k) * no0)));
     const int dy = max(-k, min(k, (int)round_(R(k) * no1)));
     const int dz = max(-k, min(k, (int)round_(R(k) * no2)));
@@ -694,121 +792,83 @@ __device__ __forceinline__ int nc_scan(const R* sp, int c, int x, int y, int z, 
   return 0;
 }
 
-// Scan every queued interface node of the tile; threads take queue entries
-// in turn, so no lane idles on a bulk-phase node.
-template <typename R, int TX, int TY, int TZ, int H, int HX, bool WALLFREE>
-__device__ __forceinline__ void nc_queue(const R* sp, const unsigned short* queue, int n, const Geo& g, const Phys& P,
-                                         unsigned char* __restrict__ hout, int x0, int y0, int z0) {
-  constexpr int SX = TX + 2 * HX, SXY = SX * (TY + 2 * H);
-  for (int q = threadIdx.y * TX + threadIdx.x; q < n; q += TX * TY) {
-    const int o = queue[q];
-    const int lx = o % TX, ly = (o / TX) % TY, lz = o / (TX * TY);
-    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-    const int c = (lz + H) * SXY + (ly + H) * SX + (lx + HX);
-    R gr[3];
-    tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
-    const R gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-    int h = 0;
-    if (gg >= R(NC_GRAD_MIN)) h = nc_scan<R, WALLFREE, H, SX, SXY>(sp, c, x, y, z, g, P, gr, gg);
-    hout[x + g.nx * (y + g.ny * z)] = (unsigned char)h;
-  }
-}
-
-// x halo of the near-contact tile: H rounded up to whole 16-byte vectors.
-template <typename R, int H>
-__host__ __device__ constexpr int nc_halo_x() {
-  constexpr int V = 16 / (int)sizeof(R);
-  return (H + V - 1) / V * V;
-}
-
-// One tile of the near-contact pass (halo H = K + 1; HX along x): stage phi,
-// queue the tile's interface nodes (|phi| < phi_I; solid nodes hold PHI_SOLID
-// and are never queued) by warp-aggregated appends, write h = 0 for the
-// others, then scan the queue.  Ends with a barrier, so the caller may reuse
-// the shared memory.  Shared memory: phi tile, a 16-byte counter, TX*TY*TZ
-// queue slots.
-template <typename R, int TX, int TY, int TZ, int H>
-__device__ __forceinline__ void nc_tile(const R* __restrict__ phi, const Geo& g, const Phys& P,
-                                        unsigned char* __restrict__ hout, R* sp, int x0, int y0, int z0) {
-  constexpr int HX = nc_halo_x<R, H>();
-  constexpr int SX = TX + 2 * HX, SY = TY + 2 * H, SZ = TZ + 2 * H, SXY = SX * SY;
-  int* count = reinterpret_cast<int*>(sp + (size_t)SXY * SZ);
-  unsigned short* queue = reinterpret_cast<unsigned short*>(count + 4);
+// Near-contact distance of every node of the tile into hs (Layout::NT bytes,
+// 0 for nodes without a partner): queue the tile's interface nodes (|phi| <
+// phi_I; solid nodes hold PHI_SOLID and are never queued) by warp-aggregated
+// appends, then all threads take queue entries in turn, so no lane idles on a
+// bulk node.  The counter was cleared before the staging barrier.  Ends with
+// a barrier.
+template <typename R, int TX, int TY, int TZ, int H, bool WALLFREE>
+__device__ __forceinline__ void nc_tile(const R* sp, const Geo& g, const Phys& P, unsigned char* hs,
+                                        unsigned short* queue, int* count, int x0, int y0, int z0) {
+  using L = Layout<R, TX, TY, TZ, H>;
   const int tid = threadIdx.y * TX + threadIdx.x;
-  if (tid == 0) *count = 0;
-  // both stagings end with a barrier
-  const bool wallfree = (g.nx % (16 / (int)sizeof(R)) == 0)
-                            ? stage_phi_vec<R, TX, TY, HX, H, SZ>(phi, g, sp, x0, y0, z0)
-                            : stage_phi<R, TX, TY>(phi, g, HX, H, SZ, sp, x0, y0, z0);
   const int lane = tid & 31;
   const R phi_I = R(P.phi_I);
   for (int lz = 0; lz < TZ; ++lz) {
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
     const bool in = x < g.nx && y < g.ny && z < g.nz;
-    const int c = (lz + H) * SXY + (threadIdx.y + H) * SX + (threadIdx.x + HX);
+    const int o = (lz * TY + threadIdx.y) * TX + threadIdx.x;
+    const int c = (lz + H) * L::SXY + (threadIdx.y + H) * L::SX + (threadIdx.x + L::HX);
     const bool iface = in && fabs(sp[c]) < phi_I;
-    if (in && !iface) hout[x + g.nx * (y + g.ny * z)] = 0;
+    hs[o] = 0;
     const unsigned m = __ballot_sync(0xffffffffu, iface);
     if (m) {
       const int leader = __ffs(m) - 1;
       int base = 0;
       if (lane == leader) base = atomicAdd(count, __popc(m));
       base = __shfl_sync(0xffffffffu, base, leader);
-      if (iface) queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned short)((lz * TY + threadIdx.y) * TX + threadIdx.x);
+      if (iface) queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned short)o;
     }
   }
   __syncthreads();
   const int n = *count;
-  if (wallfree) nc_queue<R, TX, TY, TZ, H, HX, true>(sp, queue, n, g, P, hout, x0, y0, z0);
-  else nc_queue<R, TX, TY, TZ, H, HX, false>(sp, queue, n, g, P, hout, x0, y0, z0);
+  for (int q = tid; q < n; q += TX * TY) {
+    const int o = queue[q];
+    const int lx = o % TX, ly = (o / TX) % TY, lz = o / (TX * TY);
+    const int c = (lz + H) * L::SXY + (ly + H) * L::SX + (lx + L::HX);
+    R gr[3];
+    tile_grad<R, WALLFREE>(sp, c, L::SX, L::SXY, gr);
+    const R gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+    int h = 0;
+    if (gg >= R(NC_GRAD_MIN))
+      h = nc_scan<R, WALLFREE>(sp, c, L::SX, L::SXY, P.K, x0 + lx, y0 + ly, z0 + lz, g, P, gr, gg);
+    hs[o] = (unsigned char)h;
+  }
   __syncthreads();
 }
 
-// Shared memory of one near-contact tile with halo H (x halo rounded up to
-// whole 16-byte vectors).
-template <typename R>
-inline size_t nc_smem_bytes(int TX, int TY, int TZ, int H) {
-  const int V = 16 / (int)sizeof(R);
-  const int HX = (H + V - 1) / V * V;
-  return sizeof(R) * (size_t)(TX + 2 * HX) * (TY + 2 * H) * (TZ + 2 * H) + 16 + 2 * (size_t)TX * TY * TZ;
-}
-
-// Calls f with the near-contact halo H = K + 1 (2..7) as a compile-time
-// constant.
-template <typename F>
-__host__ __device__ __forceinline__ void with_halo(int halo, F&& f) {
-  switch (halo) {
-    case 2: f(std::integral_constant<int, 2>{}); break;
-    case 3: f(std::integral_constant<int, 3>{}); break;
-    case 4: f(std::integral_constant<int, 4>{}); break;
-    case 5: f(std::integral_constant<int, 5>{}); break;
-    case 6: f(std::integral_constant<int, 6>{}); break;
-    case 7: f(std::integral_constant<int, 7>{}); break;
-    default: break;
+// ---------------------------------------------------------------------------
+// the nodes of one tile
+// ---------------------------------------------------------------------------
+// Send the component populations (a, b) of direction i of the node at
+// accumulator index e0 to the node that pulls them: x + c_i, or the node
+// itself when x + c_i is solid (halfway bounce-back).
+template <typename R, bool WALLFREE, int EX, int EXY>
+__device__ __forceinline__ void send(typename Acc<R>::S* sa, typename Acc<R>::S* sb, int e0, const Nbr& n, int i, R a,
+                                     R b) {
+  int e = e0 + cx(i) + EX * cy(i) + EXY * cz(i);
+  if constexpr (!WALLFREE) {
+    if (n.sx[1 + cx(i)] | n.sy[1 + cy(i)] | n.sz[1 + cz(i)]) e = e0;
   }
+  Acc<R>::add_shared(sa + e, Acc<R>::q(a));
+  Acc<R>::add_shared(sb + e, Acc<R>::q(b));
 }
 
-// (templated on the storage format, not only on R, so that every translation
-// unit instantiates kernels of its own)
-template <int ST, int TX, int TY, int TZ, int H>
-__global__ void __launch_bounds__(TX* TY) k_nc(const typename Store<ST>::R* __restrict__ phi, Geo g, Phys P,
-                                               unsigned char* __restrict__ hout) {
-  using R = typename Store<ST>::R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  nc_tile<R, TX, TY, TZ, H>(phi, g, P, hout, reinterpret_cast<R*>(smem_raw), blockIdx.x * TX, blockIdx.y * TY,
-                            blockIdx.z * TZ);
-}
-
-// The nodes of one fused-step tile; sp holds phi of the tile with a one-node
-// halo, hnc the near-contact distance of every node (read when A_h != 0).
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32, bool REG>
+// Pull, collide, recolour and store every node of the tile; with WS also
+// send the post-collision component populations to the tile's partial sums.
+// sp holds phi of the tile and its halo (Layout), hs the near-contact
+// distance of each tile node (read when A_h != 0).
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, bool WALLFREE, bool IDX32, bool REG>
 __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O, const InitBuf& init, const Geo& g,
-                                           const Phys& P, const unsigned char* __restrict__ hnc,
+                                           const Phys& P, const unsigned char* hs,
                                            typename Store<ST>::R* __restrict__ fields,
-                                           unsigned* __restrict__ status, const typename Store<ST>::R* sp, int x0,
-                                           int y0, int z0) {
-  constexpr int SX = TX + 2, SXY = SX * (TY + 2);
+                                           unsigned* __restrict__ status, const typename Store<ST>::R* sp,
+                                           typename Acc<typename Store<ST>::R>::S* sa,
+                                           typename Acc<typename Store<ST>::R>::S* sb,
+                                           const unsigned long long* __restrict__ accin, int x0, int y0, int z0) {
   using R = typename Store<ST>::R;
+  using L = Layout<R, TX, TY, TZ, H>;
   using I = typename std::conditional<IDX32, unsigned, size_t>::type;
   const R tau_a = R(P.tau_a), tau_b = R(P.tau_b);
   const R A2 = R(P.A2), beta = R(P.beta), A_h = R(P.A_h);
@@ -828,21 +888,26 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
     Nbr n;
     make_nbr(g, x, y, z, n);
     R f[Q], rA, rB;
-    const int c = (lz + 1) * SXY + (threadIdx.y + 1) * SX + (threadIdx.x + 1);
+    const int c = (lz + H) * L::SXY + (threadIdx.y + H) * L::SX + (threadIdx.x + L::HX);
+    const int e0 = (lz + 1) * L::EXY + (threadIdx.y + 1) * L::EX + (threadIdx.x + 1);
     const R phx = sp[c];
     if constexpr (LOADER == LOAD_PULL) {
       if constexpr (Store<ST>::TWOSET) {
         pull_fast<ST, WALLFREE, IDX32, false>(S, g, n, self, f, rA, rB);
       } else {
-        // reduced state: the component densities follow from the total and
-        // this time level's phase field phi = (rhoA - rhoB)/rho (the tile),
-        // so the neighbours' colour scalars need not be read again
+        // single set: rhoA of the node is the sum the senders accumulated
+        // (what a pull of the rebuilt f^A_i gives), so the neighbours' colour
+        // scalars need not be read
         pull_fast<ST, WALLFREE, IDX32, true>(S, g, n, self, f, rA, rB);
         R rt = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) rt += f[i];
-        rA = R(0.5) * rt * (R(1) + phx);
-        rB = rt - rA;
+        if (accin) {
+          Acc<R>::densities(accin, (size_t)self, rA, rB);
+        } else {  // phi given as an array: split the pulled total by it
+          rA = R(0.5) * rt * (R(1) + phx);
+        }
+        rB = rt - rA;  // rho is the sum of the pulled totals, as for the momentum
       }
     } else {
       fields_node<R, false>(init, g, P, n, (long long)self, f, rA, rB, nullptr, nullptr);
@@ -860,14 +925,14 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       if (cz(p)) j2 += R(cz(p)) * d;
     }
 
-    // colour gradient from the tile; near-contact distance from the scan pass
+    // colour gradient from the tile; near-contact distance from the scan
     R gr[3];
-    tile_grad<R, WALLFREE>(sp, c, SX, SXY, gr);
+    tile_grad<R, WALLFREE>(sp, c, L::SX, L::SXY, gr);
     const R gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
     int h = 0;
     R Ahh = R(0);
-    if (A_h != R(0)) {
-      h = hnc[self];
+    if (H > 1 && A_h != R(0)) {
+      h = hs[(lz * TY + threadIdx.y) * TX + threadIdx.x];
       if (h > 0) {
         const R hk = R(h);
         if (hk <= R(P.h_min)) Ahh = A_h;
@@ -894,7 +959,8 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
     // Guo-shifted velocity
     const R irho = R(1) / rho;
     const R u0 = (j0 + R(0.5) * F0) * irho, u1 = (j1 + R(0.5) * F1) * irho, u2 = (j2 + R(0.5) * F2) * irho;
-    if (!(rho > R(0)) || !finite_(rho)) atomicOr(status, 1u);
+    // a density outside (0, RHO_MAX), or not finite, marks the run unstable
+    if (!(rho > R(0) && rho < R(Acc<R>::RHO_MAX))) atomicOr(status, 1u);
 
     if constexpr (WF) {
       fields[(size_t)F_PHI * NF + self] = phx;
@@ -972,6 +1038,12 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       Pyz -= rho * u1 * u2;
       trP = Pxx + Pyy + Pzz;
     }
+    // colour scalars of the single-set storages, as stored
+    float4 svo = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (!Store<ST>::TWOSET) {
+      svo = make_float4(sA, segamp * gr[0], segamp * gr[1], segamp * gr[2]);
+      O.sv[self] = svo;
+    }
     if constexpr (Store<ST>::MOMENT) {
       // f*_i = w_i (alpha + beta.c_i + c_i.Gamma.c_i): the equilibrium, the
       // relaxed Hermite orders 1-2, the perturbation (B_i = w_i (|c_i|^2 - 2/3))
@@ -980,18 +1052,25 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       // the regularised collision only)
       const R kP = keep * R(4.5), hg9 = R(0.5) * g9;
       const R bF = g3 - R(1.5) * keep;  // beta = 3 rho u + (3 guo - 1.5 keep) F
-      reinterpret_cast<float4*>(O.f)[self] =
-          make_float4(r0 + gm3uF - R(1.5) * keep * trP + (R(2) / R(3)) * A2g, r3 * u0 + bF * F0, r3 * u1 + bF * F1,
-                      r3 * u2 + bF * F2);
-      reinterpret_cast<float4*>(O.f + (I)4 * N)[self] =
-          make_float4(r45 * u0 * u0 + g9 * u0 * F0 + A2ig * gr[0] * gr[0] - A2g + kP * Pxx,
-                      r45 * u1 * u1 + g9 * u1 * F1 + A2ig * gr[1] * gr[1] - A2g + kP * Pyy,
-                      r45 * u2 * u2 + g9 * u2 * F2 + A2ig * gr[2] * gr[2] - A2g + kP * Pzz,
-                      R(2) * (r45 * u0 * u1 + hg9 * (u0 * F1 + F0 * u1) + A2ig * gr[0] * gr[1] + kP * Pxy));
-      reinterpret_cast<float2*>(O.f + (I)8 * N)[self] =
+      const float4 qa = make_float4(r0 + gm3uF - R(1.5) * keep * trP + (R(2) / R(3)) * A2g, r3 * u0 + bF * F0,
+                                    r3 * u1 + bF * F1, r3 * u2 + bF * F2);
+      const float4 qb = make_float4(r45 * u0 * u0 + g9 * u0 * F0 + A2ig * gr[0] * gr[0] - A2g + kP * Pxx,
+                                    r45 * u1 * u1 + g9 * u1 * F1 + A2ig * gr[1] * gr[1] - A2g + kP * Pyy,
+                                    r45 * u2 * u2 + g9 * u2 * F2 + A2ig * gr[2] * gr[2] - A2g + kP * Pzz,
+                                    R(2) * (r45 * u0 * u1 + hg9 * (u0 * F1 + F0 * u1) + A2ig * gr[0] * gr[1] + kP * Pxy));
+      const float2 qc =
           make_float2(R(2) * (r45 * u0 * u2 + hg9 * (u0 * F2 + F0 * u2) + A2ig * gr[0] * gr[2] + kP * Pxz),
                       R(2) * (r45 * u1 * u2 + hg9 * (u1 * F2 + F1 * u2) + A2ig * gr[1] * gr[2] + kP * Pyz));
-      O.sv[self] = make_float4(sA, segamp * gr[0], segamp * gr[1], segamp * gr[2]);
+      reinterpret_cast<float4*>(O.f)[self] = qa;
+      reinterpret_cast<float4*>(O.f + (I)4 * N)[self] = qb;
+      reinterpret_cast<float2*>(O.f + (I)8 * N)[self] = qc;
+      // what the neighbours will pull: the quadratic form at each c_i
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        R va, vb;
+        colour_split<R, false>(eval_moment<R>(qa, qb, qc, i, false), svo, i, false, va, vb);
+        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, i, va, vb);
+      }
       continue;
     }
     {  // rest direction
@@ -1000,10 +1079,16 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       const R fs = keep * rel + wf * W * r0 - bweight<R>(REST) * A2g + W * gm3uF;
       if constexpr (Store<ST>::TWOSET) {
         const R fa = sA * fs;
+        const R fb = fs - fa;
         O.f[(I)REST * N + (I)self] = encode<ST>(fa, REST);
-        O.f[(I)(Q + REST) * N + (I)self] = encode<ST>(fs - fa, REST);
+        O.f[(I)(Q + REST) * N + (I)self] = encode<ST>(fb, REST);
+        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, REST, fa, fb);
       } else {
-        O.f[(I)REST * N + (I)self] = encode<ST>(fs, REST);
+        const typename Store<ST>::E enc = encode<ST>(fs, REST);
+        O.f[(I)REST * N + (I)self] = enc;
+        R va, vb;
+        colour_split<R, false>(decode<ST>(enc, REST), svo, REST, false, va, vb);
+        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, REST, va, vb);
       }
     }
 #pragma unroll
@@ -1037,109 +1122,153 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
         const R seg = segamp * W * inv_norm<R>(p) * cg;
         const R fap = sA * fsp + seg;
         const R faq = sA * fsq - seg;
+        const R fbp = fsp - fap, fbq = fsq - faq;
         O.f[(I)p * N + (I)self] = encode<ST>(fap, p);
         O.f[(I)q * N + (I)self] = encode<ST>(faq, q);
-        O.f[(I)(Q + p) * N + (I)self] = encode<ST>(fsp - fap, p);
-        O.f[(I)(Q + q) * N + (I)self] = encode<ST>(fsq - faq, q);
+        O.f[(I)(Q + p) * N + (I)self] = encode<ST>(fbp, p);
+        O.f[(I)(Q + q) * N + (I)self] = encode<ST>(fbq, q);
+        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, p, fap, fbp);
+        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, q, faq, fbq);
       } else {
-        O.f[(I)p * N + (I)self] = encode<ST>(fsp, p);
-        O.f[(I)q * N + (I)self] = encode<ST>(fsq, q);
+        const typename Store<ST>::E ep = encode<ST>(fsp, p), eq = encode<ST>(fsq, q);
+        O.f[(I)p * N + (I)self] = ep;
+        O.f[(I)q * N + (I)self] = eq;
+        R va, vb;
+        colour_split<R, false>(decode<ST>(ep, p), svo, p, false, va, vb);
+        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, p, va, vb);
+        colour_split<R, false>(decode<ST>(eq, q), svo, q, false, va, vb);
+        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, q, va, vb);
       }
     }
-    if constexpr (!Store<ST>::TWOSET) {
-      O.sv[self] = make_float4(sA, segamp * gr[0], segamp * gr[1], segamp * gr[2]);
+  }
+}
+
+// Add the tile's partial sums (tile plus a one-node ring) to the global
+// accumulator; entries beyond a wall are never sent to, periodic axes wrap.
+template <typename R, int TX, int TY, int TZ, int H>
+__device__ __forceinline__ void flush_partials(const typename Acc<R>::S* sa, const typename Acc<R>::S* sb,
+                                               unsigned long long* __restrict__ acc, const Geo& g, int x0, int y0,
+                                               int z0) {
+  using L = Layout<R, TX, TY, TZ, H>;
+  for (int e = threadIdx.y * TX + threadIdx.x; e < L::E; e += TX * TY) {
+    const typename Acc<R>::S a = sa[e], b = sb[e];
+    if (a == 0 && b == 0) continue;
+    const int ex = e % L::EX, ey = (e / L::EX) % L::EY, ez = e / L::EXY;
+    int gx = x0 - 1 + ex, gy = y0 - 1 + ey, gz = z0 - 1 + ez;
+    if ((unsigned)gx >= (unsigned)g.nx) {
+      if (g.wx) continue;
+      gx = ((gx % g.nx) + g.nx) % g.nx;
+    }
+    if ((unsigned)gy >= (unsigned)g.ny) {
+      if (g.wy) continue;
+      gy = ((gy % g.ny) + g.ny) % g.ny;
+    }
+    if ((unsigned)gz >= (unsigned)g.nz) {
+      if (g.wz) continue;
+      gz = ((gz % g.nz) + g.nz) % g.nz;
+    }
+    Acc<R>::flush(acc, (size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * gz), a, b);
+  }
+}
+
+// One tile of the step: clear, stage, scan, step, flush.  Ends with a
+// barrier, so the caller may reuse the shared memory.
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, bool IDX32>
+__device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, const InitBuf& init, const PhiSrc& src,
+                                          const AccBufs& ab, const Geo& g, const Phys& P,
+                                          typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status,
+                                          unsigned char* smem, int x0, int y0, int z0) {
+  using R = typename Store<ST>::R;
+  using L = Layout<R, TX, TY, TZ, H>;
+  using SA = typename Acc<R>::S;
+  R* sp = reinterpret_cast<R*>(smem);
+  SA* sa = reinterpret_cast<SA*>(smem + L::off_acc);
+  SA* sb = sa + L::E;
+  unsigned short* queue = reinterpret_cast<unsigned short*>(smem + L::off_queue);
+  unsigned char* hs = smem + L::off_h;
+  int* count = reinterpret_cast<int*>(smem + L::off_count);
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  if constexpr (WS) {
+    // this tile's nodes of the accumulator two steps ahead
+    for (int lz = 0; lz < TZ; ++lz) {
+      const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
+      if (x < g.nx && y < g.ny && z < g.nz) Acc<R>::zero(ab.zero, (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z));
+    }
+    for (int e = tid; e < L::E; e += TX * TY) {
+      sa[e] = 0;
+      sb[e] = 0;
     }
   }
-}
-
-// One tile of the fused step: stage phi of the tile + a one-node halo, then
-// update the tile's nodes.  Ends with a barrier, so the caller may reuse the
-// shared tile.
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32>
-__device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, const InitBuf& init,
-                                          const typename Store<ST>::R* __restrict__ phi,
-                                          const unsigned char* __restrict__ hnc, const Geo& g, const Phys& P,
-                                          typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status,
-                                          typename Store<ST>::R* sp, int x0, int y0, int z0) {
-  using R = typename Store<ST>::R;
-  // a tile whose halo holds no solid node needs no bounce-back or wall tests
-  const bool wallfree = stage_phi<R, TX, TY>(phi, g, 1, 1, TZ + 2, sp, x0, y0, z0);
+  if (H > 1 && tid == 0) *count = 0;
+  if (src.acc) stage_phi<R, true, TX, TY, TZ, H>(src, g, sp, x0, y0, z0);
+  else stage_phi<R, false, TX, TY, TZ, H>(src, g, sp, x0, y0, z0);
+  __syncthreads();
+  if constexpr (H > 1) {
+    if (P.A_h != 0.0) {
+      if (region_walled(g, x0, y0, z0, TX, TY, TZ, P.K + 1))
+        nc_tile<R, TX, TY, TZ, H, false>(sp, g, P, hs, queue, count, x0, y0, z0);
+      else
+        nc_tile<R, TX, TY, TZ, H, true>(sp, g, P, hs, queue, count, x0, y0, z0);
+    }
+  }
+  // a tile whose one-node halo holds no solid node needs no bounce-back or wall tests
+  const bool wallfree = !region_walled(g, x0, y0, z0, TX, TY, TZ, 1);
   if (P.collision == 1) {  // regularised collision
     if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, true>(S, O, init, g, P, hnc, fields, status, sp, x0,
-                                                                    y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, true>(S, O, init, g, P, hs, fields, status, sp, sa,
+                                                                       sb, src.acc, x0, y0, z0);
     else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, true>(S, O, init, g, P, hnc, fields, status, sp, x0,
-                                                                     y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, true>(S, O, init, g, P, hs, fields, status, sp, sa,
+                                                                        sb, src.acc, x0, y0, z0);
   } else {
     if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32, false>(S, O, init, g, P, hnc, fields, status, sp, x0,
-                                                                     y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, false>(S, O, init, g, P, hs, fields, status, sp, sa,
+                                                                        sb, src.acc, x0, y0, z0);
     else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32, false>(S, O, init, g, P, hnc, fields, status, sp, x0,
-                                                                      y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, false>(S, O, init, g, P, hs, fields, status, sp, sa,
+                                                                         sb, src.acc, x0, y0, z0);
   }
   __syncthreads();
+  if constexpr (WS) {
+    flush_partials<R, TX, TY, TZ, H>(sa, sb, ab.out, g, x0, y0, z0);
+    __syncthreads();
+  }
 }
 
-// Shared memory of one fused-step tile: phi with a one-node halo.
-template <typename R>
-inline size_t step_smem_bytes(int TX, int TY, int TZ) {
-  return sizeof(R) * (size_t)(TX + 2) * (TY + 2) * (TZ + 2);
-}
-
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32, int MINB = 2>
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, bool IDX32, int MINB = 2>
 __global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : MINB)
-    k_step(View<ST> S, View<ST> O, InitBuf init, const typename Store<ST>::R* __restrict__ phi,
-           const unsigned char* __restrict__ hnc, Geo g, Phys P, typename Store<ST>::R* __restrict__ fields,
-           unsigned* __restrict__ status) {
-  using R = typename Store<ST>::R;
+    k_step(View<ST> S, View<ST> O, InitBuf init, PhiSrc src, AccBufs ab, Geo g, Phys P,
+           typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  step_tile<ST, LOADER, WS, WF, TX, TY, TZ, IDX32>(S, O, init, phi, hnc, g, P, fields, status,
-                                                   reinterpret_cast<R*>(smem_raw), blockIdx.x * TX, blockIdx.y * TY,
-                                                   blockIdx.z * TZ);
+  step_tile<ST, LOADER, WS, WF, TX, TY, TZ, H, IDX32>(S, O, init, src, ab, g, P, fields, status, smem_raw,
+                                                      blockIdx.x * TX, blockIdx.y * TY, blockIdx.z * TZ);
 }
 
 // ---------------------------------------------------------------------------
-// batched persistent kernels: many independent runs of uneven sizes and
-// parameters.  Work items are (run, tile) for the step and (run, 256-node
-// chunk) for the phase field; persistent CTAs stride over the item list and
-// find the run of an item by binary search over the runs' prefix offsets.
+// batched persistent kernel: many independent runs of uneven sizes and
+// parameters, one launch per step.  Work items are (run, tile); persistent
+// CTAs stride over the item list and find the run of an item by binary
+// search over the runs' prefix offsets.  Every run's accumulators are at the
+// same phase k of their rotation.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_run(const RunDesc* runs, int nruns, long long item, bool by_tile) {
+__device__ __forceinline__ int find_run(const RunDesc* runs, int nruns, long long item) {
   int lo = 0, hi = nruns - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    const long long b = by_tile ? runs[mid].tile_begin : runs[mid].chunk_begin;
-    if (b <= item) lo = mid;
+    if (runs[mid].tile_begin <= item) lo = mid;
     else hi = mid - 1;
   }
   return lo;
 }
 
-template <int ST, bool IDX32>
-__global__ void __launch_bounds__(256) k_phi_batched(const RunDesc* __restrict__ runs, int nruns, long long nchunks,
-                                                     int parity) {
-  using R = typename Store<ST>::R;
-  for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    const int r = find_run(runs, nruns, c, false);
-    const Geo g = runs[r].g;
-    const long long idx = (c - runs[r].chunk_begin) * 256 + threadIdx.x;
-    if (idx >= g.N) continue;
-    phi_node<ST, IDX32>(view<ST>(runs[r].S[parity]), g, idx, reinterpret_cast<R*>(runs[r].phi));
-  }
-}
-
-template <int ST, int TX, int TY, int TZ, bool IDX32, int MINB = 2>
+template <int ST, int TX, int TY, int TZ, int H, bool IDX32, int MINB = 2>
 __global__ void __launch_bounds__(TX* TY, MINB)
-    k_step_batched(const RunDesc* __restrict__ runs, int nruns, long long ntiles, int parity,
+    k_step_batched(const RunDesc* __restrict__ runs, int nruns, long long ntiles, int parity, int k,
                    unsigned* __restrict__ status) {
-  using R = typename Store<ST>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sp = reinterpret_cast<R*>(smem_raw);
   InitBuf none{nullptr, nullptr, nullptr, 0};
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int r = find_run(runs, nruns, t, true);
+    const int r = find_run(runs, nruns, t);
     const RunDesc& d = runs[r];
     const long long lt = t - d.tile_begin;
     const int bx = (int)(lt % d.tiles_x);
@@ -1147,31 +1276,11 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     const int bz = (int)(lt / ((long long)d.tiles_x * d.tiles_y));
     const Geo g = d.g;
     const Phys P = d.p;
-    step_tile<ST, LOAD_PULL, true, false, TX, TY, TZ, IDX32>(
-        view<ST>(d.S[parity]), view<ST>(d.S[parity ^ 1]), none, reinterpret_cast<const R*>(d.phi), d.hnc, g, P,
-        nullptr, status, sp, bx * TX, by * TY, bz * TZ);
-  }
-}
-
-// Near-contact pass of a batch over the same (run, tile) items; runs without
-// near contact are skipped (their step never reads h).
-template <int ST, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX* TY) k_nc_batched(const RunDesc* __restrict__ runs, int nruns, long long ntiles) {
-  using R = typename Store<ST>::R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sp = reinterpret_cast<R*>(smem_raw);
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int r = find_run(runs, nruns, t, true);
-    const RunDesc& d = runs[r];
-    if (d.p.A_h == 0.0) continue;
-    const long long lt = t - d.tile_begin;
-    const int bx = (int)(lt % d.tiles_x);
-    const int by = (int)((lt / d.tiles_x) % d.tiles_y);
-    const int bz = (int)(lt / ((long long)d.tiles_x * d.tiles_y));
-    with_halo(d.p.halo, [&](auto hc) {
-      nc_tile<R, TX, TY, TZ, decltype(hc)::value>(reinterpret_cast<const R*>(d.phi), d.g, d.p, d.hnc, sp, bx * TX,
-                                                  by * TY, bz * TZ);
-    });
+    const PhiSrc src{nullptr, d.acc[k]};
+    const AccBufs ab{d.acc[(k + 1) % 3], d.acc[(k + 2) % 3]};
+    step_tile<ST, LOAD_PULL, true, false, TX, TY, TZ, H, IDX32>(view<ST>(d.S[parity]), view<ST>(d.S[parity ^ 1]),
+                                                                none, src, ab, g, P, nullptr, status, smem_raw,
+                                                                bx * TX, by * TY, bz * TZ);
   }
 }
 

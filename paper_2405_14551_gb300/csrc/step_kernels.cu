@@ -4,58 +4,44 @@
 
 namespace lbcg {
 
-// tiles 2 and 4: the 32x8x4 tile with registers capped for 3 and 4 CTAs per SM
-const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 8, 4}, {64, 4, 4}, {32, 8, 4}};
+// tiles 2 and 4: the 32x8x4 tile with registers capped for 3 and 4 CTAs per
+// SM; tile 3: the 32x8x8 tile capped for 3 CTAs per SM
+const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 8, 4}, {32, 8, 8}, {32, 8, 4}};
 
 template <int ST>
-cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st);
-template <int ST>
-cudaError_t launch_nc_t(int variant, const Geo& g, const Phys& p, const void* phi, unsigned char* hnc,
-                        cudaStream_t st);
+cudaError_t launch_phi_acc_t(const Geo& g, const StateBuf& in, unsigned long long* acc, cudaStream_t st);
 template <int ST>
 cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, const Phys& p, const StateBuf& in,
-                          const InitBuf& init, const void* phi, const unsigned char* hnc, StateBuf out, void* fields,
-                          unsigned* status, cudaStream_t st);
+                          const InitBuf& init, PhiSrc src, AccBufs ab, StateBuf out, void* fields, unsigned* status,
+                          cudaStream_t st);
 template <int ST>
-cudaError_t launch_batched_t(const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles, int tile,
-                             int halo_max, long long max_nodes, int parity, int blocks_per_sm, unsigned* status,
+cudaError_t launch_batched_t(const RunDesc* d_runs, int nruns, long long ntiles, int tile, int halo,
+                             long long max_nodes, int parity, int k, int blocks_per_sm, unsigned* status,
                              cudaStream_t st);
 template <int ST>
 cudaError_t launch_export_t(int loader, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init, int x0,
                             int y0, int z0, int bx, int by, int bz, double* outA, double* outB, cudaStream_t st);
 
-cudaError_t launch_phi(int storage, const Geo& g, const StateBuf& in, void* phi, cudaStream_t st) {
+cudaError_t launch_phi_acc(int storage, const Geo& g, const StateBuf& in, unsigned long long* acc, cudaStream_t st) {
   switch (storage) {
-    case 0: return launch_phi_t<0>(g, in, phi, st);
-    case 1: return launch_phi_t<1>(g, in, phi, st);
-    case 2: return launch_phi_t<2>(g, in, phi, st);
-    case 3: return launch_phi_t<3>(g, in, phi, st);
-    case 4: return launch_phi_t<4>(g, in, phi, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_nc(int storage, int variant, const Geo& g, const Phys& p, const void* phi, unsigned char* hnc,
-                      cudaStream_t st) {
-  switch (storage) {
-    case 0: return launch_nc_t<0>(variant, g, p, phi, hnc, st);
-    case 1: return launch_nc_t<1>(variant, g, p, phi, hnc, st);
-    case 2: return launch_nc_t<2>(variant, g, p, phi, hnc, st);
-    case 3: return launch_nc_t<3>(variant, g, p, phi, hnc, st);
-    case 4: return launch_nc_t<4>(variant, g, p, phi, hnc, st);
+    case 0: return launch_phi_acc_t<0>(g, in, acc, st);
+    case 1: return launch_phi_acc_t<1>(g, in, acc, st);
+    case 2: return launch_phi_acc_t<2>(g, in, acc, st);
+    case 3: return launch_phi_acc_t<3>(g, in, acc, st);
+    case 4: return launch_phi_acc_t<4>(g, in, acc, st);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step(int storage, int loader, bool write_state, bool write_fields, int tile, const Geo& g,
-                        const Phys& p, const StateBuf& in, const InitBuf& init, const void* phi,
-                        const unsigned char* hnc, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
+                        const Phys& p, const StateBuf& in, const InitBuf& init, PhiSrc src, AccBufs ab, StateBuf out,
+                        void* fields, unsigned* status, cudaStream_t st) {
   switch (storage) {
-    case 0: return launch_step_s<0>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
-    case 1: return launch_step_s<1>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
-    case 2: return launch_step_s<2>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
-    case 3: return launch_step_s<3>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
-    case 4: return launch_step_s<4>(loader, write_state, write_fields, tile, g, p, in, init, phi, hnc, out, fields, status, st);
+    case 0: return launch_step_s<0>(loader, write_state, write_fields, tile, g, p, in, init, src, ab, out, fields, status, st);
+    case 1: return launch_step_s<1>(loader, write_state, write_fields, tile, g, p, in, init, src, ab, out, fields, status, st);
+    case 2: return launch_step_s<2>(loader, write_state, write_fields, tile, g, p, in, init, src, ab, out, fields, status, st);
+    case 3: return launch_step_s<3>(loader, write_state, write_fields, tile, g, p, in, init, src, ab, out, fields, status, st);
+    case 4: return launch_step_s<4>(loader, write_state, write_fields, tile, g, p, in, init, src, ab, out, fields, status, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -73,15 +59,15 @@ cudaError_t launch_export(int storage, int loader, const Geo& g, const Phys& p, 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_batched(int storage, const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles,
-                           int tile, int halo_max, long long max_nodes, int parity, int blocks_per_sm,
-                           unsigned* status, cudaStream_t st) {
+cudaError_t launch_batched(int storage, const RunDesc* d_runs, int nruns, long long ntiles, int tile, int halo,
+                           long long max_nodes, int parity, int k, int blocks_per_sm, unsigned* status,
+                           cudaStream_t st) {
   switch (storage) {
-    case 0: return launch_batched_t<0>(d_runs, nruns, nchunks, ntiles, tile, halo_max, max_nodes, parity, blocks_per_sm, status, st);
-    case 1: return launch_batched_t<1>(d_runs, nruns, nchunks, ntiles, tile, halo_max, max_nodes, parity, blocks_per_sm, status, st);
-    case 2: return launch_batched_t<2>(d_runs, nruns, nchunks, ntiles, tile, halo_max, max_nodes, parity, blocks_per_sm, status, st);
+    case 0: return launch_batched_t<0>(d_runs, nruns, ntiles, tile, halo, max_nodes, parity, k, blocks_per_sm, status, st);
+    case 1: return launch_batched_t<1>(d_runs, nruns, ntiles, tile, halo, max_nodes, parity, k, blocks_per_sm, status, st);
+    case 2: return launch_batched_t<2>(d_runs, nruns, ntiles, tile, halo, max_nodes, parity, k, blocks_per_sm, status, st);
   }
-  return cudaErrorInvalidValue;  // no batched FP64 instantiation
+  return cudaErrorInvalidValue;  // no batched FP64 or moment instantiation
 }
 
 int sm_count_host() {

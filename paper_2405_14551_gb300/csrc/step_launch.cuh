@@ -26,77 +26,41 @@ inline int resident_ctas(K kern, int threads, size_t smem) {
   return b;
 }
 
-template <int ST>
-cudaError_t launch_phi_t(const Geo& g, const StateBuf& in, void* phi, cudaStream_t st) {
-  using R = typename Store<ST>::R;
-  if constexpr (!Store<ST>::TWOSET) {  // reduced storage: tiles with staged colour scalars
-    constexpr int TX = 32, TY = 8, TZ = 4;
-    const bool idx32r = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
-    const size_t smem = sizeof(float4) * (TX + 2) * (TY + 2) * (TZ + 2);
-    const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
-    auto kern = idx32r ? k_phi_tiled<ST, TX, TY, TZ, true> : k_phi_tiled<ST, TX, TY, TZ, false>;
-    trace_kernel("k_phi_tiled", kern, grid, dim3(TX, TY), smem);
-    kern<<<grid, dim3(TX, TY), smem, st>>>(view<ST>(in), g, reinterpret_cast<R*>(phi));
-    return cudaGetLastError();
+// 32-bit population offsets when every offset of a lattice of N nodes fits
+inline bool fits_idx32(long long N) { return (unsigned long long)(2 * Q) * (unsigned long long)N < (1ull << 32); }
+
+// Calls f with the staging halo (1, 4 or 7) as a compile-time constant.
+template <typename F>
+inline cudaError_t with_stage_halo(int halo, F&& f) {
+  switch (halo) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 7: return f(std::integral_constant<int, 7>{});
   }
-  static const int occ32 = resident_ctas(k_phi<ST, true>, 256, 0);
-  static const int occ64 = resident_ctas(k_phi<ST, false>, 256, 0);
-  const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
-  // one wave of resident CTAs striding over the lattice: no second, partial wave
-  const long long blocks_needed = (g.N + 255) / 256;
+  return cudaErrorInvalidValue;
+}
+
+template <int ST>
+cudaError_t launch_phi_acc_t(const Geo& g, const StateBuf& in, unsigned long long* acc, cudaStream_t st) {
+  const bool idx32 = fits_idx32(g.N);
+  static const int occ32 = resident_ctas(k_phi_acc<ST, true>, 256, 0);
+  static const int occ64 = resident_ctas(k_phi_acc<ST, false>, 256, 0);
+  const long long need = (g.N + 255) / 256;
   const long long cap = (long long)sm_count() * (idx32 ? occ32 : occ64);
-  const int blocks = (int)(blocks_needed < cap ? blocks_needed : cap);
-  auto kern = idx32 ? k_phi<ST, true> : k_phi<ST, false>;
-  trace_kernel("k_phi", kern, dim3(blocks), dim3(256), 0);
-  kern<<<blocks, 256, 0, st>>>(view<ST>(in), g, reinterpret_cast<R*>(phi));
+  const int blocks = (int)(need < cap ? need : cap);
+  auto kern = idx32 ? k_phi_acc<ST, true> : k_phi_acc<ST, false>;
+  trace_kernel("k_phi_acc", kern, dim3(blocks), dim3(256), 0);
+  kern<<<blocks, 256, 0, st>>>(view<ST>(in), g, acc);
   return cudaGetLastError();
 }
 
-template <int ST, int TX, int TY, int TZ>
-inline cudaError_t launch_nc_tt(const Geo& g, const Phys& p, const void* phi, unsigned char* hnc, cudaStream_t st) {
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, int MINB = 2>
+inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init, PhiSrc src,
+                                 AccBufs ab, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  if (p.halo != p.K + 1 || p.halo < 2 || p.halo > 7) return cudaErrorInvalidValue;
-  const size_t smem = nc_smem_bytes<R>(TX, TY, TZ, p.halo);
-  const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
-  cudaError_t e = cudaSuccess;
-  with_halo(p.halo, [&](auto hc) {
-    auto kern = k_nc<ST, TX, TY, TZ, decltype(hc)::value>;
-    if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return;
-    trace_kernel("k_nc", kern, grid, dim3(TX, TY), smem);
-    kern<<<grid, dim3(TX, TY), smem, st>>>(reinterpret_cast<const R*>(phi), g, p, hnc);
-    e = cudaGetLastError();
-  });
-  return e;
-}
-
-// Near-contact tile shapes (x, y threads, z nodes per thread): 32x8x8,
-// 32x8x4, 32x8x16, 32x4x16.  FP64 storage (parity runs) uses 32x8x4 only.
-template <int ST>
-cudaError_t launch_nc_t(int variant, const Geo& g, const Phys& p, const void* phi, unsigned char* hnc,
-                        cudaStream_t st) {
-  if (p.A_h == 0.0) return cudaSuccess;
-  if constexpr (ST == 3) {
-    return launch_nc_tt<ST, 32, 8, 4>(g, p, phi, hnc, st);
-  } else {
-    switch (variant) {
-      case 1: return launch_nc_tt<ST, 32, 8, 4>(g, p, phi, hnc, st);
-      case 2: return launch_nc_tt<ST, 32, 8, 16>(g, p, phi, hnc, st);
-      case 3: return launch_nc_tt<ST, 32, 4, 16>(g, p, phi, hnc, st);
-      default: return launch_nc_tt<ST, 32, 8, 8>(g, p, phi, hnc, st);
-    }
-  }
-}
-
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int MINB = 2>
-inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
-                                 const void* phi, const unsigned char* hnc, StateBuf out, void* fields,
-                                 unsigned* status, cudaStream_t st) {
-  using R = typename Store<ST>::R;
-  const size_t smem = step_smem_bytes<R>(TX, TY, TZ);
-  // 32-bit population offsets when every offset of the lattice fits
-  const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)g.N < (1ull << 32);
-  auto kern = idx32 ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, true, MINB> : k_step<ST, LOADER, WS, WF, TX, TY, TZ, false, MINB>;
+  const size_t smem = Layout<R, TX, TY, TZ, H>::bytes;
+  auto kern = fits_idx32(g.N) ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, true, MINB>
+                              : k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, false, MINB>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -104,39 +68,42 @@ inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
   dim3 block(TX, TY, 1);
   trace_kernel("k_step", kern, grid, block, smem);
-  kern<<<grid, block, smem, st>>>(view<ST>(in), view<ST>(out), init, reinterpret_cast<const R*>(phi), hnc, g, p,
-                                  reinterpret_cast<R*>(fields), status);
+  kern<<<grid, block, smem, st>>>(view<ST>(in), view<ST>(out), init, src, ab, g, p, reinterpret_cast<R*>(fields),
+                                  status);
   return cudaGetLastError();
 }
 
+// Tile shapes of the hot variant (pull, write state): 0..4 as kTiles; the
+// widest halo (7) only with tile 0.  Other variants and FP64 use tile 0.
 template <int ST, int LOADER, bool WS, bool WF>
 inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
-                                     const void* phi, const unsigned char* hnc, StateBuf out, void* fields,
-                                     unsigned* status, cudaStream_t st) {
-  if constexpr (LOADER == LOAD_PULL && WS && !WF) {
-    switch (tile) {
-      case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8>(g, p, in, init, phi, hnc, out, fields, status, st);
-      case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, 3>(g, p, in, init, phi, hnc, out, fields, status, st);
-      case 3: return launch_step_t<ST, LOADER, WS, WF, 64, 4, 4>(g, p, in, init, phi, hnc, out, fields, status, st);
-      case 4: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, 4>(g, p, in, init, phi, hnc, out, fields, status, st);
-      default: break;
+                                     PhiSrc src, AccBufs ab, StateBuf out, void* fields, unsigned* status,
+                                     cudaStream_t st) {
+  return with_stage_halo(stage_halo(p), [&](auto hc) -> cudaError_t {
+    constexpr int H = decltype(hc)::value;
+    if constexpr (LOADER == LOAD_PULL && WS && !WF && ST != 3 && H < 7) {
+      switch (tile) {
+        case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8, H>(g, p, in, init, src, ab, out, fields, status, st);
+        case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, H, 3>(g, p, in, init, src, ab, out, fields, status, st);
+        case 3: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8, H, 3>(g, p, in, init, src, ab, out, fields, status, st);
+        case 4: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, H, 4>(g, p, in, init, src, ab, out, fields, status, st);
+        default: break;
+      }
     }
-  }
-  return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4>(g, p, in, init, phi, hnc, out, fields, status, st);
+    return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, H>(g, p, in, init, src, ab, out, fields, status, st);
+  });
 }
 
 template <int ST>
 cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, const Phys& p, const StateBuf& in,
-                          const InitBuf& init, const void* phi, const unsigned char* hnc, StateBuf out, void* fields,
-                          unsigned* status, cudaStream_t st) {
+                          const InitBuf& init, PhiSrc src, AccBufs ab, StateBuf out, void* fields, unsigned* status,
+                          cudaStream_t st) {
   if (loader == LOAD_PULL) {
-    if (ws && !wf) return launch_step_tiles<ST, LOAD_PULL, true, false>(tile, g, p, in, init, phi, hnc, out, fields, status, st);
-    if (ws && wf) return launch_step_tiles<ST, LOAD_PULL, true, true>(0, g, p, in, init, phi, hnc, out, fields, status, st);
-    if (!ws && wf) return launch_step_tiles<ST, LOAD_PULL, false, true>(0, g, p, in, init, phi, hnc, out, fields, status, st);
+    if (ws && !wf) return launch_step_tiles<ST, LOAD_PULL, true, false>(tile, g, p, in, init, src, ab, out, fields, status, st);
+    if (!ws && wf) return launch_step_tiles<ST, LOAD_PULL, false, true>(0, g, p, in, init, src, ab, out, fields, status, st);
   } else {
-    if (ws && !wf) return launch_step_tiles<ST, LOAD_FIELDS, true, false>(0, g, p, in, init, phi, hnc, out, fields, status, st);
-    if (ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, true, true>(0, g, p, in, init, phi, hnc, out, fields, status, st);
-    if (!ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, false, true>(0, g, p, in, init, phi, hnc, out, fields, status, st);
+    if (ws && !wf) return launch_step_tiles<ST, LOAD_FIELDS, true, false>(0, g, p, in, init, src, ab, out, fields, status, st);
+    if (!ws && wf) return launch_step_tiles<ST, LOAD_FIELDS, false, true>(0, g, p, in, init, src, ab, out, fields, status, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -155,61 +122,47 @@ cudaError_t launch_export_t(int loader, const Geo& g, const Phys& p, const State
   return cudaGetLastError();
 }
 
-template <int ST, int TX, int TY, int TZ, bool IDX32, int MINB = 2>
-inline cudaError_t launch_batched_step_t(const RunDesc* d_runs, int nruns, long long ntiles, int halo_max,
-                                         int parity, int blocks, unsigned* status, cudaStream_t st) {
+template <int ST, int TX, int TY, int TZ, int H, bool IDX32, int MINB = 2>
+inline cudaError_t launch_batched_step_t(const RunDesc* d_runs, int nruns, long long ntiles, int parity, int k,
+                                         int blocks, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  if (halo_max > 1) {  // some run has near contact
-    const size_t nsmem = nc_smem_bytes<R>(TX, TY, TZ, halo_max);
-    auto nk = k_nc_batched<ST, TX, TY, TZ>;
-    if (nsmem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(nk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsmem);
-      if (e != cudaSuccess) return e;
-    }
-    trace_kernel("k_nc_batched", nk, dim3(blocks), dim3(TX, TY), nsmem);
-    nk<<<blocks, dim3(TX, TY), nsmem, st>>>(d_runs, nruns, ntiles);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  const size_t smem = step_smem_bytes<R>(TX, TY, TZ);
-  auto kern = k_step_batched<ST, TX, TY, TZ, IDX32, MINB>;
+  const size_t smem = Layout<R, TX, TY, TZ, H>::bytes;
+  auto kern = k_step_batched<ST, TX, TY, TZ, H, IDX32, MINB>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   trace_kernel("k_step_batched", kern, dim3(blocks), dim3(TX, TY), smem);
-  kern<<<blocks, dim3(TX, TY), smem, st>>>(d_runs, nruns, ntiles, parity, status);
+  kern<<<blocks, dim3(TX, TY), smem, st>>>(d_runs, nruns, ntiles, parity, k, status);
   return cudaGetLastError();
 }
 
 template <int ST, bool IDX32>
-inline cudaError_t launch_batched_tiles(int tile, const RunDesc* d_runs, int nruns, long long ntiles, int halo_max,
-                                        int parity, int blocks, unsigned* status, cudaStream_t st) {
-  switch (tile) {
-    case 1: return launch_batched_step_t<ST, 32, 8, 8, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
-    case 2: return launch_batched_step_t<ST, 32, 8, 4, IDX32, 3>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
-    case 3: return launch_batched_step_t<ST, 64, 4, 4, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
-    case 4: return launch_batched_step_t<ST, 32, 8, 4, IDX32, 4>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
-    default: return launch_batched_step_t<ST, 32, 8, 4, IDX32>(d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
-  }
+inline cudaError_t launch_batched_tiles(int tile, int halo, const RunDesc* d_runs, int nruns, long long ntiles,
+                                        int parity, int k, int blocks, unsigned* status, cudaStream_t st) {
+  return with_stage_halo(halo, [&](auto hc) -> cudaError_t {
+    constexpr int H = decltype(hc)::value;
+    if constexpr (H < 7) {
+      switch (tile) {
+        case 1: return launch_batched_step_t<ST, 32, 8, 8, H, IDX32>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
+        case 2: return launch_batched_step_t<ST, 32, 8, 4, H, IDX32, 3>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
+        case 3: return launch_batched_step_t<ST, 32, 8, 8, H, IDX32, 3>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
+        case 4: return launch_batched_step_t<ST, 32, 8, 4, H, IDX32, 4>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
+        default: break;
+      }
+    }
+    return launch_batched_step_t<ST, 32, 8, 4, H, IDX32>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
+  });
 }
 
 template <int ST>
-cudaError_t launch_batched_t(const RunDesc* d_runs, int nruns, long long nchunks, long long ntiles, int tile,
-                             int halo_max, long long max_nodes, int parity, int blocks_per_sm, unsigned* status,
+cudaError_t launch_batched_t(const RunDesc* d_runs, int nruns, long long ntiles, int tile, int halo,
+                             long long max_nodes, int parity, int k, int blocks_per_sm, unsigned* status,
                              cudaStream_t st) {
   const int blocks = sm_count() * (blocks_per_sm > 0 ? blocks_per_sm : 2);
-  const bool idx32 = (unsigned long long)(2 * Q) * (unsigned long long)max_nodes < (1ull << 32);
-  auto pk = idx32 ? k_phi_batched<ST, true> : k_phi_batched<ST, false>;
-  static const int pocc32 = resident_ctas(k_phi_batched<ST, true>, 256, 0);
-  static const int pocc64 = resident_ctas(k_phi_batched<ST, false>, 256, 0);
-  const int pblocks = sm_count() * (idx32 ? pocc32 : pocc64);
-  trace_kernel("k_phi_batched", pk, dim3(pblocks), dim3(256), 0);
-  pk<<<pblocks, 256, 0, st>>>(d_runs, nruns, nchunks, parity);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (idx32) return launch_batched_tiles<ST, true>(tile, d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
-  return launch_batched_tiles<ST, false>(tile, d_runs, nruns, ntiles, halo_max, parity, blocks, status, st);
+  if (fits_idx32(max_nodes))
+    return launch_batched_tiles<ST, true>(tile, halo, d_runs, nruns, ntiles, parity, k, blocks, status, st);
+  return launch_batched_tiles<ST, false>(tile, halo, d_runs, nruns, ntiles, parity, k, blocks, status, st);
 }
 
 }  // namespace lbcg

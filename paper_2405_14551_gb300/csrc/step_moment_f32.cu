@@ -4,11 +4,10 @@
 
 namespace lbcg {
 
-template cudaError_t launch_phi_t<4>(const Geo&, const StateBuf&, void*, cudaStream_t);
-template cudaError_t launch_nc_t<4>(int, const Geo&, const Phys&, const void*, unsigned char*, cudaStream_t);
+template cudaError_t launch_phi_acc_t<4>(const Geo&, const StateBuf&, unsigned long long*, cudaStream_t);
 template cudaError_t launch_step_s<4>(int, bool, bool, int, const Geo&, const Phys&, const StateBuf&, const InitBuf&,
-                                         const void*, const unsigned char*, StateBuf, void*, unsigned*, cudaStream_t);
+                                      PhiSrc, AccBufs, StateBuf, void*, unsigned*, cudaStream_t);
 template cudaError_t launch_export_t<4>(int, const Geo&, const Phys&, const StateBuf&, const InitBuf&, int, int, int,
-                                          int, int, int, double*, double*, cudaStream_t);
+                                        int, int, int, double*, double*, cudaStream_t);
 
 }  // namespace lbcg

@@ -3,14 +3,13 @@
 
 namespace lbcg {
 
-template cudaError_t launch_phi_t<1>(const Geo&, const StateBuf&, void*, cudaStream_t);
-template cudaError_t launch_nc_t<1>(int, const Geo&, const Phys&, const void*, unsigned char*, cudaStream_t);
+template cudaError_t launch_phi_acc_t<1>(const Geo&, const StateBuf&, unsigned long long*, cudaStream_t);
 template cudaError_t launch_step_s<1>(int, bool, bool, int, const Geo&, const Phys&, const StateBuf&, const InitBuf&,
-                                         const void*, const unsigned char*, StateBuf, void*, unsigned*, cudaStream_t);
+                                      PhiSrc, AccBufs, StateBuf, void*, unsigned*, cudaStream_t);
 template cudaError_t launch_export_t<1>(int, const Geo&, const Phys&, const StateBuf&, const InitBuf&, int, int, int,
-                                          int, int, int, double*, double*, cudaStream_t);
+                                        int, int, int, double*, double*, cudaStream_t);
 
-template cudaError_t launch_batched_t<1>(const RunDesc*, int, long long, long long, int, int, long long, int, int,
-                                           unsigned*, cudaStream_t);
+template cudaError_t launch_batched_t<1>(const RunDesc*, int, long long, int, int, long long, int, int, int,
+                                         unsigned*, cudaStream_t);
 
 }  // namespace lbcg

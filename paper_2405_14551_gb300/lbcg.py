@@ -70,7 +70,6 @@ _SIGS = {
                                       ctypes.c_int, ctypes.c_int]),
     "lb_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "lb_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
-    "lb_set_nc_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lb_copy_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lb_surrogate_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "lb_surrogate_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -79,7 +78,6 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_double)]),
     "lb_phi_monitor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_double)]),
-    "lb_get_nc_tile": (ctypes.c_int, [ctypes.c_void_p]),
     "lb_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "lb_get_tile": (ctypes.c_int, [ctypes.c_void_p]),
     "lb_time": (ctypes.c_int64, [ctypes.c_void_p]),
@@ -258,12 +256,12 @@ def lb_step(h, nsteps: int):
     _check(load_library().lb_step(h, int(nsteps)), "lb_step")
 
 
-def lb_step_timed(h, nsteps: int):
-    """(mean ms of the phase-field pass, of the fused step kernel, of the
-    near-contact scan)."""
-    ms = np.zeros(3)
+def lb_step_timed(h, nsteps: int) -> float:
+    """Mean ms of one step kernel over nsteps steps (CUDA events on the
+    handle's stream, no graph replay)."""
+    ms = np.zeros(1)
     _check(load_library().lb_step_timed(h, int(nsteps), ms.ctypes.data), "lb_step_timed")
-    return float(ms[0]), float(ms[1]), float(ms[2])
+    return float(ms[0])
 
 
 def lb_phi_monitor(h, phi):
@@ -294,14 +292,6 @@ def lb_surrogate_cycle(h, judge, K: int, vol_tol: float, phi_tol: float):
 
 def lb_copy_state(dst, src):
     _check(load_library().lb_copy_state(dst, src), "lb_copy_state")
-
-
-def lb_set_nc_tile(h, variant: int):
-    _check(load_library().lb_set_nc_tile(h, int(variant)), "lb_set_nc_tile")
-
-
-def lb_get_nc_tile(h) -> int:
-    return int(load_library().lb_get_nc_tile(h))
 
 
 def lb_set_tile(h, tile: int):

@@ -85,12 +85,12 @@ def test_null_handle_rejected(lib):
     assert lib.lb_check(None) == L.LB_EINVAL
     assert lib.lb_destroy(None) == L.LB_OK
     assert lib.lb_time(None) == -1
-    assert lib.lb_set_nc_tile(None, 0) == L.LB_EINVAL
+    assert lib.lb_set_tile(None, 0) == L.LB_EINVAL
     assert lib.lb_phi_monitor(None, None, None, None) == L.LB_EINVAL
     assert lib.lb_copy_state(None, None) == L.LB_EINVAL
     assert lib.lb_surrogate_load(None, b"x") == L.LB_EINVAL
     assert lib.lb_surrogate_predict(None, None) == L.LB_EINVAL
-    assert lib.lb_get_nc_tile(None) == -1
+    assert lib.lb_get_tile(None) == -1
 
 
 def test_conv_argument_checks_without_gpu(lib):

@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-tune", action="store_true", help="use --tile without autotuning")
     ap.add_argument("--tile", type=int, default=0, help="tile of the step kernel when --no-tune is given")
+    ap.add_argument("--long-run", action="store_true",
+                    help="error-vs-time table of the FP32 and FP16 storages against the FP64 oracle on the 64^3 "
+                         "dense-emulsion analogue (20000 steps; prints one JSON line)")
+    ap.add_argument("--long-steps", type=int, default=20000, help="last checkpoint of --long-run")
     ap.add_argument("--conv", nargs="+", default=None, metavar="ARG",
                     help="MODE NX NY NZ CIN COUT [REPS]: time one surrogate convolution call instead "
                          "(MODE fwd, upcat or wgrad; used by the convolution profiles)")
@@ -395,12 +399,13 @@ def surrogate_extra(L, stream, ntraj=24, iters=4000, cycles=100, spinup=2000):
         t_train = time.time() - t1
         x = torch.empty((n, S.CIN), dtype=torch.bfloat16, device="cuda")
         out = torch.empty((5, n), dtype=torch.float32, device="cuda")
-        err, pers = [], []
+        err, pers, err_max = [], [], []
         for f0, f1 in zip(test[0][:-1], test[0][1:]):
             S.pack_input(f0, x, stream)
             y = net.forward(x, (nx, ny, nz, 1))
             S.unpack_output(f0, y, out, stream)
             err.append(float((out[0] - f1[0]).abs().mean()))
+            err_max.append(float((out[0] - f1[0]).abs().max()))
             pers.append(float((f0[0] - f1[0]).abs().mean()))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for _ in range(2):
@@ -426,6 +431,22 @@ def surrogate_extra(L, stream, ntraj=24, iters=4000, cycles=100, spinup=2000):
         L.lb_copy_state(b.h, a.h)
         b.step(100)
         L.lb_copy_state(b.h, a.h)
+        # noise floor: the plain LB against itself from a start one ulp away
+        # (the last mantissa bit of one population of one node, through a
+        # checkpoint), over the same steps
+        c = L.Sim(nx, ny, nz, walls=0b010, stream=stream, **p)
+        fd, ck = tempfile.mkstemp(suffix=".lbck")
+        os.close(fd)
+        try:
+            b.save(ck)
+            raw = bytearray(open(ck, "rb").read())
+            node = n // 2 + nx * (ny // 2)
+            off = len(raw) - 2 * 27 * n * 4 + (13 * n + node) * 4  # f^A, rest direction
+            raw[off] ^= 1
+            open(ck, "wb").write(bytes(raw))
+            c.load(ck)
+        finally:
+            os.remove(ck)
         ctl.reset()
         torch.cuda.synchronize()
         t2 = time.time()
@@ -436,8 +457,11 @@ def surrogate_extra(L, stream, ntraj=24, iters=4000, cycles=100, spinup=2000):
         b.step(cycles * 100)
         torch.cuda.synchronize()
         t_lb = time.time() - t3
+        c.step(cycles * 100)
         fa, fb = a.fields_device(1).reshape(-1), b.fields_device(1).reshape(-1)
         final_err = float((fa - fb).abs().mean())
+        noise = float((c.fields_device(1).reshape(-1) - fb).abs().mean())
+        c.close()
         counts = (a.droplet_count(), b.droplet_count())
         judged = [(c, round(e, 4)) for c, e in ctl.judged]
         acc, rej = ctl.accepted, ctl.rejected
@@ -448,9 +472,11 @@ def surrogate_extra(L, stream, ntraj=24, iters=4000, cycles=100, spinup=2000):
     return {"workload": "dense_emulsion_128x128x256 surrogate, K = 50", "spinup_steps": spinup,
             "train_trajectories": ntraj, "train_pairs": ntraj * 7, "train_iters": iters, "train_s": round(t_train, 1),
             "unet_forward_ms": round(fwd_ms, 2), "lb_50_steps_ms": round(t_lb / (cycles * 2) * 1e3, 2),
-            "phi_err_per_jump": round(sum(err) / len(err), 4), "persistence_err": round(sum(pers) / len(pers), 4),
+            "phi_err_per_jump": round(sum(err) / len(err), 4), "phi_err_per_jump_max": round(max(err_max), 4),
+            "persistence_err": round(sum(pers) / len(pers), 4),
             "phi_tol": 1e-2, "controller_cycles": cycles, "accepted": acc, "rejected": rej, "judged": judged,
             "speedup_vs_plain_lb": round(t_lb / t_ctl, 3), "final_phi_err_vs_plain": round(final_err, 5),
+            "noise_floor_plain_vs_plain_one_ulp": round(noise, 5),
             "droplet_count_ctrl_plain": list(counts), "total_s": round(time.time() - t0, 1)}
 
 
@@ -522,10 +548,78 @@ def conv_call(argv):
     print(f"{mode} {nx}x{ny}x{nz} {cin}->{cout}: {ms * 1e3:.1f} us, {flop / ms / 1e9:.1f} TFLOP/s")
 
 
+def long_run(args):
+    """The dense-emulsion analogue on 64^3 (walls y = 0, 63, seeded power-cell
+    droplets eroded by 6-node films, near contact on, body force 1e-6 along
+    z) from the same initial phi in the FP64 oracle (host cores) and on the
+    GPU in the FP32 two-set, FP32 reduced, FP16-deviation reduced and FP64
+    two-set storages.  At steps 1, 10, 100, 1000, 5000, 10000, 20000: max and
+    mean |field - oracle| over fluid nodes per field (phi, rho, ux, uy, uz,
+    rhoA, rhoB), and the statistics (droplet count, dispersed fraction, mean
+    u_z over fluid nodes) of every run.  Pointwise agreement of the FP32
+    forms is expected to be lost to the chaotic dynamics; the statistics are
+    what the runs should share."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2405_14551_gb300.lbcg as L
+    from paper_2405_14551_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    shape, walls, seed = (64, 64, 64), 0b010, 1234
+    phi, info = W.dense_emulsion_phi(shape, walls, seed, film=W.DENSE_FILM)
+    params = dict(W.BASE, A_h=0.1, h_min=3.0, h_max=3.0, g=(0.0, 0.0, 1e-6), g_mode=1)
+    nx, ny, nz = shape
+    o = oracle.OracleSim(oracle.make_params(nx, ny, nz, walls=walls, **params))
+    o.init_fields(phi.astype(np.float64))
+    L.load_library()
+    sims = {}
+    for st in ("twoset_f32", "reduced_f32", "reduced_f16", "twoset_f64"):
+        sims[st] = L.Sim(nx, ny, nz, walls=walls, storage=st, **params)
+        sims[st].init_fields(phi)
+    fl = W.fluid_mask(shape, walls)
+    names = ("phi", "rho", "ux", "uy", "uz", "rhoA", "rhoB")
+
+    def stats(f, count):
+        return {"droplets": int(count), "phi_d": round(float((f["phi"][fl] > 0).mean()), 5),
+                "mean_uz": float(f["uz"][fl].mean())}
+
+    rows, t, t_orc = [], 0, 0.0
+    for cp in [c for c in (1, 10, 100, 1000, 5000, 10000, 20000) if c <= args.long_steps]:
+        t0 = time.perf_counter()
+        o.step(cp - t)
+        t_orc += time.perf_counter() - t0
+        for sm in sims.values():
+            sm.step(cp - t)
+        t = cp
+        fo = o.fields()
+        row = {"step": cp, "oracle": stats(fo, o.droplet_count())}
+        for st, sm in sims.items():
+            fg = sm.fields(f64=True)
+            err = {}
+            for k in names:
+                d = np.abs(fg[k][fl] - fo[k][fl])
+                err[k] = [float(d.max()), float(d.mean())]
+            row[st] = {"max_mean": err, **stats(fg, sm.droplet_count())}
+        rows.append(row)
+        print(json.dumps({"long_run_checkpoint": cp, "oracle_s": round(t_orc, 1)}), file=sys.stderr, flush=True)
+    for sm in sims.values():
+        sm.check()
+        sm.close()
+    o.close()
+    print(json.dumps({"long_run": "dense_emulsion_64x64x64 analogue", "seed": seed, "film": W.DENSE_FILM,
+                      "droplets0": info["droplets"], "phi_d0": round(info["phi_d"], 5),
+                      "oracle_cores": int(os.environ["OMP_NUM_THREADS"]), "oracle_s": round(t_orc, 1),
+                      "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.conv:
         conv_call(args.conv)
+        return
+    if args.long_run:
+        long_run(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

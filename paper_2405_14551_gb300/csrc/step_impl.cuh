@@ -429,18 +429,31 @@ template <typename R>
 struct Acc;
 template <>
 struct Acc<float> {
-  static constexpr int W = 1;  // 64-bit words per node
-  using S = int;               // shared-memory partial sum of one component
+  static constexpr int W = 1;  // 64-bit words per node, in global and in shared memory
+  using S = int;               // sum of one component
   static constexpr float RHO_MAX = 4.0f;
   __device__ static __forceinline__ S q(float v) { return __float2int_rn(v * 268435456.0f); }
-  __device__ static __forceinline__ void add_shared(S* p, S v) { atomicAdd(p, v); }
+  // add one node's contributions (a, b) to the shared partial sums of node e:
+  // two planes of E 32-bit words (rhoA, then rhoB) in the E 64-bit words of
+  // sw; 32-bit shared atomics (one packed 64-bit shared atomic per direction
+  // measured slower)
+  __device__ static __forceinline__ void send_shared(unsigned long long* sw, int E, int e, float a, float b) {
+    int* p = reinterpret_cast<int*>(sw);
+    atomicAdd(p + e, q(a));
+    atomicAdd(p + E + e, q(b));
+  }
+  __device__ static __forceinline__ void flush_shared(unsigned long long* acc, size_t node,
+                                                      const unsigned long long* sw, int E, int e) {
+    const int* p = reinterpret_cast<const int*>(sw);
+    const unsigned long long w = pack(p[e], p[E + e]);
+    if (w) atomicAdd(acc + node, w);
+  }
+  __device__ static __forceinline__ bool shared_zero(const unsigned long long* sw, int E, int e) {
+    const int* p = reinterpret_cast<const int*>(sw);
+    return (p[e] | p[E + e]) == 0;
+  }
   __device__ static __forceinline__ unsigned long long pack(S a, S b) {
     return ((unsigned long long)(unsigned)a << 32) + (unsigned long long)(long long)b;
-  }
-  // add the partial sums (a, b) of one node; zero partials add nothing
-  __device__ static __forceinline__ void flush(unsigned long long* acc, size_t node, S a, S b) {
-    const unsigned long long w = pack(a, b);
-    if (w) atomicAdd(acc + node, w);
   }
   __device__ static __forceinline__ void store(unsigned long long* acc, size_t node, S a, S b) {
     acc[node] = pack(a, b);
@@ -476,12 +489,18 @@ struct Acc<double> {
   using S = long long;
   static constexpr double RHO_MAX = 64.0;
   __device__ static __forceinline__ S q(double v) { return __double2ll_rn(v * 72057594037927936.0); }
-  __device__ static __forceinline__ void add_shared(S* p, S v) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+  // two planes of E shared words: rhoA at sw[e], rhoB at sw[E + e]
+  __device__ static __forceinline__ void send_shared(unsigned long long* sw, int E, int e, double a, double b) {
+    atomicAdd(sw + e, (unsigned long long)q(a));
+    atomicAdd(sw + E + e, (unsigned long long)q(b));
   }
-  __device__ static __forceinline__ void flush(unsigned long long* acc, size_t node, S a, S b) {
-    if (a) atomicAdd(acc + 2 * node, (unsigned long long)a);
-    if (b) atomicAdd(acc + 2 * node + 1, (unsigned long long)b);
+  __device__ static __forceinline__ void flush_shared(unsigned long long* acc, size_t node,
+                                                      const unsigned long long* sw, int E, int e) {
+    if (sw[e]) atomicAdd(acc + 2 * node, sw[e]);
+    if (sw[E + e]) atomicAdd(acc + 2 * node + 1, sw[E + e]);
+  }
+  __device__ static __forceinline__ bool shared_zero(const unsigned long long* sw, int E, int e) {
+    return (sw[e] | sw[E + e]) == 0ull;
   }
   __device__ static __forceinline__ void store(unsigned long long* acc, size_t node, S a, S b) {
     acc[2 * node] = (unsigned long long)a;
@@ -577,9 +596,8 @@ struct Layout {
   static constexpr int SX = TX + 2 * HX, SY = TY + 2 * H, SZ = TZ + 2 * H, SXY = SX * SY, NS = SXY * SZ;
   static constexpr int EX = TX + 2, EY = TY + 2, EZ = TZ + 2, EXY = EX * EY, E = EXY * EZ;
   static constexpr int NT = TX * TY * TZ;
-  using S = typename Acc<R>::S;
   static constexpr size_t off_acc = align16(sizeof(R) * (size_t)NS);
-  static constexpr size_t off_queue = off_acc + align16(2 * sizeof(S) * (size_t)E);
+  static constexpr size_t off_queue = off_acc + align16(8 * (size_t)Acc<R>::W * (size_t)E);
   static constexpr size_t off_h = off_queue + (H > 1 ? align16(2 * (size_t)NT) : 0);
   static constexpr size_t off_count = off_h + (H > 1 ? align16((size_t)NT) : 0);
   static constexpr size_t bytes = off_count + 16;
@@ -844,15 +862,13 @@ __device__ __forceinline__ void nc_tile(const R* sp, const Geo& g, const Phys& P
 // Send the component populations (a, b) of direction i of the node at
 // accumulator index e0 to the node that pulls them: x + c_i, or the node
 // itself when x + c_i is solid (halfway bounce-back).
-template <typename R, bool WALLFREE, int EX, int EXY>
-__device__ __forceinline__ void send(typename Acc<R>::S* sa, typename Acc<R>::S* sb, int e0, const Nbr& n, int i, R a,
-                                     R b) {
+template <typename R, bool WALLFREE, int EX, int EXY, int E>
+__device__ __forceinline__ void send(unsigned long long* sw, int e0, const Nbr& n, int i, R a, R b) {
   int e = e0 + cx(i) + EX * cy(i) + EXY * cz(i);
   if constexpr (!WALLFREE) {
     if (n.sx[1 + cx(i)] | n.sy[1 + cy(i)] | n.sz[1 + cz(i)]) e = e0;
   }
-  Acc<R>::add_shared(sa + e, Acc<R>::q(a));
-  Acc<R>::add_shared(sb + e, Acc<R>::q(b));
+  Acc<R>::send_shared(sw, E, e, a, b);
 }
 
 // Pull, collide, recolour and store every node of the tile; with WS also
@@ -864,9 +880,8 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
                                            const Phys& P, const unsigned char* hs,
                                            typename Store<ST>::R* __restrict__ fields,
                                            unsigned* __restrict__ status, const typename Store<ST>::R* sp,
-                                           typename Acc<typename Store<ST>::R>::S* sa,
-                                           typename Acc<typename Store<ST>::R>::S* sb,
-                                           const unsigned long long* __restrict__ accin, int x0, int y0, int z0) {
+                                           unsigned long long* sw, const unsigned long long* __restrict__ accin,
+                                           int x0, int y0, int z0) {
   using R = typename Store<ST>::R;
   using L = Layout<R, TX, TY, TZ, H>;
   using I = typename std::conditional<IDX32, unsigned, size_t>::type;
@@ -1069,7 +1084,7 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       for (int i = 0; i < Q; ++i) {
         R va, vb;
         colour_split<R, false>(eval_moment<R>(qa, qb, qc, i, false), svo, i, false, va, vb);
-        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, i, va, vb);
+        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, i, va, vb);
       }
       continue;
     }
@@ -1082,13 +1097,13 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
         const R fb = fs - fa;
         O.f[(I)REST * N + (I)self] = encode<ST>(fa, REST);
         O.f[(I)(Q + REST) * N + (I)self] = encode<ST>(fb, REST);
-        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, REST, fa, fb);
+        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, REST, fa, fb);
       } else {
         const typename Store<ST>::E enc = encode<ST>(fs, REST);
         O.f[(I)REST * N + (I)self] = enc;
         R va, vb;
         colour_split<R, false>(decode<ST>(enc, REST), svo, REST, false, va, vb);
-        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, REST, va, vb);
+        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, REST, va, vb);
       }
     }
 #pragma unroll
@@ -1127,17 +1142,17 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
         O.f[(I)q * N + (I)self] = encode<ST>(faq, q);
         O.f[(I)(Q + p) * N + (I)self] = encode<ST>(fbp, p);
         O.f[(I)(Q + q) * N + (I)self] = encode<ST>(fbq, q);
-        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, p, fap, fbp);
-        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, q, faq, fbq);
+        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, p, fap, fbp);
+        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, q, faq, fbq);
       } else {
         const typename Store<ST>::E ep = encode<ST>(fsp, p), eq = encode<ST>(fsq, q);
         O.f[(I)p * N + (I)self] = ep;
         O.f[(I)q * N + (I)self] = eq;
         R va, vb;
         colour_split<R, false>(decode<ST>(ep, p), svo, p, false, va, vb);
-        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, p, va, vb);
+        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, p, va, vb);
         colour_split<R, false>(decode<ST>(eq, q), svo, q, false, va, vb);
-        send<R, WALLFREE, L::EX, L::EXY>(sa, sb, e0, n, q, va, vb);
+        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, q, va, vb);
       }
     }
   }
@@ -1146,13 +1161,11 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
 // Add the tile's partial sums (tile plus a one-node ring) to the global
 // accumulator; entries beyond a wall are never sent to, periodic axes wrap.
 template <typename R, int TX, int TY, int TZ, int H>
-__device__ __forceinline__ void flush_partials(const typename Acc<R>::S* sa, const typename Acc<R>::S* sb,
-                                               unsigned long long* __restrict__ acc, const Geo& g, int x0, int y0,
-                                               int z0) {
+__device__ __forceinline__ void flush_partials(const unsigned long long* sw, unsigned long long* __restrict__ acc,
+                                               const Geo& g, int x0, int y0, int z0) {
   using L = Layout<R, TX, TY, TZ, H>;
   for (int e = threadIdx.y * TX + threadIdx.x; e < L::E; e += TX * TY) {
-    const typename Acc<R>::S a = sa[e], b = sb[e];
-    if (a == 0 && b == 0) continue;
+    if (Acc<R>::shared_zero(sw, L::E, e)) continue;
     const int ex = e % L::EX, ey = (e / L::EX) % L::EY, ez = e / L::EXY;
     int gx = x0 - 1 + ex, gy = y0 - 1 + ey, gz = z0 - 1 + ez;
     if ((unsigned)gx >= (unsigned)g.nx) {
@@ -1167,7 +1180,7 @@ __device__ __forceinline__ void flush_partials(const typename Acc<R>::S* sa, con
       if (g.wz) continue;
       gz = ((gz % g.nz) + g.nz) % g.nz;
     }
-    Acc<R>::flush(acc, (size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * gz), a, b);
+    Acc<R>::flush_shared(acc, (size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * gz), sw, L::E, e);
   }
 }
 
@@ -1180,10 +1193,8 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
                                           unsigned char* smem, int x0, int y0, int z0) {
   using R = typename Store<ST>::R;
   using L = Layout<R, TX, TY, TZ, H>;
-  using SA = typename Acc<R>::S;
   R* sp = reinterpret_cast<R*>(smem);
-  SA* sa = reinterpret_cast<SA*>(smem + L::off_acc);
-  SA* sb = sa + L::E;
+  unsigned long long* sw = reinterpret_cast<unsigned long long*>(smem + L::off_acc);
   unsigned short* queue = reinterpret_cast<unsigned short*>(smem + L::off_queue);
   unsigned char* hs = smem + L::off_h;
   int* count = reinterpret_cast<int*>(smem + L::off_count);
@@ -1194,10 +1205,7 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
       const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
       if (x < g.nx && y < g.ny && z < g.nz) Acc<R>::zero(ab.zero, (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z));
     }
-    for (int e = tid; e < L::E; e += TX * TY) {
-      sa[e] = 0;
-      sb[e] = 0;
-    }
+    for (int e = tid; e < Acc<R>::W * L::E; e += TX * TY) sw[e] = 0ull;
   }
   if (H > 1 && tid == 0) *count = 0;
   if (src.acc) stage_phi<R, true, TX, TY, TZ, H>(src, g, sp, x0, y0, z0);
@@ -1215,22 +1223,22 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
   const bool wallfree = !region_walled(g, x0, y0, z0, TX, TY, TZ, 1);
   if (P.collision == 1) {  // regularised collision
     if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, true>(S, O, init, g, P, hs, fields, status, sp, sa,
-                                                                       sb, src.acc, x0, y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, true>(S, O, init, g, P, hs, fields, status, sp, sw,
+                                                                       src.acc, x0, y0, z0);
     else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, true>(S, O, init, g, P, hs, fields, status, sp, sa,
-                                                                        sb, src.acc, x0, y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, true>(S, O, init, g, P, hs, fields, status, sp, sw,
+                                                                        src.acc, x0, y0, z0);
   } else {
     if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, false>(S, O, init, g, P, hs, fields, status, sp, sa,
-                                                                        sb, src.acc, x0, y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, false>(S, O, init, g, P, hs, fields, status, sp, sw,
+                                                                        src.acc, x0, y0, z0);
     else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, false>(S, O, init, g, P, hs, fields, status, sp, sa,
-                                                                         sb, src.acc, x0, y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, false>(S, O, init, g, P, hs, fields, status, sp, sw,
+                                                                         src.acc, x0, y0, z0);
   }
   __syncthreads();
   if constexpr (WS) {
-    flush_partials<R, TX, TY, TZ, H>(sa, sb, ab.out, g, x0, y0, z0);
+    flush_partials<R, TX, TY, TZ, H>(sw, ab.out, g, x0, y0, z0);
     __syncthreads();
   }
 }

@@ -41,6 +41,9 @@ class OrcParams(ctypes.Structure):
         ("g", ctypes.c_double * 3),
         ("g_mode", ctypes.c_int32),
         ("collision", ctypes.c_int32),
+        ("model", ctypes.c_int32),
+        ("G", ctypes.c_double),
+        ("psi0", ctypes.c_double),
     ]
 
 
@@ -75,6 +78,9 @@ def lib():
             L.orc_time.restype = ctypes.c_int64
             L.orc_time.argtypes = [ctypes.c_void_p]
             L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+            L.orc_sc_psi.restype = ctypes.c_double
+            L.orc_sc_psi.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.orc_node_collide_sc.argtypes = [ctypes.POINTER(OrcParams), dp, dp, dp, dp, dp, dp, dp]
             L.orc_fields.argtypes = [ctypes.c_void_p, dp]
             L.orc_reduce.argtypes = [ctypes.c_void_p, dp]
             L.orc_laplace.restype = ctypes.c_double
@@ -101,7 +107,10 @@ def _dp(a: np.ndarray):
 
 
 def make_params(nx, ny, nz, walls=0, tau_a=1.0, tau_b=1.0, A_a=0.01, A_b=0.01, beta=0.7,
-                A_h=0.0, h_min=3.0, h_max=3.0, phi_I=0.9, g=(0.0, 0.0, 0.0), g_mode=0, collision=0) -> OrcParams:
+                A_h=0.0, h_min=3.0, h_max=3.0, phi_I=0.9, g=(0.0, 0.0, 0.0), g_mode=0, collision=0,
+                model=0, G=0.0, psi0=1.0) -> OrcParams:
+    """model 0: colour gradient (A_a, A_b, beta, near contact); model 1:
+    Shan-Chen pseudo-potential (G, psi0; Sec. III.C.3)."""
     p = OrcParams()
     p.nx, p.ny, p.nz, p.walls = int(nx), int(ny), int(nz), int(walls)
     p.tau_a, p.tau_b, p.A_a, p.A_b, p.beta = tau_a, tau_b, A_a, A_b, beta
@@ -109,6 +118,7 @@ def make_params(nx, ny, nz, walls=0, tau_a=1.0, tau_b=1.0, A_a=0.01, A_b=0.01, b
     p.g[0], p.g[1], p.g[2] = g
     p.g_mode = int(g_mode)
     p.collision = int(collision)
+    p.model, p.G, p.psi0 = int(model), float(G), float(psi0)
     return p
 
 
@@ -171,6 +181,22 @@ def node_collide(params: OrcParams, fA, fB, grad, F):
                            _dp(np.ascontiguousarray(fB, dtype=np.float64)),
                            _dp(np.ascontiguousarray(grad, dtype=np.float64)),
                            _dp(np.ascontiguousarray(F, dtype=np.float64)), _dp(oa), _dp(ob), _dp(u))
+    return oa, ob, u
+
+
+def sc_psi(rho, psi0=1.0):
+    """Shan-Chen pseudo-potential psi(rho) = rho_0 (1 - exp(-rho/rho_0))."""
+    return float(lib().orc_sc_psi(float(rho), float(psi0)))
+
+
+def node_collide_sc(params: OrcParams, fA, fB, FA, FB):
+    """One node's Shan-Chen collision (forces include the body forces)."""
+    oa, ob, u = np.zeros(Q), np.zeros(Q), np.zeros(3)
+    lib().orc_node_collide_sc(ctypes.byref(params),
+                              _dp(np.ascontiguousarray(fA, dtype=np.float64)),
+                              _dp(np.ascontiguousarray(fB, dtype=np.float64)),
+                              _dp(np.ascontiguousarray(FA, dtype=np.float64)),
+                              _dp(np.ascontiguousarray(FB, dtype=np.float64)), _dp(oa), _dp(ob), _dp(u))
     return oa, ob, u
 
 

@@ -101,6 +101,9 @@ typedef struct {
   double g[3];
   int32_t g_mode; /* 0 none, 1 rho*g, 2 s(z)*rhoA*g (mirror-opposite halves) */
   int32_t collision; /* 0 BGK, 1 regularised (non-equilibrium projected on Hermite orders 1 and 2) */
+  int32_t model;     /* 0 colour gradient, 1 Shan-Chen pseudo-potential (Sec. III.C.3) */
+  double G;          /* Shan-Chen coupling G_AB = G_BA (G_AA = G_BB = 0) */
+  double psi0;       /* rho_0 of the pseudo-potential psi(rho) = rho_0 (1 - exp(-rho/rho_0)) */
 } orc_params;
 
 #define GRAD_EPS 1e-12
@@ -263,6 +266,48 @@ void orc_node_collide(const orc_params* p, const double fA[Q], const double fB[Q
   orc_recolour(p->beta, rhoA, rhoB, fstar, grad, outA, outB);
 }
 
+/* Shan-Chen multicomponent model (Sec. III.C.3, lattice pseudo-potential
+ * approach).  Pseudo-potential of a component, Shan and Chen's choice as the
+ * paper states it: psi(rho) = rho_0 (1 - exp(-rho/rho_0)). */
+double orc_sc_psi(double rho, double psi0) { return psi0 * (1.0 - exp(-rho / psi0)); }
+
+/* One node's Shan-Chen collision: each component relaxes by BGK with its own
+ * tau_k towards its own equilibrium f^eq(rho_k, u') at the common velocity
+ * of Shan and Chen's scheme, weighted by 1/tau_k and shifted by half the
+ * force, u' = sum_k (j_k + F_k/2)/tau_k / sum_k rho_k/tau_k, and receives the
+ * Guo source of its own force F_k (reading: the forcing term of the
+ * colour-gradient path applied per component).  With this u' the collision
+ * adds exactly F_A + F_B to the total momentum for any tau_A, tau_B; for
+ * equal taus u' = (j + F/2)/rho.  FA, FB include the body forces.  u_out
+ * (nullable) receives u'. */
+void orc_node_collide_sc(const orc_params* p, const double fA[Q], const double fB[Q], const double FA[3],
+                         const double FB[3], double outA[Q], double outB[Q], double u_out[3]) {
+  lattice_build();
+  double rhoA = 0, rhoB = 0, j[3] = {0, 0, 0};
+  for (int i = 0; i < Q; ++i) {
+    rhoA += fA[i];
+    rhoB += fB[i];
+    for (int a = 0; a < 3; ++a) j[a] += (fA[i] + fB[i]) * LC[i][a];
+  }
+  double jA[3] = {0, 0, 0}, u[3];
+  for (int i = 0; i < Q; ++i)
+    for (int a = 0; a < 3; ++a) jA[a] += fA[i] * LC[i][a];
+  const double wa = 1.0 / p->tau_a, wb = 1.0 / p->tau_b;
+  for (int a = 0; a < 3; ++a)
+    u[a] = (wa * (jA[a] + 0.5 * FA[a]) + wb * (j[a] - jA[a] + 0.5 * FB[a])) / (wa * rhoA + wb * rhoB);
+  if (u_out)
+    for (int a = 0; a < 3; ++a) u_out[a] = u[a];
+  double feqA[Q], feqB[Q], SA[Q], SB[Q];
+  orc_feq(rhoA, u, feqA);
+  orc_feq(rhoB, u, feqB);
+  orc_guo(p->tau_a, u, FA, SA);
+  orc_guo(p->tau_b, u, FB, SB);
+  for (int i = 0; i < Q; ++i) {
+    outA[i] = fA[i] + (feqA[i] - fA[i]) / p->tau_a + SA[i];
+    outB[i] = fB[i] + (feqB[i] - fB[i]) / p->tau_b + SB[i];
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Whole-lattice simulation.                                                */
 /* ------------------------------------------------------------------------ */
@@ -276,6 +321,8 @@ typedef struct {
   double *rhoA, *rhoB, *phi, *jx, *jy, *jz;
   double *gx, *gy, *gz;
   double *frx, *fry, *frz;
+  double *psiA, *psiB;           /* Shan-Chen pseudo-potentials */
+  double *fax, *fay, *faz;       /* Shan-Chen force on component A (B: total minus A) */
   int32_t* h;
   int64_t t;
 } orc_sim;
@@ -308,6 +355,7 @@ orc_sim* orc_create(const orc_params* p) {
   lattice_build();
   if (!p || p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return NULL;
   if (p->tau_a <= 0.5 || p->tau_b <= 0.5) return NULL;
+  if (p->model == 1 && (p->A_h != 0.0 || p->collision != 0 || !(p->psi0 > 0.0))) return NULL;
   orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
   s->p = *p;
   s->N = (int64_t)p->nx * p->ny * p->nz;
@@ -316,8 +364,8 @@ orc_sim* orc_create(const orc_params* p) {
     s->fn[k] = (double*)calloc((size_t)Q * s->N, sizeof(double));
   }
   s->solid = (uint8_t*)calloc(s->N, 1);
-  double** arrs[] = {&s->rhoA, &s->rhoB, &s->phi, &s->jx, &s->jy, &s->jz,
-                     &s->gx,   &s->gy,   &s->gz,  &s->frx, &s->fry, &s->frz};
+  double** arrs[] = {&s->rhoA, &s->rhoB, &s->phi, &s->jx, &s->jy, &s->jz, &s->gx,  &s->gy,
+                     &s->gz,   &s->frx,  &s->fry, &s->frz, &s->psiA, &s->psiB, &s->fax, &s->fay, &s->faz};
   for (unsigned a = 0; a < sizeof(arrs) / sizeof(arrs[0]); ++a) *arrs[a] = (double*)calloc(s->N, sizeof(double));
   s->h = (int32_t*)calloc(s->N, sizeof(int32_t));
   for (int z = 0; z < p->nz; ++z)
@@ -333,7 +381,8 @@ void orc_destroy(orc_sim* s) {
     free(s->fn[k]);
   }
   free(s->solid);
-  double* arrs[] = {s->rhoA, s->rhoB, s->phi, s->jx, s->jy, s->jz, s->gx, s->gy, s->gz, s->frx, s->fry, s->frz};
+  double* arrs[] = {s->rhoA, s->rhoB, s->phi, s->jx, s->jy, s->jz, s->gx, s->gy, s->gz,
+                    s->frx,  s->fry,  s->frz, s->psiA, s->psiB, s->fax, s->fay, s->faz};
   for (unsigned a = 0; a < sizeof(arrs) / sizeof(arrs[0]); ++a) free(arrs[a]);
   free(s->h);
   free(s);
@@ -488,6 +537,51 @@ static void compute_levels(orc_sim* s) {
         s->gz[n] = 3.0 * gr[2];
       }
 
+  if (s->p.model == 1) {
+    /* Shan-Chen force (Sec. III.C.3, discretised on the lattice links):
+       F_k(x) = -psi_k(x) sum_{k'} G_{kk'} sum_i w_i psi_{k'}(x + c_i) c_i with
+       G_AB = G_BA = G and G_AA = G_BB = 0; a solid neighbour contributes the
+       node's own psi (the neutral-wall reading of the colour gradient).
+       frx.. hold the total F_A + F_B, fax.. the force on A. */
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+      s->psiA[n] = s->solid[n] ? 0.0 : orc_sc_psi(s->rhoA[n], s->p.psi0);
+      s->psiB[n] = s->solid[n] ? 0.0 : orc_sc_psi(s->rhoB[n], s->p.psi0);
+    }
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          int64_t n = nid(s, x, y, z);
+          s->h[n] = 0;
+          s->frx[n] = s->fry[n] = s->frz[n] = s->fax[n] = s->fay[n] = s->faz[n] = 0.0;
+          if (s->solid[n]) continue;
+          double sa[3] = {0, 0, 0}, sb[3] = {0, 0, 0}; /* sum_i w_i psi_k(x + c_i) c_i */
+          for (int i = 1; i < Q; ++i) {
+            int xx = wrap(x + LC[i][0], nx, wx), yy = wrap(y + LC[i][1], ny, wy), zz = wrap(z + LC[i][2], nz, wz);
+            int64_t m = nid(s, xx, yy, zz);
+            double pa = s->solid[m] ? s->psiA[n] : s->psiA[m];
+            double pb = s->solid[m] ? s->psiB[n] : s->psiB[m];
+            for (int d = 0; d < 3; ++d) {
+              sa[d] += LW[i] * pa * LC[i][d];
+              sb[d] += LW[i] * pb * LC[i][d];
+            }
+          }
+          double fa[3], fb[3];
+          for (int d = 0; d < 3; ++d) {
+            fa[d] = -s->psiA[n] * s->p.G * sb[d];
+            fb[d] = -s->psiB[n] * s->p.G * sa[d];
+          }
+          s->fax[n] = fa[0];
+          s->fay[n] = fa[1];
+          s->faz[n] = fa[2];
+          s->frx[n] = fa[0] + fb[0];
+          s->fry[n] = fa[1] + fb[1];
+          s->frz[n] = fa[2] + fb[2];
+        }
+    return;
+  }
+
   /* near-contact scan: from an interface node x (|phi| < phi_I with a defined
      normal), step along the outward normal n_out = -grad phi/|grad phi| in
      lround(k n_out) increments, k = 1..floor(h_max); the first interface node
@@ -600,8 +694,25 @@ static void step_once(orc_sim* s) {
         F[0] += s->frx[n];
         F[1] += s->fry[n];
         F[2] += s->frz[n];
-        double grad[3] = {s->gx[n], s->gy[n], s->gz[n]};
-        orc_node_collide(&s->p, fa, fb, grad, F, oa, ob, NULL);
+        if (s->p.model == 1) {
+          /* the body force acts on each component by its own density (g_mode
+             1) or on A only (g_mode 2); the Shan-Chen forces of each component */
+          double FA[3], FB[3], bA[3] = {0, 0, 0};
+          if (s->p.g_mode == 1)
+            for (int a = 0; a < 3; ++a) bA[a] = s->rhoA[n] * s->p.g[a];
+          else if (s->p.g_mode == 2)
+            body_force(s, z, rho, s->rhoA[n], bA);
+          double sf[3] = {s->fax[n], s->fay[n], s->faz[n]}, tf[3] = {s->frx[n], s->fry[n], s->frz[n]};
+          for (int a = 0; a < 3; ++a) {
+            double body = F[a] - tf[a];  /* total body force of the node */
+            FA[a] = sf[a] + bA[a];
+            FB[a] = (tf[a] - sf[a]) + (body - bA[a]);
+          }
+          orc_node_collide_sc(&s->p, fa, fb, FA, FB, oa, ob, NULL);
+        } else {
+          double grad[3] = {s->gx[n], s->gy[n], s->gz[n]};
+          orc_node_collide(&s->p, fa, fb, grad, F, oa, ob, NULL);
+        }
         for (int i = 0; i < Q; ++i) {
           int xx = wrap(x + LC[i][0], nx, wx), yy = wrap(y + LC[i][1], ny, wy), zz = wrap(z + LC[i][2], nz, wz);
           int64_t m = nid(s, xx, yy, zz);

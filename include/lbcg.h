@@ -106,7 +106,24 @@ typedef struct {
   int32_t collision;      /* 0: BGK on the total (Sec. III.B); 1: regularised colour-gradient collision (the
                              ghost-mode filtering Sec. III.C.1 cites): the non-equilibrium part of the total is
                              projected on Hermite orders 1 and 2 before relaxation; moments up to order 2 as BGK */
+  int32_t model;          /* LB_MODEL_COLOUR_GRADIENT (0) or LB_MODEL_SHAN_CHEN (1) */
+  double G;               /* Shan-Chen coupling G_AB = G_BA (G_AA = G_BB = 0); model 1 only */
+  double psi0;            /* rho_0 of the pseudo-potential psi(rho) = rho_0 (1 - exp(-rho/rho_0)); model 1 only */
 } lb_params;
+
+/* Two-component models.  COLOUR_GRADIENT: the scheme above (A_a, A_b, beta,
+ * near contact).  SHAN_CHEN: the lattice pseudo-potential model of Sec.
+ * III.C.3: each component relaxes by BGK with its own tau_k towards
+ * f^eq(rho_k, u'), u' = sum_k (j_k + F_k/2)/tau_k / sum_k rho_k/tau_k, with
+ * the Guo source of its own force F_k(x) = -psi_k(x) G sum_i w_i
+ * psi_k'(x + c_i) c_i (k' the other component; a solid neighbour
+ * contributes the node's own psi), plus its share of the body force (rho_k g
+ * for g_mode 1, all of it on A for g_mode 2).  Requires a two-set storage
+ * (TWOSET_F32 or TWOSET_F64), A_h = 0, collision = 0 and psi0 > 0; A_a, A_b
+ * and beta are ignored.  Fields: F_rep holds the total Shan-Chen force
+ * F_A + F_B, h is 0. */
+#define LB_MODEL_COLOUR_GRADIENT 0
+#define LB_MODEL_SHAN_CHEN 1
 
 /* Optional device allocator (for example PyTorch's caching allocator).  With
  * a NULL lb_alloc the library uses cudaMalloc/cudaFree.  alloc returns a

@@ -29,6 +29,9 @@ struct Phys {
   double g[3];
   int g_mode;
   int collision;  // 0 BGK, 1 regularised
+  int model;      // 0 colour gradient, 1 Shan-Chen
+  double G;       // Shan-Chen coupling
+  double psi0;    // Shan-Chen pseudo-potential scale rho_0
 };
 
 // Device pointers of one population lattice.  Two-set storage: f holds

@@ -32,7 +32,7 @@ namespace {
 // leaves both where they were
 constexpr int STEPS_PER_GRAPH = 12;
 constexpr uint32_t CKPT_MAGIC = 0x4742434cu;  // "LCBG"
-constexpr uint32_t CKPT_VERSION = 2;  // 2: lb_params carries the collision model
+constexpr uint32_t CKPT_VERSION = 3;  // 2: lb_params carries the collision model; 3: and the Shan-Chen model
 
 std::atomic<uint64_t> g_launches{0};
 thread_local std::string g_last_error;
@@ -225,6 +225,13 @@ int validate(const lb_grid* gr, const lb_params* p) {
   if (p->collision < 0 || p->collision > 1) return set_err(LB_EINVAL, "collision must be 0 (BGK) or 1 (regularised)");
   if (p->storage == LB_STORAGE_MOMENT_F32 && p->collision != 1)
     return set_err(LB_EINVAL, "the moment storage holds the regularised collision only (collision = 1)");
+  if (p->model < 0 || p->model > 1) return set_err(LB_EINVAL, "model must be 0 (colour gradient) or 1 (Shan-Chen)");
+  if (p->model == LB_MODEL_SHAN_CHEN) {
+    if (p->storage != LB_STORAGE_TWOSET_F32 && p->storage != LB_STORAGE_TWOSET_F64)
+      return set_err(LB_EINVAL, "the Shan-Chen model needs a two-set storage");
+    if (p->A_h != 0.0 || p->collision != 0) return set_err(LB_EINVAL, "the Shan-Chen model takes A_h = 0 and collision = 0");
+    if (!fin(p->G) || !(p->psi0 > 0.0) || !fin(p->psi0)) return set_err(LB_EINVAL, "Shan-Chen needs a finite G and psi0 > 0");
+  }
   return LB_OK;
 }
 
@@ -379,6 +386,9 @@ int lb_create(const lb_grid* grid, const lb_params* params, const lb_alloc* allo
   for (int a = 0; a < 3; ++a) p.g[a] = params->g[a];
   p.g_mode = params->g_mode;
   p.collision = params->collision;
+  p.model = params->model;
+  p.G = params->G;
+  p.psi0 = params->psi0;
   if (alloc && alloc->alloc && alloc->free) {
     h->alloc = *alloc;
     h->have_alloc = true;
@@ -1025,6 +1035,7 @@ int lb_batch_create(int32_t nruns, const lb_grid* grids, const lb_params* params
     int rc = validate(&grids[r], &params[r]);
     if (rc) return rc;
     if (params[r].storage != params[0].storage) return set_err(LB_EINVAL, "all runs of a batch share one storage");
+    if (params[r].model != LB_MODEL_COLOUR_GRADIENT) return set_err(LB_EINVAL, "batches run the colour-gradient model");
   }
   if (params[0].storage == LB_STORAGE_TWOSET_F64 || params[0].storage == LB_STORAGE_MOMENT_F32)
     return set_err(LB_EINVAL, "batches support the two-set and reduced FP32/FP16 storages only");

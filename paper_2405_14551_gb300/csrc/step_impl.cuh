@@ -590,13 +590,15 @@ __global__ void __launch_bounds__(256) k_phi_acc(View<ST> S, Geo g, unsigned lon
 // the queue counter.
 constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 
-template <typename R, int TX, int TY, int TZ, int H>
+template <typename R, int TX, int TY, int TZ, int H, int NPH = 1>
 struct Layout {
   static constexpr int HX = H == 1 ? 1 : (H + 3) / 4 * 4;
   static constexpr int SX = TX + 2 * HX, SY = TY + 2 * H, SZ = TZ + 2 * H, SXY = SX * SY, NS = SXY * SZ;
   static constexpr int EX = TX + 2, EY = TY + 2, EZ = TZ + 2, EXY = EX * EY, E = EXY * EZ;
   static constexpr int NT = TX * TY * TZ;
-  static constexpr size_t off_acc = align16(sizeof(R) * (size_t)NS);
+  // NPH staged scalar fields of NS values each (phi; the Shan-Chen model
+  // adds psi_A and psi_B)
+  static constexpr size_t off_acc = align16(sizeof(R) * (size_t)NS * NPH);
   static constexpr size_t off_queue = off_acc + align16(8 * (size_t)Acc<R>::W * (size_t)E);
   static constexpr size_t off_h = off_queue + (H > 1 ? align16(2 * (size_t)NT) : 0);
   static constexpr size_t off_count = off_h + (H > 1 ? align16((size_t)NT) : 0);
@@ -1182,6 +1184,238 @@ __device__ __forceinline__ void flush_partials(const unsigned long long* sw, uns
     }
     Acc<R>::flush_shared(acc, (size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * gz), sw, L::E, e);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Shan-Chen multicomponent model (Sec. III.C.3, lattice pseudo-potential)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float sc_psi(float r, float psi0) { return psi0 * (1.0f - expf(-r / psi0)); }
+__device__ __forceinline__ double sc_psi(double r, double psi0) { return psi0 * (1.0 - exp(-r / psi0)); }
+
+// Stage phi, psi_A and psi_B (pseudo-potential psi(rho) = rho_0 (1 -
+// exp(-rho/rho_0)) of each component) of the tile plus a one-node halo; solid
+// and beyond-wall nodes get the marker.  The component densities come from
+// the accumulator of the step before, or (first step) from the initial
+// fields: rho_k = rho (1 +- phi)/2.  No barrier.
+template <typename R, bool FROM_ACC, int TX, int TY, int TZ>
+__device__ __forceinline__ void stage_sc(const PhiSrc& src, const InitBuf& init, const Geo& g, R psi0, R* sp,
+                                         R* spa, R* spb, int x0, int y0, int z0) {
+  using L = Layout<R, TX, TY, TZ, 1, 3>;
+  for (int q = threadIdx.y * TX + threadIdx.x; q < L::NS; q += TX * TY) {
+    const int lx = q % L::SX, row = q / L::SX;
+    const int ly = row % L::SY, lz = row / L::SY;
+    int gx = x0 - 1 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
+    bool solid = false;
+    if (g.wx) solid |= (gx <= 0 || gx >= g.nx - 1);
+    else if ((unsigned)gx >= (unsigned)g.nx) gx = ((gx % g.nx) + g.nx) % g.nx;
+    if (g.wy) solid |= (gy <= 0 || gy >= g.ny - 1);
+    else if ((unsigned)gy >= (unsigned)g.ny) gy = ((gy % g.ny) + g.ny) % g.ny;
+    if (g.wz) solid |= (gz <= 0 || gz >= g.nz - 1);
+    else if ((unsigned)gz >= (unsigned)g.nz) gz = ((gz % g.nz) + g.nz) % g.nz;
+    if (solid) {
+      sp[q] = spa[q] = spb[q] = R(PHI_SOLID);
+      continue;
+    }
+    const size_t node = (size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * gz);
+    R ra, rb;
+    if constexpr (FROM_ACC) {
+      Acc<R>::densities(src.acc, node, ra, rb);
+    } else {
+      const R ph = reinterpret_cast<const R*>(src.phi)[node];
+      const R rho = init.rho ? R(init.rho[node]) : R(1);
+      ra = rho * (R(1) + ph) * R(0.5);
+      rb = rho * (R(1) - ph) * R(0.5);
+    }
+    sp[q] = (ra - rb) / (ra + rb);
+    spa[q] = sc_psi(ra, psi0);
+    spb[q] = sc_psi(rb, psi0);
+  }
+}
+
+// Pull of both component sets (two-set storages): f^A_i, f^B_i and their sums.
+template <int ST, bool WALLFREE, bool IDX32>
+__device__ __forceinline__ void pull_comp(const View<ST>& S, const Geo& g, const Nbr& n, int self,
+                                          typename Store<ST>::R fa[Q], typename Store<ST>::R fb[Q],
+                                          typename Store<ST>::R& rA, typename Store<ST>::R& rB) {
+  using R = typename Store<ST>::R;
+  using I = typename std::conditional<IDX32, unsigned, size_t>::type;
+  const I N = (I)g.N;
+  rA = R(0);
+  rB = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int a = 1 - cx(i), b = 1 - cy(i), c = 1 - cz(i);
+    const bool bb = WALLFREE ? false : (n.sx[a] | n.sy[b] | n.sz[c]);
+    const I src = bb ? (I)self : (I)n.xs[a] + (I)g.nx * ((I)n.ys[b] + (I)g.ny * (I)n.zs[c]);
+    const I dir = bb ? (I)opp(i) : (I)i;
+    fa[i] = decode<ST>(S.f[dir * N + src], i);
+    fb[i] = decode<ST>(S.f[((I)Q + dir) * N + src], i);
+    rA += fa[i];
+    rB += fb[i];
+  }
+}
+
+// The nodes of one tile in the Shan-Chen model: pull both components, the
+// pseudo-potential forces F_A = -psi_A G sum_i w_i psi_B(x + c_i) c_i (= -psi_A
+// (G/3) times the stencil gradient of psi_B; a solid neighbour contributes the
+// node's own psi) and F_B alike, the body force, the common velocity
+// u' = sum_k (j_k + F_k/2)/tau_k / sum_k rho_k/tau_k, then per component BGK
+// towards f^eq(rho_k, u') with the Guo source of F_k, store and send.
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool WALLFREE, bool IDX32>
+__device__ __forceinline__ void step_nodes_sc(const View<ST>& S, const View<ST>& O, const InitBuf& init,
+                                              const Geo& g, const Phys& P, typename Store<ST>::R* __restrict__ fields,
+                                              unsigned* __restrict__ status, const typename Store<ST>::R* sp,
+                                              const typename Store<ST>::R* spa, const typename Store<ST>::R* spb,
+                                              unsigned long long* sw, int x0, int y0, int z0) {
+  using R = typename Store<ST>::R;
+  using L = Layout<R, TX, TY, TZ, 1, 3>;
+  using I = typename std::conditional<IDX32, unsigned, size_t>::type;
+  const I N = (I)g.N;
+  const size_t NF = (size_t)g.N;
+  const R wa = R(1) / R(P.tau_a), wb = R(1) / R(P.tau_b);
+  const R G3 = R(P.G) / R(3);
+  for (int lz = 0; lz < TZ; ++lz) {
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
+    if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
+    const int self = x + g.nx * (y + g.ny * z);
+    if (!WALLFREE && is_solid(g, x, y, z)) {
+      if constexpr (WF) {
+        for (int k = 0; k < NFIELDS; ++k) fields[(size_t)k * NF + self] = R(0);
+      }
+      continue;
+    }
+    Nbr n;
+    make_nbr(g, x, y, z, n);
+    R fa[Q], fb[Q], rA, rB;
+    if constexpr (LOADER == LOAD_PULL) {
+      pull_comp<ST, WALLFREE, IDX32>(S, g, n, self, fa, fb, rA, rB);
+    } else {
+      R f[Q];
+      fields_node<R, true>(init, g, P, n, (long long)self, f, rA, rB, fa, fb);
+    }
+    const int c = (lz + 1) * L::SXY + (threadIdx.y + 1) * L::SX + (threadIdx.x + 1);
+    const int e0 = (lz + 1) * L::EXY + (threadIdx.y + 1) * L::EX + (threadIdx.x + 1);
+    R jA[3] = {R(0), R(0), R(0)}, jB[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (cx(i)) { jA[0] += R(cx(i)) * fa[i]; jB[0] += R(cx(i)) * fb[i]; }
+      if (cy(i)) { jA[1] += R(cy(i)) * fa[i]; jB[1] += R(cy(i)) * fb[i]; }
+      if (cz(i)) { jA[2] += R(cz(i)) * fa[i]; jB[2] += R(cz(i)) * fb[i]; }
+    }
+    R gA[3], gB[3], gphi[3];
+    tile_grad<R, WALLFREE>(spa, c, L::SX, L::SXY, gA);
+    tile_grad<R, WALLFREE>(spb, c, L::SX, L::SXY, gB);
+    R FA[3], FB[3], Fs[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      FA[a] = -spa[c] * G3 * gB[a];
+      FB[a] = -spb[c] * G3 * gA[a];
+      Fs[a] = FA[a] + FB[a];
+    }
+    if (P.g_mode == 1) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        FA[a] += rA * R(P.g[a]);
+        FB[a] += rB * R(P.g[a]);
+      }
+    } else if (P.g_mode == 2) {
+      const R sg = (z == 0 || 2 * z == g.nz) ? R(0) : (2 * z < g.nz ? R(1) : R(-1));
+#pragma unroll
+      for (int a = 0; a < 3; ++a) FA[a] += sg * rA * R(P.g[a]);
+    }
+    const R rho = rA + rB;
+    if (!(rho > R(0) && rho < R(Acc<R>::RHO_MAX))) atomicOr(status, 1u);
+    const R iw = R(1) / (wa * rA + wb * rB);
+    R u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = (wa * (jA[a] + R(0.5) * FA[a]) + wb * (jB[a] + R(0.5) * FB[a])) * iw;
+    if constexpr (WF) {
+      tile_grad<R, WALLFREE>(sp, c, L::SX, L::SXY, gphi);
+      const R irho = R(1) / rho;
+      fields[(size_t)F_PHI * NF + self] = sp[c];
+      fields[(size_t)F_RHO * NF + self] = rho;
+      fields[(size_t)F_UX * NF + self] = (jA[0] + jB[0] + R(0.5) * (FA[0] + FB[0])) * irho;
+      fields[(size_t)F_UY * NF + self] = (jA[1] + jB[1] + R(0.5) * (FA[1] + FB[1])) * irho;
+      fields[(size_t)F_UZ * NF + self] = (jA[2] + jB[2] + R(0.5) * (FA[2] + FB[2])) * irho;
+      fields[(size_t)F_RHOA * NF + self] = rA;
+      fields[(size_t)F_RHOB * NF + self] = rB;
+      fields[(size_t)F_FRX * NF + self] = Fs[0];
+      fields[(size_t)F_FRY * NF + self] = Fs[1];
+      fields[(size_t)F_FRZ * NF + self] = Fs[2];
+      fields[(size_t)F_H * NF + self] = R(0);
+      fields[(size_t)F_GX * NF + self] = gphi[0];
+      fields[(size_t)F_GY * NF + self] = gphi[1];
+      fields[(size_t)F_GZ * NF + self] = gphi[2];
+    }
+    if constexpr (!WS) continue;
+    const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const R ga = R(1) - R(0.5) * wa, gb = R(1) - R(0.5) * wb;
+    const R uFA = u[0] * FA[0] + u[1] * FA[1] + u[2] * FA[2], uFB = u[0] * FB[0] + u[1] * FB[1] + u[2] * FB[2];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R W = wgt<R>(i);
+      R cu = R(0), cFA = R(0), cFB = R(0);
+      if (cx(i)) { cu += R(cx(i)) * u[0]; cFA += R(cx(i)) * FA[0]; cFB += R(cx(i)) * FB[0]; }
+      if (cy(i)) { cu += R(cy(i)) * u[1]; cFA += R(cy(i)) * FA[1]; cFB += R(cy(i)) * FB[1]; }
+      if (cz(i)) { cu += R(cz(i)) * u[2]; cFA += R(cz(i)) * FA[2]; cFB += R(cz(i)) * FB[2]; }
+      const R e = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;  // f^eq_i / (w_i rho_k)
+      // Guo: (1 - 1/(2 tau_k)) w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F_k
+      const R sA = ga * W * (R(3) * (cFA - uFA) + R(9) * cu * cFA);
+      const R sB = gb * W * (R(3) * (cFB - uFB) + R(9) * cu * cFB);
+      const R oa = fa[i] + wa * (W * rA * e - fa[i]) + sA;
+      const R ob = fb[i] + wb * (W * rB * e - fb[i]) + sB;
+      O.f[(I)i * N + (I)self] = encode<ST>(oa, i);
+      O.f[(I)(Q + i) * N + (I)self] = encode<ST>(ob, i);
+      send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, i, oa, ob);
+    }
+  }
+}
+
+// One tile of the Shan-Chen step: clear, stage, step, flush.  Ends with a
+// barrier.
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32>
+__device__ __forceinline__ void step_tile_sc(const View<ST>& S, const View<ST>& O, const InitBuf& init,
+                                             const PhiSrc& src, const AccBufs& ab, const Geo& g, const Phys& P,
+                                             typename Store<ST>::R* __restrict__ fields,
+                                             unsigned* __restrict__ status, unsigned char* smem, int x0, int y0,
+                                             int z0) {
+  using R = typename Store<ST>::R;
+  using L = Layout<R, TX, TY, TZ, 1, 3>;
+  R* sp = reinterpret_cast<R*>(smem);
+  R* spa = sp + L::NS;
+  R* spb = spa + L::NS;
+  unsigned long long* sw = reinterpret_cast<unsigned long long*>(smem + L::off_acc);
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  if constexpr (WS) {
+    for (int lz = 0; lz < TZ; ++lz) {
+      const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
+      if (x < g.nx && y < g.ny && z < g.nz) Acc<R>::zero(ab.zero, (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z));
+    }
+    for (int e = tid; e < Acc<R>::W * L::E; e += TX * TY) sw[e] = 0ull;
+  }
+  if (src.acc) stage_sc<R, true, TX, TY, TZ>(src, init, g, R(P.psi0), sp, spa, spb, x0, y0, z0);
+  else stage_sc<R, false, TX, TY, TZ>(src, init, g, R(P.psi0), sp, spa, spb, x0, y0, z0);
+  __syncthreads();
+  if (!region_walled(g, x0, y0, z0, TX, TY, TZ, 1))
+    step_nodes_sc<ST, LOADER, WS, WF, TX, TY, TZ, true, IDX32>(S, O, init, g, P, fields, status, sp, spa, spb, sw, x0,
+                                                               y0, z0);
+  else
+    step_nodes_sc<ST, LOADER, WS, WF, TX, TY, TZ, false, IDX32>(S, O, init, g, P, fields, status, sp, spa, spb, sw,
+                                                                x0, y0, z0);
+  __syncthreads();
+  if constexpr (WS) {
+    flush_partials<R, TX, TY, TZ, 1>(sw, ab.out, g, x0, y0, z0);
+    __syncthreads();
+  }
+}
+
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32>
+__global__ void __launch_bounds__(TX* TY, 1)
+    k_step_sc(View<ST> S, View<ST> O, InitBuf init, PhiSrc src, AccBufs ab, Geo g, Phys P,
+              typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  step_tile_sc<ST, LOADER, WS, WF, TX, TY, TZ, IDX32>(S, O, init, src, ab, g, P, fields, status, smem_raw,
+                                                      blockIdx.x * TX, blockIdx.y * TY, blockIdx.z * TZ);
 }
 
 // One tile of the step: clear, stage, scan, step, flush.  Ends with a

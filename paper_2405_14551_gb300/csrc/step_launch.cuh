@@ -94,10 +94,44 @@ inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, cons
   });
 }
 
+// Shan-Chen step (two-set storages; one tile shape, one-node halo)
+template <int ST, int LOADER, bool WS, bool WF>
+inline cudaError_t launch_step_sc(const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init, PhiSrc src,
+                                  AccBufs ab, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
+  if constexpr (!Store<ST>::TWOSET) {
+    return cudaErrorInvalidValue;
+  } else {
+    using R = typename Store<ST>::R;
+    constexpr int TX = 32, TY = 8, TZ = 4;
+    const size_t smem = Layout<R, TX, TY, TZ, 1, 3>::bytes;
+    auto kern = fits_idx32(g.N) ? k_step_sc<ST, LOADER, WS, WF, TX, TY, TZ, true>
+                                : k_step_sc<ST, LOADER, WS, WF, TX, TY, TZ, false>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
+    trace_kernel("k_step_sc", kern, grid, dim3(TX, TY), smem);
+    kern<<<grid, dim3(TX, TY), smem, st>>>(view<ST>(in), view<ST>(out), init, src, ab, g, p,
+                                           reinterpret_cast<R*>(fields), status);
+    return cudaGetLastError();
+  }
+}
+
 template <int ST>
 cudaError_t launch_step_s(int loader, bool ws, bool wf, int tile, const Geo& g, const Phys& p, const StateBuf& in,
                           const InitBuf& init, PhiSrc src, AccBufs ab, StateBuf out, void* fields, unsigned* status,
                           cudaStream_t st) {
+  if (p.model == 1) {
+    if (loader == LOAD_PULL) {
+      if (ws && !wf) return launch_step_sc<ST, LOAD_PULL, true, false>(g, p, in, init, src, ab, out, fields, status, st);
+      if (!ws && wf) return launch_step_sc<ST, LOAD_PULL, false, true>(g, p, in, init, src, ab, out, fields, status, st);
+    } else {
+      if (ws && !wf) return launch_step_sc<ST, LOAD_FIELDS, true, false>(g, p, in, init, src, ab, out, fields, status, st);
+      if (!ws && wf) return launch_step_sc<ST, LOAD_FIELDS, false, true>(g, p, in, init, src, ab, out, fields, status, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   if (loader == LOAD_PULL) {
     if (ws && !wf) return launch_step_tiles<ST, LOAD_PULL, true, false>(tile, g, p, in, init, src, ab, out, fields, status, st);
     if (!ws && wf) return launch_step_tiles<ST, LOAD_PULL, false, true>(0, g, p, in, init, src, ab, out, fields, status, st);

@@ -47,6 +47,9 @@ class lb_params(ctypes.Structure):
         ("g_mode", ctypes.c_int32),
         ("storage", ctypes.c_int32),
         ("collision", ctypes.c_int32),
+        ("model", ctypes.c_int32),
+        ("G", ctypes.c_double),
+        ("psi0", ctypes.c_double),
     ]
 
 
@@ -195,7 +198,9 @@ def make_grid(nx, ny, nz, walls=0) -> lb_grid:
 
 
 def make_params(tau_a=1.0, tau_b=1.0, A_a=0.01, A_b=0.01, beta=0.7, A_h=0.0, h_min=3.0, h_max=3.0, phi_I=0.9,
-                g=(0.0, 0.0, 0.0), g_mode=0, storage="twoset_f32", collision=0) -> lb_params:
+                g=(0.0, 0.0, 0.0), g_mode=0, storage="twoset_f32", collision=0, model=0, G=0.0,
+                psi0=1.0) -> lb_params:
+    """model 0: colour gradient; model 1: Shan-Chen (G, psi0; two-set storages only)."""
     st = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p = lb_params()
     p.tau_a, p.tau_b, p.A_a, p.A_b, p.beta = tau_a, tau_b, A_a, A_b, beta
@@ -204,6 +209,7 @@ def make_params(tau_a=1.0, tau_b=1.0, A_a=0.01, A_b=0.01, beta=0.7, A_h=0.0, h_m
     p.g_mode = int(g_mode)
     p.storage = st
     p.collision = int(collision)
+    p.model, p.G, p.psi0 = int(model), float(G), float(psi0)
     return p
 
 

@@ -60,6 +60,11 @@ def test_validation_without_gpu(lib):
         (L.make_grid(4, 4, 4), L.make_params(storage="moment_f32")),  # moment storage needs collision = 1
         (L.make_grid(4, 4, 4), L.make_params(g=(float("nan"), 0.0, 0.0))),
         (L.make_grid(1 << 11, 1 << 11, 1 << 10), L.make_params()),
+        (L.make_grid(4, 4, 4), L.make_params(model=2)),
+        (L.make_grid(4, 4, 4), L.make_params(model=1, G=7.5, storage="reduced_f32")),  # Shan-Chen needs two sets
+        (L.make_grid(4, 4, 4), L.make_params(model=1, G=7.5, A_h=0.1)),
+        (L.make_grid(4, 4, 4), L.make_params(model=1, G=7.5, collision=1)),
+        (L.make_grid(4, 4, 4), L.make_params(model=1, G=7.5, psi0=0.0)),
     ]
     for grid, params in bad:
         with pytest.raises(L.LBError) as ei:
@@ -109,6 +114,17 @@ def test_conv_argument_checks_without_gpu(lib):
                                      None) == L.LB_EINVAL  # ny % 16
     assert lib.lbnn_conv3d_fwd_upcat(buf, 32, buf, 64, buf, None, buf, None, 32, 0, 16, 16, 3, 1, 0, 1, st,
                                      None) == L.LB_EINVAL  # odd nz
+
+
+def test_model_constants_agree_between_header_and_binding():
+    import re
+
+    import paper_2405_14551_gb300.lbcg as L
+    h = open(os.path.join(ROOT, "include", "lbcg.h")).read()
+    consts = dict(re.findall(r"#define (LB_MODEL_\w+) (\d+)", h))
+    assert consts == {"LB_MODEL_COLOUR_GRADIENT": "0", "LB_MODEL_SHAN_CHEN": "1"}
+    names = [f[0] for f in L.lb_params._fields_]
+    assert names[-3:] == ["model", "G", "psi0"]
 
 
 def test_storage_formats_agree_between_header_and_binding():

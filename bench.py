@@ -308,7 +308,7 @@ def other_storages(args, L, make, stream, tile, world, nodes, maxall, peak):
         s2.step(3)
         best, t2ms = tile, None
         if not args.no_tune:  # the tile of each storage tuned on its own
-            for tl in range(5):
+            for tl in range(L.NUM_TILES):
                 L.lb_set_tile(s2.h, tl)
                 s2.step(2)
                 km = L.lb_step_timed(s2.h, 4)
@@ -335,6 +335,35 @@ def other_storages(args, L, make, stream, tile, world, nodes, maxall, peak):
         del s2
         torch.cuda.empty_cache()
     return extra
+
+
+def shan_chen_extra(args, L, wl, stream, world, nodes, maxall, peak):
+    """The Shan-Chen model (Sec. III.C.3; G = 7.5, psi_0 = 1, tau = 1, the
+    emulsion's phi and body force) on the same grid in FP32 two-set storage:
+    one kernel per step, 432 B per node update like the colour-gradient
+    step."""
+    import torch
+    nx, ny, nz = wl.shape
+    p = dict(wl.params, A_h=0.0, A_a=0.0, A_b=0.0, beta=0.0, model=1, G=7.5, psi0=1.0)
+    s = L.Sim(nx, ny, nz, walls=wl.walls, stream=stream, storage="twoset_f32", **p)
+    s.init_fields(wl.phi)
+    s.step(max(3, args.warmup))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s.check()
+    m = maxall(e0.elapsed_time(e1))
+    v = world * nodes * args.steps / (m / 1e3) / 1e6
+    km = L.lb_step_timed(s.h, 20)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"MLUPS": round(v, 1), "bytes_per_node": 432, "whole_step_frac": round(432 * v * 1e6 / world / 1e9 / peak, 4),
+            "step_kernel_ms": round(km, 4), "step_kernel_GBps": round(432 * nodes / (km / 1e3) / 1e9, 1),
+            "params": {"G": 7.5, "psi0": 1.0, "tau": 1.0}}
 
 
 def batch_extra(args, L, W, stream):
@@ -671,7 +700,7 @@ def main():
     # autotune the tile of the step kernel: time every shape, keep the fastest
     tile_ms = []
     sim.step(max(3, args.warmup))
-    for tile in range(0 if args.no_tune else 5):
+    for tile in range(0 if args.no_tune else L.NUM_TILES):
         L.lb_set_tile(sim.h, tile)
         sim.step(12)
         tile_ms.append(L.lb_step_timed(sim.h, 6))
@@ -711,6 +740,8 @@ def main():
     del sim
     torch.cuda.empty_cache()
     extra = {} if args.no_extra else other_storages(args, L, make, stream, best_tile, world, nodes, maxall, peak)
+    if not args.no_extra:
+        extra["shan_chen_twoset_f32"] = shan_chen_extra(args, L, wl, stream, world, nodes, maxall, peak)
     if not args.no_extra:
         extra["fp32_alu"] = {"sgemm_tflops": fp32_alu_peak(),
                              "how": "cuBLAS SGEMM 8192^3 with TF32 off, best of 5 (FMA pipes only)"}

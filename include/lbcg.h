@@ -179,7 +179,7 @@ int lb_step(lb_handle* h, int64_t nsteps);
 
 /* Choose the tile shape of the step kernel (0..4: 32x8x4, 32x8x8, 32x8x4
  * with a register cap for 3 CTAs per SM, 32x8x6 capped for 3 CTAs per SM,
- * 32x8x4 capped for 4 CTAs per SM, nodes per CTA); used by the autotuner.
+ * 32x4x4 capped for 6 CTAs per SM, nodes per CTA); used by the autotuner.
  * Results do not depend on the tile (bit for bit).  lb_get_tile returns the
  * current index. */
 int lb_set_tile(lb_handle* h, int tile);

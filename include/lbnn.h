@@ -22,6 +22,23 @@
 extern "C" {
 #endif
 
+/* Poll limit of the bounded handshake waits (copies -> UMMAs -> epilogue)
+ * inside the convolution kernels launched after this call (a kernel takes the
+ * value at launch; a captured CUDA graph keeps the value of its capture).  A
+ * wait that runs out makes the kernel give up: it still waits, with a fixed
+ * bound of its own, for every UMMA it has committed, frees its tensor memory,
+ * sets bit 4 of the status word and leaves its output unwritten or partial.
+ * limit = 0 gives up at the first wait (exercises that path).  The default is
+ * LBNN_WAIT_LIMIT_DEFAULT.  previous (may be NULL) receives the limit in force
+ * before the call.  Process-wide; returns LB_OK. */
+#define LBNN_WAIT_LIMIT_DEFAULT (1u << 22)
+int lbnn_set_wait_limit(uint32_t limit, uint32_t* previous);
+
+/* Reads the status word of the calls above (device pointer) after
+ * synchronising `stream`, clears it, and returns LB_ETIMEOUT if bit 4 was set
+ * (a bounded wait gave up), LB_ECUDA on a CUDA error, else LB_OK. */
+int lbnn_check_status(unsigned* status, void* stream);
+
 /* y[v][co] = act(bias[co] + sum_{t<taps, ci} w[co][t][ci] x[v + off_t][ci]),
  * taps = 27 (3x3x3, tap t = (dx+1) + 3(dy+1) + 9(dz+1)) or 1 (1x1x1).
  * cin, cout: multiples of 16 (cin <= 1024, cout <= 256).  bias may be NULL;

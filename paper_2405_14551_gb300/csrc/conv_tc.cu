@@ -20,6 +20,7 @@
 // up sets bit 4 of the status word.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/lbcg.h"
@@ -36,6 +37,9 @@ struct ConvGeo {
 
 constexpr int CONV_M = 128;
 constexpr unsigned CONV_TIMEOUT = 16u;
+// Polls of a drain wait (all committed UMMAs done before tensor memory is
+// freed); the handshake waits take their limit from the launch.
+constexpr uint32_t CONV_DRAIN_SPIN = 1u << 22;
 
 __device__ __forceinline__ long long conv_nbr(const ConvGeo& g, int b, int x, int y, int z, int dx, int dy, int dz) {
   x += dx;
@@ -69,7 +73,7 @@ template <int NT>
 __global__ void __launch_bounds__(128, 1)
     k_conv_fwd(const __nv_bfloat16* __restrict__ X, int Cin, const __nv_bfloat16* __restrict__ W,
                const float* __restrict__ bias, __nv_bfloat16* __restrict__ Y, float* __restrict__ Yf, int Cout, int ldy,
-               int KC, ConvGeo g, int relu, unsigned* __restrict__ status) {
+               int KC, ConvGeo g, int relu, unsigned spin, unsigned* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int t = threadIdx.x;
   const int warp = t >> 5;
@@ -113,11 +117,12 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t idesc = tc::idesc_bf16(CONV_M, Cout, false, false);
   const uint32_t a_lbo = CONV_M * 16, b_lbo = (uint32_t)Cout * 16;
   bool ok = true;
+  int issued = 0;  // chunks whose UMMAs were issued and committed
 
   for (int ch = 0; ch < nchunks; ++ch) {
     const int buf = ch & 1;
     if (ch >= 2) {  // the UMMAs that read this buffer two chunks ago must be done
-      bool w = tc::mbar_wait(&bar[buf], (uint32_t)(((ch >> 1) - 1) & 1), 1u << 22);
+      bool w = tc::mbar_wait(&bar[buf], (uint32_t)(((ch >> 1) - 1) & 1), spin);
       ok = __syncthreads_and(w);
       if (!ok) break;
     }
@@ -150,11 +155,16 @@ __global__ void __launch_bounds__(128, 1)
       }
       tc::mma_commit(&bar[buf]);
     }
+    issued = ch + 1;
   }
-  // all UMMAs: the last commit covers every earlier one of the issuing thread
-  const int last = nchunks - 1;
-  bool done = tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), 1u << 22);
-  if (!done) done = tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), 1u << 22);  // second bounded wait
+  // every committed UMMA, also after a give-up: the last commit covers every
+  // earlier one of the issuing thread; the drain has its own fixed bound
+  bool done = true;
+  if (issued > 0) {
+    const int last = issued - 1;
+    done = tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), CONV_DRAIN_SPIN);
+    if (!done) done = tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), CONV_DRAIN_SPIN);
+  }
   ok = __syncthreads_and(ok && done);
   tc::fence_after_sync();
   if (ok) {
@@ -233,7 +243,6 @@ constexpr int PCONV_MMA_WARP = 8;
 constexpr int PCONV_MAXWP = 8;    // weight pieces per copy thread and step (3 CT or CT rows x KC / 8 <= 1024)
 constexpr int PCONV_LAG = 5;      // steps a copy thread keeps in flight before it signals them
 constexpr int PCONV_NSW_MAX = 8;  // weight ring slots (at most)
-constexpr uint32_t PCONV_SPIN = 1u << 22;
 
 __device__ __forceinline__ int wrap_or_pad(int c, int n, int periodic) {
   if (c >= 0 && c < n) return c;
@@ -244,8 +253,8 @@ __device__ __forceinline__ int wrap_or_pad(int c, int n, int periodic) {
 // Bounded wait that also gives up once another role has given up.
 // After a few polls the waiting warp backs off briefly, so that idle roles do
 // not crowd the shared-memory pipe that the copies and the UMMAs use.
-__device__ __forceinline__ bool pconv_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t it = 0; it < PCONV_SPIN; ++it) {
+__device__ __forceinline__ bool pconv_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (tc::mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u && *abort_flag) return false;
     if (it >= 16) __nanosleep(32);
@@ -264,6 +273,7 @@ struct PConvArgs {
   int Cin, Cout, ldy, KC, CT, nsw;
   ConvGeo g;
   int relu;
+  unsigned spin;  // polls of a handshake wait before it gives up
   unsigned* status;
 };
 
@@ -372,7 +382,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
         const int c0 = c * KC;
         for (int st = 0; st < SPC; ++st, ++gs) {
           const int slot = gs % nsw;
-          if (gs >= nsw && !pconv_wait(&w_empty[slot], (uint32_t)(((gs / nsw) - 1) & 1), abort_flag)) {
+          if (gs >= nsw && !pconv_wait(&w_empty[slot], (uint32_t)(((gs / nsw) - 1) & 1), abort_flag, P.spin)) {
             ok = false;
             break;
           }
@@ -383,7 +393,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
             if (woff[i] >= 0) tc::cp_async16(wdst + wdo[i], wsrc + woff[i], true);
           if (st == 0) {
             const int cg = gs / SPC;
-            if (cg >= 2 && !pconv_wait(&h_empty[cg & 1], (uint32_t)(((cg >> 1) - 1) & 1), abort_flag)) {
+            if (cg >= 2 && !pconv_wait(&h_empty[cg & 1], (uint32_t)(((cg >> 1) - 1) & 1), abort_flag, P.spin)) {
               ok = false;
               break;
             }
@@ -442,7 +452,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
       uint32_t wphase = 0;
       for (int k = 0; k < my_items && ok; ++k) {
         const int ab = k & 1;
-        if (k >= 2 && !pconv_wait(&a_empty[ab], (uint32_t)(((k >> 1) - 1) & 1), abort_flag)) {
+        if (k >= 2 && !pconv_wait(&a_empty[ab], (uint32_t)(((k >> 1) - 1) & 1), abort_flag, P.spin)) {
           ok = false;
           break;
         }
@@ -450,13 +460,13 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
         const uint32_t acc = tmem + (uint32_t)(ab * TZ * CT);
         for (int c = 0; c < nchunks && ok; ++c) {
           const int cg = gs / SPC;
-          if (!pconv_wait(&h_full[cg & 1], (uint32_t)((cg >> 1) & 1), abort_flag)) {
+          if (!pconv_wait(&h_full[cg & 1], (uint32_t)((cg >> 1) & 1), abort_flag, P.spin)) {
             ok = false;
             break;
           }
           const uint32_t hb = tc::smem_u32(sH + (size_t)(cg & 1) * halo_bytes);
           for (int st = 0; st < SPC; ++st, ++gs) {
-            if (!pconv_wait(&w_full[slot], wphase, abort_flag)) {
+            if (!pconv_wait(&w_full[slot], wphase, abort_flag, P.spin)) {
               ok = false;
               break;
             }
@@ -511,7 +521,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
       }
       // every UMMA issued so far has completed before the CTA winds down
       tc::mma_commit(fin);
-      if (!tc::mbar_wait(fin, 0u, PCONV_SPIN)) ok = false;
+      if (!tc::mbar_wait(fin, 0u, CONV_DRAIN_SPIN)) ok = false;
       if (!ok) {
         *abort_flag = 1;
         atomicOr(P.status, CONV_TIMEOUT);
@@ -525,7 +535,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_fwd_pipe(PConvArgs P)
     for (int k = 0; k < my_items; ++k) {
       const int ab = k & 1;
       // warp-uniform, so that the warp's tensor-memory loads stay converged
-      if (!__all_sync(0xffffffffu, pconv_wait(&a_full[ab], (uint32_t)((k >> 1) & 1), abort_flag))) {
+      if (!__all_sync(0xffffffffu, pconv_wait(&a_full[ab], (uint32_t)((k >> 1) & 1), abort_flag, P.spin))) {
         *abort_flag = 1;
         atomicOr(P.status, CONV_TIMEOUT);
         break;
@@ -609,6 +619,7 @@ struct WConvArgs {
   int CH, CP, Cin, o2;
   int CN, TG, ngroups, nchunks, blocks_per_cta, nst;  // nst: staged blocks in flight (2..4)
   ConvGeo g;
+  unsigned spin;  // polls of a handshake wait before it gives up
   unsigned* status;
 };
 
@@ -680,7 +691,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
     bool ok = true;
     for (int i = 0; i < nmine && ok; ++i) {
       const int s = i % nst;
-      if (i >= nst && !pconv_wait(&empty[s], (uint32_t)(((i / nst) - 1) & 1), abort_flag)) {
+      if (i >= nst && !pconv_wait(&empty[s], (uint32_t)(((i / nst) - 1) & 1), abort_flag, P.spin)) {
         ok = false;
         break;
       }
@@ -731,7 +742,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
       bool ok = true;
       for (int i = 0; i < nmine; ++i) {
         const int s = i % nst;
-        if (!pconv_wait(&full[s], (uint32_t)((i / nst) & 1), abort_flag)) {
+        if (!pconv_wait(&full[s], (uint32_t)((i / nst) & 1), abort_flag, P.spin)) {
           ok = false;
           break;
         }
@@ -750,6 +761,9 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
         tc::mma_commit(&empty[s]);
       }
       tc::mma_commit(done);  // every UMMA of this CTA, or none
+      // drained here too, so that tensor memory outlives every committed UMMA
+      // even when the epilogue's wait gives up
+      if (!tc::mbar_wait(done, 0u, CONV_DRAIN_SPIN)) ok = false;
       if (!ok) {
         *abort_flag = 1;
         atomicOr(P.status, CONV_TIMEOUT);
@@ -758,7 +772,7 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
     __syncwarp();
   } else if (warp < PCONV_EPI / 32) {
     // ------------------------------------------------------------ epilogue
-    bool ok = __all_sync(0xffffffffu, pconv_wait(done, 0u, abort_flag));
+    bool ok = __all_sync(0xffffffffu, pconv_wait(done, 0u, abort_flag, P.spin));
     ok = __all_sync(0xffffffffu, ok && *abort_flag == 0);  // no partial sums after a give-up
     tc::fence_after_sync();
     const int m = t;
@@ -806,7 +820,8 @@ __global__ void __launch_bounds__(PCONV_THREADS, 1) k_conv_wgrad_pipe(WConvArgs 
 template <int NT>
 __global__ void __launch_bounds__(128, 1)
     k_conv_wgrad(const __nv_bfloat16* __restrict__ dY, int Cout, const __nv_bfloat16* __restrict__ X, int Cin,
-                 float* __restrict__ dW, ConvGeo g, long long vox_per_cta, unsigned* __restrict__ status) {
+                 float* __restrict__ dW, ConvGeo g, long long vox_per_cta, unsigned spin,
+                 unsigned* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int KV = 64;  // voxels per stage (the GEMM K)
   const int t = threadIdx.x;
@@ -849,11 +864,12 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t b_lbo = b_k, b_sbo = b_mn;
   const uint32_t idesc = tc::idesc_bf16(CONV_M, Cout, true, true);
   bool ok = true;
+  int issued = 0;  // chunks whose UMMAs were issued and committed
 
   for (int ch = 0; ch < nchunks; ++ch) {
     const int buf = ch & 1;
     if (ch >= 2) {
-      bool w = tc::mbar_wait(&bar[buf], (uint32_t)(((ch >> 1) - 1) & 1), 1u << 22);
+      bool w = tc::mbar_wait(&bar[buf], (uint32_t)(((ch >> 1) - 1) & 1), spin);
       ok = __syncthreads_and(w);
       if (!ok) break;
     }
@@ -900,11 +916,15 @@ __global__ void __launch_bounds__(128, 1)
       }
       tc::mma_commit(&bar[buf]);
     }
+    issued = ch + 1;
   }
-  if (nchunks > 0) {
-    const int last = nchunks - 1;
-    bool done = tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), 1u << 22);
-    if (!done) done = tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), 1u << 22);
+  if (nchunks > 0) {  // every committed UMMA (fixed bound, also after a give-up)
+    bool done = true;
+    if (issued > 0) {
+      const int last = issued - 1;
+      done = tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), CONV_DRAIN_SPIN);
+      if (!done) done = tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), CONV_DRAIN_SPIN);
+    }
     ok = __syncthreads_and(ok && done);
   }
   tc::fence_after_sync();
@@ -930,6 +950,10 @@ __global__ void __launch_bounds__(128, 1)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// Poll limit of the handshake waits of the next launches (lbnn_set_wait_limit).
+static std::atomic<uint32_t> g_wait_limit{LBNN_WAIT_LIMIT_DEFAULT};
+static uint32_t wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
 // Dynamic shared memory of a conv CTA: the staged operands, raised where
 // needed so that no more CTAs share an SM than their tensor-memory
 // allocations (ncols columns each, 512 per SM) fit side by side; an
@@ -1022,7 +1046,7 @@ static int conv_fwd_pipe(const void* x, int cs, const void* x2, int cin, const v
   if (!c.tz) return report_error(LB_EINVAL, "conv fwd: no tiled configuration fits shared memory");
   const size_t smem = conv_smem(pconv_smem_need(c.tz, c.kc, c.ct, c.merge, c.nsw), 2 * c.tz * c.ct);
   PConvArgs a{(const __nv_bfloat16*)x, (const __nv_bfloat16*)x2, cs, (const __nv_bfloat16*)w, bias,
-              (__nv_bfloat16*)y, yf, cin, cout, ldy, c.kc, c.ct, c.nsw, g, relu, status};
+              (__nv_bfloat16*)y, yf, cin, cout, ldy, c.kc, c.ct, c.nsw, g, relu, wait_limit(), status};
   cudaError_t e = cudaSuccess;
   auto launch = [&](auto kern) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1091,7 +1115,7 @@ static int conv_wgrad_pipe(const void* dy, int cout, const void* x, int cin, flo
   if (nst < 2) return report_error(LB_EINVAL, "conv wgrad: staging does not fit shared memory");
   const size_t smem = conv_smem((size_t)nst * stage + 128, o.TG * o.CN);
   WConvArgs args{(const __nv_bfloat16*)(o.o2 ? dy : x), (const __nv_bfloat16*)(o.o2 ? x : dy), dw, o.CH, o.CP, cin,
-                 o.o2, o.CN, o.TG, o.ngroups, o.nchunks, (int)per, nst, g, status};
+                 o.o2, o.CN, o.TG, o.ngroups, o.nchunks, (int)per, nst, g, wait_limit(), status};
   cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     k_conv_wgrad_pipe<<<dim3((unsigned)slices, (unsigned)npass), PCONV_THREADS, smem, st>>>(args);
@@ -1113,6 +1137,24 @@ static int pick_kc(int Cin) {
 using namespace lbcg;
 
 extern "C" {
+
+int lbnn_set_wait_limit(uint32_t limit, uint32_t* previous) {
+  const uint32_t old = g_wait_limit.exchange(limit);
+  if (previous) *previous = old;
+  return LB_OK;
+}
+
+int lbnn_check_status(unsigned* status, void* stream) {
+  if (!status) return report_error(LB_EINVAL, "null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, status, sizeof(word), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(word), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return report_error(LB_ECUDA, std::string("conv status: ") + cudaGetErrorString(e));
+  if (word & CONV_TIMEOUT) return report_error(LB_ETIMEOUT, "a convolution gave up a bounded wait");
+  return LB_OK;
+}
 
 int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, const float* bias, void* y, float* yf,
                     int32_t cout, int32_t ldy, int32_t nx, int32_t ny, int32_t nz, int32_t nb, uint32_t periodic,
@@ -1140,12 +1182,12 @@ int lbnn_conv3d_fwd(const void* x, int32_t cin, const void* w, int32_t taps, con
     e = cudaFuncSetAttribute(k_conv_fwd<27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       k_conv_fwd<27><<<blocks, CONV_M, smem, st>>>((const __nv_bfloat16*)x, cin, (const __nv_bfloat16*)w, bias,
-                                                   (__nv_bfloat16*)y, yf, cout, ldy, KC, g, relu, status);
+                                                   (__nv_bfloat16*)y, yf, cout, ldy, KC, g, relu, wait_limit(), status);
   } else {
     e = cudaFuncSetAttribute(k_conv_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       k_conv_fwd<1><<<blocks, CONV_M, smem, st>>>((const __nv_bfloat16*)x, cin, (const __nv_bfloat16*)w, bias,
-                                                  (__nv_bfloat16*)y, yf, cout, ldy, KC, g, relu, status);
+                                                  (__nv_bfloat16*)y, yf, cout, ldy, KC, g, relu, wait_limit(), status);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return report_error(LB_ECUDA, std::string("conv fwd: ") + cudaGetErrorString(e));
@@ -1194,12 +1236,12 @@ int lbnn_conv3d_wgrad(const void* dy, int32_t cout, const void* x, int32_t cin, 
     e = cudaFuncSetAttribute(k_conv_wgrad<27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       k_conv_wgrad<27><<<grid, 128, smem, st>>>((const __nv_bfloat16*)dy, cout, (const __nv_bfloat16*)x, cin, dw, g,
-                                                vox_per_cta, status);
+                                                vox_per_cta, wait_limit(), status);
   } else {
     e = cudaFuncSetAttribute(k_conv_wgrad<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       k_conv_wgrad<1><<<grid, 128, smem, st>>>((const __nv_bfloat16*)dy, cout, (const __nv_bfloat16*)x, cin, dw, g,
-                                               vox_per_cta, status);
+                                               vox_per_cta, wait_limit(), status);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return report_error(LB_ECUDA, std::string("conv wgrad: ") + cudaGetErrorString(e));

@@ -1150,11 +1150,18 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
         const typename Store<ST>::E ep = encode<ST>(fsp, p), eq = encode<ST>(fsq, q);
         O.f[(I)p * N + (I)self] = ep;
         O.f[(I)q * N + (I)self] = eq;
-        R va, vb;
-        colour_split<R, false>(decode<ST>(ep, p), svo, p, false, va, vb);
-        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, p, va, vb);
-        colour_split<R, false>(decode<ST>(eq, q), svo, q, false, va, vb);
-        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, q, va, vb);
+        // colour_split of p and of its opposite q: c_q.v = -(c_p.v) exactly,
+        // so the segregation term is formed once and negated (bit for bit
+        // what colour_split gives for q)
+        R cv = R(0);
+        if (cx(p)) cv += R(cx(p)) * R(svo.y);
+        if (cy(p)) cv += R(cy(p)) * R(svo.z);
+        if (cz(p)) cv += R(cz(p)) * R(svo.w);
+        const R seg = mul_rn(W * inv_norm<R>(p), cv);
+        const R dp = decode<ST>(ep, p), dq = decode<ST>(eq, q);
+        const R vap = fma_rn(R(svo.x), dp, seg), vaq = fma_rn(R(svo.x), dq, -seg);
+        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, p, vap, dp - vap);
+        send<R, WALLFREE, L::EX, L::EXY, L::E>(sw, e0, n, q, vaq, dq - vaq);
       }
     }
   }
@@ -1410,7 +1417,7 @@ __device__ __forceinline__ void step_tile_sc(const View<ST>& S, const View<ST>& 
 }
 
 template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, bool IDX32>
-__global__ void __launch_bounds__(TX* TY, 1)
+__global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : 2)
     k_step_sc(View<ST> S, View<ST> O, InitBuf init, PhiSrc src, AccBufs ab, Geo g, Phys P,
               typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

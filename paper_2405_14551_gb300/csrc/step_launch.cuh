@@ -86,7 +86,7 @@ inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, cons
         case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8, H>(g, p, in, init, src, ab, out, fields, status, st);
         case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, H, 3>(g, p, in, init, src, ab, out, fields, status, st);
         case 3: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 6, H, 3>(g, p, in, init, src, ab, out, fields, status, st);
-        case 4: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, H, 4>(g, p, in, init, src, ab, out, fields, status, st);
+        case 4: return launch_step_t<ST, LOADER, WS, WF, 32, 4, 4, H, 6>(g, p, in, init, src, ab, out, fields, status, st);
         default: break;
       }
     }
@@ -181,7 +181,7 @@ inline cudaError_t launch_batched_tiles(int tile, int halo, const RunDesc* d_run
         case 1: return launch_batched_step_t<ST, 32, 8, 8, H, IDX32>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
         case 2: return launch_batched_step_t<ST, 32, 8, 4, H, IDX32, 3>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
         case 3: return launch_batched_step_t<ST, 32, 8, 6, H, IDX32, 3>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
-        case 4: return launch_batched_step_t<ST, 32, 8, 4, H, IDX32, 4>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
+        case 4: return launch_batched_step_t<ST, 32, 4, 4, H, IDX32, 6>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
         default: break;
       }
     }

@@ -109,6 +109,8 @@ _SIGS = {
     "lb_batch_check": (ctypes.c_int, [ctypes.c_void_p]),
     "lb_reduce_fields_f64_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
                                                    ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+    "lbnn_set_wait_limit": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+    "lbnn_check_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lbnn_conv3d_fwd": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
@@ -300,6 +302,9 @@ def lb_copy_state(dst, src):
     _check(load_library().lb_copy_state(dst, src), "lb_copy_state")
 
 
+NUM_TILES = 5  # tile shapes of lb_set_tile and lb_batch_set_tile
+
+
 def lb_set_tile(h, tile: int):
     _check(load_library().lb_set_tile(h, int(tile)), "lb_set_tile")
 
@@ -365,6 +370,22 @@ def lb_reduce_fields_f64_static(fields_ptr: int, fields_are_f64: bool, nx: int, 
                                                       int(ny), int(nz), int(walls), ctypes.c_void_p(out_ptr),
                                                       ctypes.c_void_p(stream_ptr)),
            "lb_reduce_fields_f64_static")
+
+
+LBNN_WAIT_LIMIT_DEFAULT = 1 << 22
+
+
+def lbnn_set_wait_limit(limit: int) -> int:
+    """Poll limit of the convolutions' handshake waits; returns the previous one."""
+    prev = ctypes.c_uint32(0)
+    _check(load_library().lbnn_set_wait_limit(int(limit), ctypes.byref(prev)), "lbnn_set_wait_limit")
+    return int(prev.value)
+
+
+def lbnn_check_status(status_ptr: int, stream_ptr: int = 0):
+    """Reads and clears a convolution status word; LBError(LB_ETIMEOUT) after a give-up."""
+    _check(load_library().lbnn_check_status(ctypes.c_void_p(status_ptr), ctypes.c_void_p(stream_ptr)),
+           "lbnn_check_status")
 
 
 def lb_launch_count() -> int:

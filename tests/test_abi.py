@@ -116,6 +116,22 @@ def test_conv_argument_checks_without_gpu(lib):
                                      None) == L.LB_EINVAL  # odd nz
 
 
+def test_conv_wait_limit_setting_without_gpu(lib):
+    """The convolutions' wait limit is a process-wide host setting: it starts
+    at the header's default, a set returns the previous value, and a null
+    status word is rejected before any CUDA call."""
+    import paper_2405_14551_gb300.lbcg as L
+    with open(os.path.join(ROOT, "include", "lbnn.h")) as f:
+        hdr = f.read()
+    m = re.search(r"#define LBNN_WAIT_LIMIT_DEFAULT \(1u << (\d+)\)", hdr)
+    assert m and L.LBNN_WAIT_LIMIT_DEFAULT == 1 << int(m.group(1))
+    prev = L.lbnn_set_wait_limit(0)
+    assert prev == L.LBNN_WAIT_LIMIT_DEFAULT
+    assert L.lbnn_set_wait_limit(prev) == 0
+    assert L.lbnn_set_wait_limit(prev) == prev
+    assert lib.lbnn_check_status(None, None) == L.LB_EINVAL
+
+
 def test_model_constants_agree_between_header_and_binding():
     import re
 

@@ -158,7 +158,7 @@ def test_tile_shapes_give_identical_results():
     import paper_2405_14551_gb300.lbcg as L
     wl = W.droplet_pair(48, 40, 56, R=8.0, sep=20.0)
     ref = None
-    for tile in range(5):
+    for tile in range(L.NUM_TILES):
         s = make_gpu(wl)
         L.lb_set_tile(s.h, tile)
         assert L.lb_get_tile(s.h) == tile

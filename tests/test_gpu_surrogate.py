@@ -290,3 +290,63 @@ def test_native_surrogate_matches_python_driver():
     for k in fr:
         np.testing.assert_array_equal(fs[k], fr[k])
     assert sim.t == 0
+
+
+@pytest.mark.parametrize("kind,dims", [("fwd", (12, 12, 4, 1)), ("fwd", (16, 16, 4, 1)),
+                                       ("wgrad", (12, 12, 4, 1)), ("wgrad", (16, 16, 4, 1))])
+def test_conv_bounded_wait_gives_up_cleanly(kind, dims):
+    """With a wait limit of 0 every handshake wait of the convolutions gives
+    up at its first poll (12 x 12 grids take the two-buffer kernels, whose
+    third channel chunk waits for the first one's UMMAs; 16 x 16 grids take
+    the warp-specialised kernels, whose UMMA and epilogue roles wait for the
+    copies).  The kernel must then drain what it committed, free its tensor
+    memory and return: the status word carries bit 4, lbnn_check_status maps
+    it to LB_ETIMEOUT and clears it, the output is left unwritten, and the
+    same call with the default limit right after gives the reference result
+    on the same context."""
+    import torch
+    import paper_2405_14551_gb300.lbcg as L
+    lib = L.load_library()
+    rng = np.random.default_rng(11)
+    nx, ny, nz, nb = dims
+    cin, cout = 32, 32
+    X = _bf(rng.standard_normal((nb, nz, ny, nx, cin)))
+    W = _bf(rng.standard_normal((cout, 27, cin)) / np.sqrt(27 * cin))
+    G = _bf(rng.standard_normal((nb, nz, ny, nx, cout)))
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).to(dev)
+    Wd = torch.from_numpy(W.astype(np.float32)).to(torch.bfloat16).to(dev)
+    Gd = torch.from_numpy(G.astype(np.float32)).to(torch.bfloat16).to(dev)
+    st = torch.zeros(4, dtype=torch.int32, device=dev)
+    out = (torch.full((nb, nz, ny, nx, cout), 7.0, dtype=torch.float32, device=dev) if kind == "fwd"
+           else torch.zeros((cout, 27, cin), dtype=torch.float32, device=dev))
+
+    def call():
+        if kind == "fwd":
+            return lib.lbnn_conv3d_fwd(Xd.data_ptr(), cin, Wd.data_ptr(), 27, None, None, out.data_ptr(), cout, 0,
+                                       nx, ny, nz, nb, 7, 0, st.data_ptr(), None)
+        # 192 voxels per CTA: three chunks of 64, so the third one waits
+        return lib.lbnn_conv3d_wgrad(Gd.data_ptr(), cout, Xd.data_ptr(), cin, 27, out.data_ptr(), nx, ny, nz, nb, 7,
+                                     192, st.data_ptr(), None)
+
+    prev = L.lbnn_set_wait_limit(0)
+    try:
+        assert call() == 0, lib.lb_last_error()
+        torch.cuda.synchronize()
+        assert int(st[0].item()) & 16
+        with pytest.raises(L.LBError) as e:
+            L.lbnn_check_status(st.data_ptr())
+        assert e.value.code == L.LB_ETIMEOUT
+        assert int(st[0].item()) == 0  # cleared by the check
+    finally:
+        L.lbnn_set_wait_limit(prev)
+    before = out.cpu().numpy()
+    assert np.all(before == (7.0 if kind == "fwd" else 0.0))  # nothing written after the give-up
+    assert call() == 0, lib.lb_last_error()
+    L.lbnn_check_status(st.data_ptr())
+    got = out.cpu().numpy()
+    if kind == "fwd":
+        ref = U.conv3d(X, W, np.zeros(cout), (1, 1, 1), 27)
+    else:
+        _, ref, _ = U.conv3d_backward(X, np.zeros((cout, 27, cin)), G, (1, 1, 1), 27)
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())

@@ -177,11 +177,12 @@ int lb_init_fields(lb_handle* h, const float* phi, const float* rho, const float
  * Runs of 12 steps are replayed from a captured CUDA graph. */
 int lb_step(lb_handle* h, int64_t nsteps);
 
-/* Choose the tile shape of the step kernel (0..4: 32x8x4, 32x8x8, 32x8x4
+/* Choose the tile shape of the step kernel (0..5: 32x8x4, 32x8x8, 32x8x4
  * with a register cap for 3 CTAs per SM, 32x8x6 capped for 3 CTAs per SM,
- * 32x4x4 capped for 6 CTAs per SM, nodes per CTA); used by the autotuner.
- * Results do not depend on the tile (bit for bit).  lb_get_tile returns the
- * current index. */
+ * 32x4x4 capped for 6 CTAs per SM, nodes per CTA; 5: 32x8x8 with the
+ * near-contact scan of each interface node inside the node loop instead of
+ * a phase of its own); used by the autotuner.  Results do not depend on the
+ * tile (bit for bit).  lb_get_tile returns the current index. */
 int lb_set_tile(lb_handle* h, int tile);
 int lb_get_tile(const lb_handle* h);
 

@@ -415,6 +415,54 @@ __device__ __forceinline__ void pull_fast(const View<ST>& S, const Geo& g, const
   }
 }
 
+// The pull of pull_fast split in two: the raw stored values (both sets, or
+// the single set's totals) are loaded first and decoded and summed later, so
+// that independent work (the near-contact scan) runs while the loads are in
+// flight.  Same values and the same order of additions as pull_fast.
+template <int ST, bool WALLFREE, bool IDX32>
+__device__ __forceinline__ void pull_raw(const View<ST>& S, const Geo& g, const Nbr& n, int self,
+                                         typename Store<ST>::E ra[Q], typename Store<ST>::E rb[Q]) {
+  using I = typename std::conditional<IDX32, unsigned, size_t>::type;
+  const I N = (I)g.N;
+  int rbo[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rbo[b][c] = g.nx * (n.ys[b] + g.ny * n.zs[c]);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int a = 1 - cx(i), b = 1 - cy(i), c = 1 - cz(i);
+    int src = n.xs[a] + rbo[b][c];
+    I dir = (I)i;
+    if constexpr (!WALLFREE) {
+      const bool bb = n.sx[a] | n.sy[b] | n.sz[c];
+      src = bb ? self : src;
+      dir = bb ? (I)opp(i) : dir;
+    }
+    ra[i] = S.f[dir * N + (I)src];
+    if constexpr (Store<ST>::TWOSET) rb[i] = S.f[((I)Q + dir) * N + (I)src];
+  }
+}
+template <int ST>
+__device__ __forceinline__ void pull_raw_finish(const typename Store<ST>::E ra[Q], const typename Store<ST>::E rb[Q],
+                                                typename Store<ST>::R f[Q], typename Store<ST>::R& rA,
+                                                typename Store<ST>::R& rB) {
+  using R = typename Store<ST>::R;
+  rA = R(0);
+  rB = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if constexpr (Store<ST>::TWOSET) {
+      const R va = decode<ST>(ra[i], i), vb = decode<ST>(rb[i], i);
+      f[i] = va + vb;
+      rA += va;
+      rB += vb;
+    } else {
+      f[i] = decode<ST>(ra[i], i);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // write-side accumulation of the next time level's component densities
 // ---------------------------------------------------------------------------
@@ -590,7 +638,7 @@ __global__ void __launch_bounds__(256) k_phi_acc(View<ST> S, Geo g, unsigned lon
 // the queue counter.
 constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 
-template <typename R, int TX, int TY, int TZ, int H, int NPH = 1>
+template <typename R, int TX, int TY, int TZ, int H, int NPH = 1, bool QH = true>
 struct Layout {
   static constexpr int HX = H == 1 ? 1 : (H + 3) / 4 * 4;
   static constexpr int SX = TX + 2 * HX, SY = TY + 2 * H, SZ = TZ + 2 * H, SXY = SX * SY, NS = SXY * SZ;
@@ -599,9 +647,10 @@ struct Layout {
   // NPH staged scalar fields of NS values each (phi; the Shan-Chen model
   // adds psi_A and psi_B)
   static constexpr size_t off_acc = align16(sizeof(R) * (size_t)NS * NPH);
+  // the scan's queue and h (QH: a tile that scans in its own phase)
   static constexpr size_t off_queue = off_acc + align16(8 * (size_t)Acc<R>::W * (size_t)E);
-  static constexpr size_t off_h = off_queue + (H > 1 ? align16(2 * (size_t)NT) : 0);
-  static constexpr size_t off_count = off_h + (H > 1 ? align16((size_t)NT) : 0);
+  static constexpr size_t off_h = off_queue + (H > 1 && QH ? align16(2 * (size_t)NT) : 0);
+  static constexpr size_t off_count = off_h + (H > 1 && QH ? align16((size_t)NT) : 0);
   static constexpr size_t bytes = off_count + 16;
 };
 
@@ -877,13 +926,18 @@ __device__ __forceinline__ void send(unsigned long long* sw, int e0, const Nbr& 
 // send the post-collision component populations to the tile's partial sums.
 // sp holds phi of the tile and its halo (Layout), hs the near-contact
 // distance of each tile node (read when A_h != 0).
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, bool WALLFREE, bool IDX32, bool REG>
+// INL: the near-contact scan of an interface node runs here, between the
+// loads and the sums of its pull, instead of in a separate phase of the tile
+// (same h: the same scan from the same gradient).  zero_acc (non-null): the
+// accumulator two steps ahead, zeroed here node by node.
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, bool WALLFREE, bool IDX32, bool REG,
+          bool INL = false>
 __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O, const InitBuf& init, const Geo& g,
                                            const Phys& P, const unsigned char* hs,
                                            typename Store<ST>::R* __restrict__ fields,
                                            unsigned* __restrict__ status, const typename Store<ST>::R* sp,
                                            unsigned long long* sw, const unsigned long long* __restrict__ accin,
-                                           int x0, int y0, int z0) {
+                                           int x0, int y0, int z0, unsigned long long* __restrict__ zero_acc = nullptr) {
   using R = typename Store<ST>::R;
   using L = Layout<R, TX, TY, TZ, H>;
   using I = typename std::conditional<IDX32, unsigned, size_t>::type;
@@ -896,6 +950,7 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
     if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
     const int self = x + g.nx * (y + g.ny * z);
+    if (zero_acc) Acc<R>::zero(zero_acc, (size_t)self);  // the accumulator two steps ahead
     if (!WALLFREE && is_solid(g, x, y, z)) {
       if constexpr (WF) {
         for (int k = 0; k < NFIELDS; ++k) fields[(size_t)k * NF + self] = R(0);
@@ -908,14 +963,29 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
     const int c = (lz + H) * L::SXY + (threadIdx.y + H) * L::SX + (threadIdx.x + L::HX);
     const int e0 = (lz + 1) * L::EXY + (threadIdx.y + 1) * L::EX + (threadIdx.x + 1);
     const R phx = sp[c];
-    if constexpr (LOADER == LOAD_PULL) {
+    // colour gradient from the tile; near-contact distance from the scan
+    R gr[3], gg;
+    int h = 0;
+    constexpr bool SPLIT = INL && LOADER == LOAD_PULL && !Store<ST>::MOMENT;
+    if constexpr (SPLIT) {
+      typename Store<ST>::E ra[Q], rb[Q];
+      pull_raw<ST, WALLFREE, IDX32>(S, g, n, self, ra, rb);
+      tile_grad<R, WALLFREE>(sp, c, L::SX, L::SXY, gr);
+      gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+      if (H > 1 && A_h != R(0) && fabs(phx) < R(P.phi_I) && gg >= R(NC_GRAD_MIN))
+        h = nc_scan<R, WALLFREE>(sp, c, L::SX, L::SXY, P.K, x, y, z, g, P, gr, gg);
+      pull_raw_finish<ST>(ra, rb, f, rA, rB);
+    }
+    if constexpr (SPLIT && Store<ST>::TWOSET) {
+      // pulled and summed above
+    } else if constexpr (LOADER == LOAD_PULL) {
       if constexpr (Store<ST>::TWOSET) {
         pull_fast<ST, WALLFREE, IDX32, false>(S, g, n, self, f, rA, rB);
       } else {
         // single set: rhoA of the node is the sum the senders accumulated
         // (what a pull of the rebuilt f^A_i gives), so the neighbours' colour
         // scalars need not be read
-        pull_fast<ST, WALLFREE, IDX32, true>(S, g, n, self, f, rA, rB);
+        if constexpr (!SPLIT) pull_fast<ST, WALLFREE, IDX32, true>(S, g, n, self, f, rA, rB);
         R rt = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) rt += f[i];
@@ -942,14 +1012,20 @@ __device__ __forceinline__ void step_nodes(const View<ST>& S, const View<ST>& O,
       if (cz(p)) j2 += R(cz(p)) * d;
     }
 
-    // colour gradient from the tile; near-contact distance from the scan
-    R gr[3];
-    tile_grad<R, WALLFREE>(sp, c, L::SX, L::SXY, gr);
-    const R gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-    int h = 0;
+    if constexpr (!SPLIT) {
+      tile_grad<R, WALLFREE>(sp, c, L::SX, L::SXY, gr);
+      gg = sqrt_(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+      if (H > 1 && A_h != R(0)) {
+        if constexpr (INL) {
+          if (fabs(phx) < R(P.phi_I) && gg >= R(NC_GRAD_MIN))
+            h = nc_scan<R, WALLFREE>(sp, c, L::SX, L::SXY, P.K, x, y, z, g, P, gr, gg);
+        } else {
+          h = hs[(lz * TY + threadIdx.y) * TX + threadIdx.x];
+        }
+      }
+    }
     R Ahh = R(0);
     if (H > 1 && A_h != R(0)) {
-      h = hs[(lz * TY + threadIdx.y) * TX + threadIdx.x];
       if (h > 0) {
         const R hk = R(h);
         if (hk <= R(P.h_min)) Ahh = A_h;
@@ -1427,13 +1503,13 @@ __global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : 2)
 
 // One tile of the step: clear, stage, scan, step, flush.  Ends with a
 // barrier, so the caller may reuse the shared memory.
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, bool IDX32>
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, bool IDX32, bool INL = false>
 __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, const InitBuf& init, const PhiSrc& src,
                                           const AccBufs& ab, const Geo& g, const Phys& P,
                                           typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status,
                                           unsigned char* smem, int x0, int y0, int z0) {
   using R = typename Store<ST>::R;
-  using L = Layout<R, TX, TY, TZ, H>;
+  using L = Layout<R, TX, TY, TZ, H, 1, !INL>;
   R* sp = reinterpret_cast<R*>(smem);
   unsigned long long* sw = reinterpret_cast<unsigned long long*>(smem + L::off_acc);
   unsigned short* queue = reinterpret_cast<unsigned short*>(smem + L::off_queue);
@@ -1441,10 +1517,13 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
   int* count = reinterpret_cast<int*>(smem + L::off_count);
   const int tid = threadIdx.y * TX + threadIdx.x;
   if constexpr (WS) {
-    // this tile's nodes of the accumulator two steps ahead
-    for (int lz = 0; lz < TZ; ++lz) {
-      const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
-      if (x < g.nx && y < g.ny && z < g.nz) Acc<R>::zero(ab.zero, (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z));
+    // this tile's nodes of the accumulator two steps ahead (INL: in the node loop)
+    if constexpr (!INL) {
+      for (int lz = 0; lz < TZ; ++lz) {
+        const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + lz;
+        if (x < g.nx && y < g.ny && z < g.nz)
+          Acc<R>::zero(ab.zero, (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z));
+      }
     }
     for (int e = tid; e < Acc<R>::W * L::E; e += TX * TY) sw[e] = 0ull;
   }
@@ -1452,30 +1531,32 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
   if (src.acc) stage_phi<R, true, TX, TY, TZ, H>(src, g, sp, x0, y0, z0);
   else stage_phi<R, false, TX, TY, TZ, H>(src, g, sp, x0, y0, z0);
   __syncthreads();
-  if constexpr (H > 1) {
-    if (P.A_h != 0.0) {
+  const bool nc = H > 1 && P.A_h != 0.0;
+  if constexpr (H > 1 && !INL) {
+    if (nc) {
       if (region_walled(g, x0, y0, z0, TX, TY, TZ, P.K + 1))
         nc_tile<R, TX, TY, TZ, H, false>(sp, g, P, hs, queue, count, x0, y0, z0);
       else
         nc_tile<R, TX, TY, TZ, H, true>(sp, g, P, hs, queue, count, x0, y0, z0);
     }
   }
-  // a tile whose one-node halo holds no solid node needs no bounce-back or wall tests
-  const bool wallfree = !region_walled(g, x0, y0, z0, TX, TY, TZ, 1);
+  // a tile whose one-node halo holds no solid node needs no bounce-back or
+  // wall tests (INL: nor the scan's halo of K + 1 nodes)
+  const bool wallfree = !region_walled(g, x0, y0, z0, TX, TY, TZ, (INL && nc) ? P.K + 1 : 1);
   if (P.collision == 1) {  // regularised collision
     if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, true>(S, O, init, g, P, hs, fields, status, sp, sw,
-                                                                       src.acc, x0, y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, true, INL>(S, O, init, g, P, hs, fields, status, sp,
+                                                                            sw, src.acc, x0, y0, z0, INL ? ab.zero : nullptr);
     else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, true>(S, O, init, g, P, hs, fields, status, sp, sw,
-                                                                        src.acc, x0, y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, true, INL>(S, O, init, g, P, hs, fields, status, sp,
+                                                                             sw, src.acc, x0, y0, z0, INL ? ab.zero : nullptr);
   } else {
     if (wallfree)
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, false>(S, O, init, g, P, hs, fields, status, sp, sw,
-                                                                        src.acc, x0, y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, false, INL>(S, O, init, g, P, hs, fields, status, sp,
+                                                                             sw, src.acc, x0, y0, z0, INL ? ab.zero : nullptr);
     else
-      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, false>(S, O, init, g, P, hs, fields, status, sp, sw,
-                                                                         src.acc, x0, y0, z0);
+      step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, false, INL>(S, O, init, g, P, hs, fields, status,
+                                                                              sp, sw, src.acc, x0, y0, z0, INL ? ab.zero : nullptr);
   }
   __syncthreads();
   if constexpr (WS) {
@@ -1484,13 +1565,14 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
   }
 }
 
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, bool IDX32, int MINB = 2>
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, bool IDX32, int MINB = 2,
+          bool INL = false>
 __global__ void __launch_bounds__(TX* TY, (ST == 3) ? 1 : MINB)
     k_step(View<ST> S, View<ST> O, InitBuf init, PhiSrc src, AccBufs ab, Geo g, Phys P,
            typename Store<ST>::R* __restrict__ fields, unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  step_tile<ST, LOADER, WS, WF, TX, TY, TZ, H, IDX32>(S, O, init, src, ab, g, P, fields, status, smem_raw,
-                                                      blockIdx.x * TX, blockIdx.y * TY, blockIdx.z * TZ);
+  step_tile<ST, LOADER, WS, WF, TX, TY, TZ, H, IDX32, INL>(S, O, init, src, ab, g, P, fields, status, smem_raw,
+                                                           blockIdx.x * TX, blockIdx.y * TY, blockIdx.z * TZ);
 }
 
 // ---------------------------------------------------------------------------

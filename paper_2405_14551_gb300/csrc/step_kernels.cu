@@ -6,8 +6,9 @@ namespace lbcg {
 
 // tile 2: the 32x8x4 tile with registers capped for 3 CTAs per SM; tile 3: a
 // 32x8x6 tile capped for 3 CTAs per SM; tile 4: 32x4x4 (128 threads) capped
-// for 6 CTAs per SM
-const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 8, 4}, {32, 8, 6}, {32, 4, 4}};
+// for 6 CTAs per SM; tile 5: 32x8x8 with the near-contact scan inside the
+// node loop
+const Tile kTiles[NUM_TILES] = {{32, 8, 4}, {32, 8, 8}, {32, 8, 4}, {32, 8, 6}, {32, 4, 4}, {32, 8, 8}};
 
 template <int ST>
 cudaError_t launch_phi_acc_t(const Geo& g, const StateBuf& in, unsigned long long* acc, cudaStream_t st);

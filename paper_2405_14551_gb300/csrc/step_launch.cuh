@@ -54,13 +54,13 @@ cudaError_t launch_phi_acc_t(const Geo& g, const StateBuf& in, unsigned long lon
   return cudaGetLastError();
 }
 
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, int MINB = 2>
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, int MINB = 2, bool INL = false>
 inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init, PhiSrc src,
                                  AccBufs ab, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  const size_t smem = Layout<R, TX, TY, TZ, H>::bytes;
-  auto kern = fits_idx32(g.N) ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, true, MINB>
-                              : k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, false, MINB>;
+  const size_t smem = Layout<R, TX, TY, TZ, H, 1, !INL>::bytes;
+  auto kern = fits_idx32(g.N) ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, true, MINB, INL>
+                              : k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, false, MINB, INL>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -73,7 +73,7 @@ inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in
   return cudaGetLastError();
 }
 
-// Tile shapes of the hot variant (pull, write state): 0..4 as kTiles; the
+// Tile shapes of the hot variant (pull, write state): 0..5 as kTiles; the
 // widest halo (7) only with tile 0.  Other variants and FP64 use tile 0.
 template <int ST, int LOADER, bool WS, bool WF>
 inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
@@ -87,6 +87,7 @@ inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, cons
         case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, H, 3>(g, p, in, init, src, ab, out, fields, status, st);
         case 3: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 6, H, 3>(g, p, in, init, src, ab, out, fields, status, st);
         case 4: return launch_step_t<ST, LOADER, WS, WF, 32, 4, 4, H, 6>(g, p, in, init, src, ab, out, fields, status, st);
+        case 5: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8, H, 2, true>(g, p, in, init, src, ab, out, fields, status, st);
         default: break;
       }
     }

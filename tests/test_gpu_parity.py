@@ -171,6 +171,40 @@ def test_tile_shapes_give_identical_results():
                 np.testing.assert_array_equal(f[k], ref[k])
 
 
+@pytest.mark.parametrize("storage,walls,ah", [("twoset_f32", 0b110, 0.1), ("reduced_f32", 0b010, 0.1),
+                                              ("reduced_f16", 0b111, 0.1), ("moment_f32", 0b100, 0.1),
+                                              ("twoset_f32", 0b000, 0.1), ("twoset_f32", 0b010, 0.0),
+                                              ("twoset_f64", 0b010, 0.1)])
+def test_inline_scan_tiles_match_tile_zero(storage, walls, ah):
+    """Tile 5 runs the near-contact scan of each interface node inside the
+    node loop (between the loads and the sums of its pull) instead of in a
+    phase of the tile, and zeroes the accumulator two steps ahead there too;
+    the scan, its gradient and so h are the same, so the results must equal
+    tile 0's bit for bit: a dense emulsion with walls on various axes, a
+    ragged nz = 45, every storage, near contact on and off."""
+    import paper_2405_14551_gb300.lbcg as L
+    shape = (40, 36, 45)
+    phi, _ = W.dense_emulsion_phi(shape, walls, 77, rmin=5.0, rmax=7.0, film=6.0)
+    p = dict(W.BASE, A_h=ah, h_min=3.0, h_max=3.0, g=(0.0, 0.0, 1e-6), g_mode=1)
+    wl = W.Workload("emulsion_40x36x45", shape, walls, p, 0, phi=phi)
+    coll = {"collision": 1} if storage == "moment_f32" else {}
+    ref = None
+    for tile in (0, 5):
+        s = make_gpu(wl, storage=storage, **coll)
+        L.lb_set_tile(s.h, tile)
+        s.step(29)
+        s.check()
+        f = s.fields(("phi", "rho", "ux", "uz", "h"))
+        s.close()
+        if ref is None:
+            ref = f
+            if ah > 0:
+                assert np.count_nonzero(f["h"]) > 0
+        else:
+            for k in f:
+                np.testing.assert_array_equal(f[k], ref[k], err_msg=f"tile {tile} field {k}")
+
+
 def test_reductions_laplace_count(small_oracle_200):
     wl, _, _, red_o = small_oracle_200
     s = make_gpu(wl)

@@ -205,8 +205,7 @@ class ClockSampler:
 # grows with the node count) together with a digest of the kernel sources it
 # was taken on: a changed kernel reports null until it is captured again.
 K_STEP_TRAFFIC = {  # storage -> (bytes per node, source digest, tile)
-    "twoset_f32": (452.2, "504c38d2226b5550", 1),   # mean of 2 launches: 1896.1 / 1897.5 MB per 4194304 nodes
-    "reduced_f16": (145.2, "504c38d2226b5550", 3),  # 609.2 MB per 4194304 nodes
+    "twoset_f32": (450.4, "ad4181f074899177", 5),  # 975.3 + 913.8 MB per 4194304 nodes
 }
 
 

@@ -182,7 +182,9 @@ int lb_step(lb_handle* h, int64_t nsteps);
  * 32x4x4 capped for 6 CTAs per SM, nodes per CTA; 5: 32x8x8 with the
  * near-contact scan of each interface node inside the node loop instead of
  * a phase of its own); used by the autotuner.  Results do not depend on the
- * tile (bit for bit).  lb_get_tile returns the current index. */
+ * tile (bit for bit).  Lattices too large for 32-bit population offsets
+ * (2 x 27 x nodes >= 2^32) step with tile 0 whatever the setting.
+ * lb_get_tile returns the current index. */
 int lb_set_tile(lb_handle* h, int tile);
 int lb_get_tile(const lb_handle* h);
 
@@ -319,7 +321,7 @@ int lb_batch_step(lb_batch* b, int64_t nsteps);
 /* The one-run-at-a-time baseline: lb_step on each run in turn. */
 int lb_batch_step_sequential(lb_batch* b, int64_t nsteps);
 
-/* Tile shape (0..4, as lb_set_tile) and persistent CTAs per SM (1..16). */
+/* Tile shape (0..5, as lb_set_tile) and persistent CTAs per SM (1..16). */
 int lb_batch_set_tile(lb_batch* b, int tile, int blocks_per_sm);
 
 /* Autotuner: time `steps` batched steps for every tile shape and CTAs-per-SM

@@ -84,13 +84,11 @@ struct RunDesc {
 };
 
 // Tile shapes of the fused step kernel (x, y extent of the thread block and z
-// nodes per thread).  Tile 5 scans near contact inside the node loop; the
-// batched kernel takes tiles 0..NUM_BATCH_TILES - 1.
+// nodes per thread).  Tile 5 scans near contact inside the node loop.
 struct Tile {
   int tx, ty, tz;
 };
 constexpr int NUM_TILES = 6;
-constexpr int NUM_BATCH_TILES = 5;
 extern const Tile kTiles[NUM_TILES];
 
 size_t elem_bytes(int storage);

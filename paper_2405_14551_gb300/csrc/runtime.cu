@@ -1105,8 +1105,8 @@ int lb_batch_set_stream(lb_batch* b, void* stream) {
 
 int lb_batch_set_tile(lb_batch* b, int tile, int blocks_per_sm) {
   if (!b) return set_err(LB_EINVAL, "null batch");
-  if (tile < 0 || tile >= NUM_BATCH_TILES || blocks_per_sm < 1 || blocks_per_sm > 16)
-    return set_err(LB_EINVAL, "tile in 0..4 and blocks_per_sm in 1..16");
+  if (tile < 0 || tile >= NUM_TILES || blocks_per_sm < 1 || blocks_per_sm > 16)
+    return set_err(LB_EINVAL, "tile in 0..5 and blocks_per_sm in 1..16");
   if (tile != b->tile || blocks_per_sm != b->blocks_per_sm) {
     b->tile = tile;
     b->blocks_per_sm = blocks_per_sm;
@@ -1198,7 +1198,7 @@ int batch_tune(lb_batch* b, int32_t steps, int use_cache, double* result) {
     int tile, bps;
     double ms;
     while (in >> k >> tile >> bps >> ms) {
-      if (k == key && tile >= 0 && tile < NUM_BATCH_TILES && bps >= 1 && bps <= 16) {
+      if (k == key && tile >= 0 && tile < NUM_TILES && bps >= 1 && bps <= 16) {
         if ((rc = lb_batch_set_tile(b, tile, bps))) return rc;
         result[0] = tile;
         result[1] = bps;
@@ -1214,7 +1214,7 @@ int batch_tune(lb_batch* b, int32_t steps, int use_cache, double* result) {
   cudaEvent_t e0, e1;
   LB_CUDA(cudaEventCreate(&e0));
   LB_CUDA(cudaEventCreate(&e1));
-  for (int tile = 0; tile < NUM_BATCH_TILES; ++tile) {
+  for (int tile = 0; tile < NUM_TILES; ++tile) {
     for (int bps : bps_opts) {
       if ((rc = lb_batch_set_tile(b, tile, bps)) || (rc = batch_prepare(b))) break;
       for (int k = 0; k < 2 && rc == LB_OK; ++k) {

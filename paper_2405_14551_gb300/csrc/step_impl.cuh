@@ -1543,20 +1543,21 @@ __device__ __forceinline__ void step_tile(const View<ST>& S, const View<ST>& O, 
   // a tile whose one-node halo holds no solid node needs no bounce-back or
   // wall tests (INL: nor the scan's halo of K + 1 nodes)
   const bool wallfree = !region_walled(g, x0, y0, z0, TX, TY, TZ, (INL && nc) ? P.K + 1 : 1);
+  unsigned long long* zacc = INL ? ab.zero : nullptr;
   if (P.collision == 1) {  // regularised collision
     if (wallfree)
       step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, true, INL>(S, O, init, g, P, hs, fields, status, sp,
-                                                                            sw, src.acc, x0, y0, z0, INL ? ab.zero : nullptr);
+                                                                            sw, src.acc, x0, y0, z0, zacc);
     else
       step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, true, INL>(S, O, init, g, P, hs, fields, status, sp,
-                                                                             sw, src.acc, x0, y0, z0, INL ? ab.zero : nullptr);
+                                                                             sw, src.acc, x0, y0, z0, zacc);
   } else {
     if (wallfree)
       step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, true, IDX32, false, INL>(S, O, init, g, P, hs, fields, status, sp,
-                                                                             sw, src.acc, x0, y0, z0, INL ? ab.zero : nullptr);
+                                                                             sw, src.acc, x0, y0, z0, zacc);
     else
       step_nodes<ST, LOADER, WS, WF, TX, TY, TZ, H, false, IDX32, false, INL>(S, O, init, g, P, hs, fields, status,
-                                                                              sp, sw, src.acc, x0, y0, z0, INL ? ab.zero : nullptr);
+                                                                              sp, sw, src.acc, x0, y0, z0, zacc);
   }
   __syncthreads();
   if constexpr (WS) {
@@ -1592,7 +1593,7 @@ __device__ __forceinline__ int find_run(const RunDesc* runs, int nruns, long lon
   return lo;
 }
 
-template <int ST, int TX, int TY, int TZ, int H, bool IDX32, int MINB = 2>
+template <int ST, int TX, int TY, int TZ, int H, bool IDX32, int MINB = 2, bool INL = false>
 __global__ void __launch_bounds__(TX* TY, MINB)
     k_step_batched(const RunDesc* __restrict__ runs, int nruns, long long ntiles, int parity, int k,
                    unsigned* __restrict__ status) {
@@ -1609,9 +1610,10 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     const Phys P = d.p;
     const PhiSrc src{nullptr, d.acc[k]};
     const AccBufs ab{d.acc[(k + 1) % 3], d.acc[(k + 2) % 3]};
-    step_tile<ST, LOAD_PULL, true, false, TX, TY, TZ, H, IDX32>(view<ST>(d.S[parity]), view<ST>(d.S[parity ^ 1]),
-                                                                none, src, ab, g, P, nullptr, status, smem_raw,
-                                                                bx * TX, by * TY, bz * TZ);
+    step_tile<ST, LOAD_PULL, true, false, TX, TY, TZ, H, IDX32, INL>(view<ST>(d.S[parity]),
+                                                                     view<ST>(d.S[parity ^ 1]), none, src, ab, g, P,
+                                                                     nullptr, status, smem_raw, bx * TX, by * TY,
+                                                                     bz * TZ);
   }
 }
 

@@ -54,13 +54,24 @@ cudaError_t launch_phi_acc_t(const Geo& g, const StateBuf& in, unsigned long lon
   return cudaGetLastError();
 }
 
-template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, int MINB = 2, bool INL = false>
+// IX: the offset width the kernel is built for (1: 32-bit, 0: 64-bit, -1:
+// either, chosen by the lattice size).
+template <int ST, int LOADER, bool WS, bool WF, int TX, int TY, int TZ, int H, int MINB = 2, bool INL = false,
+          int IX = -1>
 inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init, PhiSrc src,
                                  AccBufs ab, StateBuf out, void* fields, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
   const size_t smem = Layout<R, TX, TY, TZ, H, 1, !INL>::bytes;
-  auto kern = fits_idx32(g.N) ? k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, true, MINB, INL>
-                              : k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, false, MINB, INL>;
+  const bool i32 = fits_idx32(g.N);
+  using K = decltype(&k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, true, MINB, INL>);
+  K kern = nullptr;
+  if constexpr (IX != 0) {
+    if (i32) kern = k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, true, MINB, INL>;
+  }
+  if constexpr (IX != 1) {
+    if (!i32) kern = k_step<ST, LOADER, WS, WF, TX, TY, TZ, H, false, MINB, INL>;
+  }
+  if (!kern) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -74,7 +85,8 @@ inline cudaError_t launch_step_t(const Geo& g, const Phys& p, const StateBuf& in
 }
 
 // Tile shapes of the hot variant (pull, write state): 0..5 as kTiles; the
-// widest halo (7) only with tile 0.  Other variants and FP64 use tile 0.
+// widest halo (7) only with tile 0.  Other variants, FP64 and lattices that
+// need 64-bit offsets use tile 0.
 template <int ST, int LOADER, bool WS, bool WF>
 inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, const StateBuf& in, const InitBuf& init,
                                      PhiSrc src, AccBufs ab, StateBuf out, void* fields, unsigned* status,
@@ -82,13 +94,15 @@ inline cudaError_t launch_step_tiles(int tile, const Geo& g, const Phys& p, cons
   return with_stage_halo(stage_halo(p), [&](auto hc) -> cudaError_t {
     constexpr int H = decltype(hc)::value;
     if constexpr (LOADER == LOAD_PULL && WS && !WF && ST != 3 && H < 7) {
-      switch (tile) {
-        case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8, H>(g, p, in, init, src, ab, out, fields, status, st);
-        case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, H, 3>(g, p, in, init, src, ab, out, fields, status, st);
-        case 3: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 6, H, 3>(g, p, in, init, src, ab, out, fields, status, st);
-        case 4: return launch_step_t<ST, LOADER, WS, WF, 32, 4, 4, H, 6>(g, p, in, init, src, ab, out, fields, status, st);
-        case 5: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8, H, 2, true>(g, p, in, init, src, ab, out, fields, status, st);
-        default: break;
+      if (fits_idx32(g.N)) {
+        switch (tile) {
+          case 1: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8, H, 2, false, 1>(g, p, in, init, src, ab, out, fields, status, st);
+          case 2: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, H, 3, false, 1>(g, p, in, init, src, ab, out, fields, status, st);
+          case 3: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 6, H, 3, false, 1>(g, p, in, init, src, ab, out, fields, status, st);
+          case 4: return launch_step_t<ST, LOADER, WS, WF, 32, 4, 4, H, 6, false, 1>(g, p, in, init, src, ab, out, fields, status, st);
+          case 5: return launch_step_t<ST, LOADER, WS, WF, 32, 8, 8, H, 2, true, 1>(g, p, in, init, src, ab, out, fields, status, st);
+          default: break;
+        }
       }
     }
     return launch_step_t<ST, LOADER, WS, WF, 32, 8, 4, H>(g, p, in, init, src, ab, out, fields, status, st);
@@ -157,12 +171,12 @@ cudaError_t launch_export_t(int loader, const Geo& g, const Phys& p, const State
   return cudaGetLastError();
 }
 
-template <int ST, int TX, int TY, int TZ, int H, bool IDX32, int MINB = 2>
+template <int ST, int TX, int TY, int TZ, int H, bool IDX32, int MINB = 2, bool INL = false>
 inline cudaError_t launch_batched_step_t(const RunDesc* d_runs, int nruns, long long ntiles, int parity, int k,
                                          int blocks, unsigned* status, cudaStream_t st) {
   using R = typename Store<ST>::R;
-  const size_t smem = Layout<R, TX, TY, TZ, H>::bytes;
-  auto kern = k_step_batched<ST, TX, TY, TZ, H, IDX32, MINB>;
+  const size_t smem = Layout<R, TX, TY, TZ, H, 1, !INL>::bytes;
+  auto kern = k_step_batched<ST, TX, TY, TZ, H, IDX32, MINB, INL>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -177,12 +191,13 @@ inline cudaError_t launch_batched_tiles(int tile, int halo, const RunDesc* d_run
                                         int parity, int k, int blocks, unsigned* status, cudaStream_t st) {
   return with_stage_halo(halo, [&](auto hc) -> cudaError_t {
     constexpr int H = decltype(hc)::value;
-    if constexpr (H < 7) {
+    if constexpr (H < 7 && IDX32) {  // 64-bit offsets: tile 0
       switch (tile) {
         case 1: return launch_batched_step_t<ST, 32, 8, 8, H, IDX32>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
         case 2: return launch_batched_step_t<ST, 32, 8, 4, H, IDX32, 3>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
         case 3: return launch_batched_step_t<ST, 32, 8, 6, H, IDX32, 3>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
         case 4: return launch_batched_step_t<ST, 32, 4, 4, H, IDX32, 6>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
+        case 5: return launch_batched_step_t<ST, 32, 8, 8, H, IDX32, 2, true>(d_runs, nruns, ntiles, parity, k, blocks, status, st);
         default: break;
       }
     }

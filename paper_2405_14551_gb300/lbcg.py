@@ -302,7 +302,7 @@ def lb_copy_state(dst, src):
     _check(load_library().lb_copy_state(dst, src), "lb_copy_state")
 
 
-NUM_TILES = 6  # tile shapes of lb_set_tile (lb_batch_set_tile takes the first 5)
+NUM_TILES = 6  # tile shapes of lb_set_tile and lb_batch_set_tile
 
 
 def lb_set_tile(h, tile: int):

@@ -34,7 +34,7 @@ def test_batch_equals_one_at_a_time(storage):
     runs = small_sweep()
     b = L.Batch(runs, storage=storage)
     tile, bps, ms, cached = b.autotune(steps=2, use_cache=False)
-    assert 0 <= tile < 5 and bps in (1, 2, 4) and ms > 0
+    assert 0 <= tile < L.NUM_TILES and bps in (1, 2, 4) and ms > 0
     b.step(37)  # first step per run, two graph replays, four direct steps
     b.check()
     for r, w in enumerate(runs):

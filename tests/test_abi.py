@@ -155,3 +155,22 @@ def test_storage_formats_agree_between_header_and_binding():
                    "twoset_f64": 2 * 27 * 8, "moment_f32": 10 * 4 + 16}
     for name, st in L.STORAGE.items():
         assert L.BYTES_PER_NODE[st] == 2 * per_lattice[name], name
+
+
+def test_tile_count_agrees_between_library_and_binding(lib):
+    """The binding's tile count (which the bench's autotuner walks) is the
+    library's: the tile table has that many shapes, each a whole number of
+    warps, and lb_set_tile's documented range ends there."""
+    import paper_2405_14551_gb300.lbcg as L
+    csrc = os.path.join(ROOT, "paper_2405_14551_gb300", "csrc")
+    with open(os.path.join(csrc, "internal.h")) as f:
+        m = re.search(r"constexpr int NUM_TILES = (\d+);", f.read())
+    assert m and int(m.group(1)) == L.NUM_TILES
+    with open(os.path.join(csrc, "step_kernels.cu")) as f:
+        m = re.search(r"kTiles\[NUM_TILES\] = \{(.*?)\};", f.read(), re.S)
+    shapes = re.findall(r"\{(\d+), (\d+), (\d+)\}", m.group(1))
+    assert len(shapes) == L.NUM_TILES
+    assert all(int(x) * int(y) % 32 == 0 for x, y, _ in shapes)
+    with open(os.path.join(ROOT, "include", "lbcg.h")) as f:
+        assert f"(0..{L.NUM_TILES - 1}:" in f.read()
+    assert lib.lb_set_tile(None, 0) == L.LB_EINVAL

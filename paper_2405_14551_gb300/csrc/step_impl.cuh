@@ -11,7 +11,9 @@
 //      phi = (rhoA - rhoB)/(rhoA + rhoB) (Eq. order_param) from them;
 //   2. with near contact (A_h != 0, halo H > K): every interface node of the
 //      tile scans along its outward normal (Eqs. stress_jump,
-//      near_cont_force); the distance h stays in shared memory;
+//      near_cont_force); the distance h stays in shared memory.  The
+//      in-loop tile (INL) scans each interface node in item 3 instead,
+//      while the node's population loads are in flight;
 //   3. every thread pulls the 27 (x2) populations of its nodes (periodic
 //      wrap, halfway bounce-back at solid neighbours, Sec. III.D), takes the
 //      moments, the colour gradient from the staged tile, the repulsion from

@@ -53,6 +53,9 @@ def parse():
                     help="error-vs-time table of the FP32 and FP16 storages against the FP64 oracle on the 64^3 "
                          "dense-emulsion analogue (20000 steps; prints one JSON line)")
     ap.add_argument("--long-steps", type=int, default=20000, help="last checkpoint of --long-run")
+    ap.add_argument("--full-box", action="store_true",
+                    help="the dense emulsion at full size, 200 steps in the FP64 oracle and on the GPU (FP32 two-set, "
+                         "FP16-deviation): per-field errors over a fixed 64^3 crop and the whole box (prints one JSON line)")
     ap.add_argument("--conv", nargs="+", default=None, metavar="ARG",
                     help="MODE NX NY NZ CIN COUT [REPS]: time one surrogate convolution call instead "
                          "(MODE fwd, upcat or wgrad; used by the convolution profiles)")
@@ -650,6 +653,64 @@ def long_run(args):
                       "rows": rows}), flush=True)
 
 
+def full_box(args):
+    """The dense emulsion at its full size (256x256x512, walls y, seed 1234,
+    6-node films, near contact on, body force 1e-6 along z) from the same
+    initial phi in the FP64 oracle (host cores) and on the GPU in FP32 two-set
+    and FP16-deviation storage (the bench's step kernel, tile 5).  At steps 1,
+    10, 100 and 200: max and mean |field - oracle| per field over the fluid
+    nodes of a fixed 64^3 crop (x 96..159, y 96..159, z 224..287) and of the
+    whole box."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2405_14551_gb300.lbcg as L
+    from paper_2405_14551_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    wl = W.dense_emulsion((256, 256, 512), seed=SEED, device=torch.device("cuda"))
+    nx, ny, nz = wl.shape
+    o = oracle.OracleSim(oracle.make_params(nx, ny, nz, walls=wl.walls, **wl.params))
+    o.init_fields(wl.phi.astype(np.float64))
+    L.load_library()
+    sims = {}
+    for st in ("twoset_f32", "reduced_f16"):
+        sims[st] = L.Sim(nx, ny, nz, walls=wl.walls, storage=st, **wl.params)
+        sims[st].init_fields(wl.phi)
+        L.lb_set_tile(sims[st].h, 5)
+    fl = W.fluid_mask(wl.shape, wl.walls)
+    crop = (slice(224, 288), slice(96, 160), slice(96, 160))  # [z][y][x]
+    flc = fl[crop]
+    names = ("phi", "rho", "ux", "uy", "uz", "rhoA", "rhoB")
+    rows, t, t_orc = [], 0, 0.0
+    for cp in (1, 10, 100, 200):
+        t0 = time.perf_counter()
+        o.step(cp - t)
+        t_orc += time.perf_counter() - t0
+        for sm in sims.values():
+            sm.step(cp - t)
+        t = cp
+        fo = o.fields()
+        row = {"step": cp}
+        for st, sm in sims.items():
+            fg = sm.fields(names, f64=True)
+            err = {}
+            for k in names:
+                dc = np.abs(fg[k][crop][flc] - fo[k][crop][flc])
+                db = np.abs(fg[k][fl] - fo[k][fl])
+                err[k] = {"crop": [float(dc.max()), float(dc.mean())], "box": [float(db.max()), float(db.mean())]}
+            row[st] = err
+        rows.append(row)
+        print(json.dumps({"full_box_checkpoint": cp, "oracle_s": round(t_orc, 1)}), file=sys.stderr, flush=True)
+    for sm in sims.values():
+        sm.check()
+        sm.close()
+    o.close()
+    print(json.dumps({"full_box": wl.name, "seed": SEED, "droplets": wl.info.get("droplets"),
+                      "crop": "x 96..159, y 96..159, z 224..287", "oracle_cores": int(os.environ["OMP_NUM_THREADS"]),
+                      "oracle_s": round(t_orc, 1), "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.conv:
@@ -657,6 +718,9 @@ def main():
         return
     if args.long_run:
         long_run(args)
+        return
+    if args.full_box:
+        full_box(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -475,6 +475,34 @@ __device__ __forceinline__ void pull_raw_finish(const typename Store<ST>::E ra[Q
 // half, two's complement), so one atomic adds both.  FP64: SHIFT = 56 (sums
 // within +-128, step 1.4e-17), two 64-bit words per node.  RHO_MAX bounds the
 // density that the status check accepts, so that no sum leaves its range.
+// The accumulator words are staged, zeroed and updated by every step while
+// the population state streams through L2; their loads, stores and
+// reductions carry an evict-last L2 policy, so that more of them are still
+// in L2 when the next access comes (measured: 3.24 -> 3.17 ms per step on
+// the 256x256x512 emulsion).
+__device__ __forceinline__ unsigned long long acc_policy() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void acc_red(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(__cvta_generic_to_global(p)), "l"(v),
+               "l"(acc_policy())
+               : "memory");
+}
+__device__ __forceinline__ void acc_st(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(__cvta_generic_to_global(p)), "l"(v),
+               "l"(acc_policy())
+               : "memory");
+}
+__device__ __forceinline__ ulonglong2 acc_ld2(const unsigned long long* p) {
+  ulonglong2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+               : "=l"(v.x), "=l"(v.y)
+               : "l"(__cvta_generic_to_global(p)), "l"(acc_policy()));
+  return v;
+}
+
 template <typename R>
 struct Acc;
 template <>
@@ -496,7 +524,7 @@ struct Acc<float> {
                                                       const unsigned long long* sw, int E, int e) {
     const int* p = reinterpret_cast<const int*>(sw);
     const unsigned long long w = pack(p[e], p[E + e]);
-    if (w) atomicAdd(acc + node, w);
+    if (w) acc_red(acc + node, w);
   }
   __device__ static __forceinline__ bool shared_zero(const unsigned long long* sw, int E, int e) {
     const int* p = reinterpret_cast<const int*>(sw);
@@ -508,7 +536,7 @@ struct Acc<float> {
   __device__ static __forceinline__ void store(unsigned long long* acc, size_t node, S a, S b) {
     acc[node] = pack(a, b);
   }
-  __device__ static __forceinline__ void zero(unsigned long long* acc, size_t node) { acc[node] = 0ull; }
+  __device__ static __forceinline__ void zero(unsigned long long* acc, size_t node) { acc_st(acc + node, 0ull); }
   // phi = (rhoA - rhoB)/(rhoA + rhoB) of one packed word.  The halves are
   // rhoA and rhoB in units of 2^-28; with densities below RHO_MAX (< 2^30
   // units) the difference and the sum are exact 32-bit integers, each rounded
@@ -546,8 +574,8 @@ struct Acc<double> {
   }
   __device__ static __forceinline__ void flush_shared(unsigned long long* acc, size_t node,
                                                       const unsigned long long* sw, int E, int e) {
-    if (sw[e]) atomicAdd(acc + 2 * node, sw[e]);
-    if (sw[E + e]) atomicAdd(acc + 2 * node + 1, sw[E + e]);
+    if (sw[e]) acc_red(acc + 2 * node, sw[e]);
+    if (sw[E + e]) acc_red(acc + 2 * node + 1, sw[E + e]);
   }
   __device__ static __forceinline__ bool shared_zero(const unsigned long long* sw, int E, int e) {
     return (sw[e] | sw[E + e]) == 0ull;
@@ -557,8 +585,8 @@ struct Acc<double> {
     acc[2 * node + 1] = (unsigned long long)b;
   }
   __device__ static __forceinline__ void zero(unsigned long long* acc, size_t node) {
-    acc[2 * node] = 0ull;
-    acc[2 * node + 1] = 0ull;
+    acc_st(acc + 2 * node, 0ull);
+    acc_st(acc + 2 * node + 1, 0ull);
   }
   __device__ static __forceinline__ double phi_words(unsigned long long wa, unsigned long long wb) {
     const long long a = (long long)wa, b = (long long)wb;
@@ -668,7 +696,7 @@ struct PhiLoad {
   }
   // the V consecutive nodes from `node` (a multiple of V) as one load ...
   __device__ static __forceinline__ Raw ld(const PhiSrc& s, size_t node) {
-    if constexpr (FROM_ACC) return *reinterpret_cast<const ulonglong2*>(s.acc + Acc<R>::W * node);
+    if constexpr (FROM_ACC) return acc_ld2(s.acc + Acc<R>::W * node);
     else return *reinterpret_cast<const Raw*>(reinterpret_cast<const R*>(s.phi) + node);
   }
   // ... and their phi
